@@ -1,0 +1,362 @@
+"""Benchmark of the stencil-sweep hot path on GB300.
+
+Headline workload: 3D compressible Euler, FP32 stencil (FP64 dt and totals),
+256^3 cells, 5 conserved variables, MUSCL-Hancock with minmod slopes and
+Rusanov faces, halo 2, transmissive boundaries, spherical blast with 1 %
+seeded noise on rho (synthetic, seeded).  One benchmark step = one explicit
+time step of the whole field (one sweep launch: padding fill, staging,
+reconstruction, predictor, face fluxes, conservative update, CFL reduction).
+Metric: cell-updates/s (higher is better).  Inputs (335 MB per buffer) are
+larger than the 129 MB L2, so no flush is needed between steps.
+
+Also reported (secondary objects on the same JSON line): the AoS layout, the
+2D FP64 128^2 workload, the FIM eikonal solves (2048^2 and 192^3), the
+end-to-end solve through host buffers, the FP64 CPU oracle baseline, the
+roofline of the sweep kernel and the SM clocks during the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run: every rank runs an independent
+replica of the workload on its own GPU (the path is one GPU per problem),
+value = all ranks' cell-updates / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import inputs  # noqa: E402
+
+N3 = 256
+NSTEPS_SOLVE = 50
+BYTES_PER_CELL_UPDATE = 40  # FP32, 5 components: 20 B read + 20 B written per cell per step
+METRIC = "cell-updates/s"
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks / throttle reasons during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append(dict(sm=float(parts[1]), smax=float(parts[2]), power=float(parts[3]),
+                                 hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        reasons = set()
+        for r in rows:
+            if r["hw"] == "Active":
+                reasons.add("hw_slowdown")
+            if r["hwt"] == "Active":
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"] == "Active":
+                reasons.add("sw_thermal_slowdown")
+            if r["pcap"] == "Active":
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": float(np.median([r["sm"] for r in rows])), "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows),
+                "power_w_max": max(r["power"] for r in rows)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(value, world):
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def bench_gpu(args, rank, world, local):
+    import torch
+
+    import paper_2104_08571_gb300 as R
+
+    torch.cuda.set_device(local)
+    ctx = R.ripple_ctx_create(local)
+    R.use_torch_allocator(ctx, local)
+    stream = torch.cuda.Stream(device=local)
+    R.ripple_set_stream(ctx, stream)
+    MUSCL, TRA = R.RIPPLE_MUSCL_HANCOCK_MINMOD, R.RIPPLE_BC_TRANSMISSIVE
+    dims = (N3, N3, N3)
+    ncell = N3 ** 3
+    prm = R.make_fv_params([1.0 / N3] * 3, scheme=MUSCL, bc=TRA)
+    U0 = inputs.euler3d_blast(N3, seed=1).astype(np.float32)
+    U0_dev = torch.from_numpy(U0).to(f"cuda:{local}")
+    U0_dev_aos = torch.from_numpy(np.ascontiguousarray(np.moveaxis(U0, 0, -1))).to(f"cuda:{local}")
+    result = {}
+
+    def timed_steps(field, k, w):
+        for _ in range(w):
+            R.ripple_fv_step(field, prm, 1, stats=False)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            R.ripple_fv_step(field, prm, 1, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        barrier(world)
+        return ms
+
+    # ---- headline: SoA, inputs resident in HBM ----
+    f = R.ripple_field_create(ctx, dims, 5, R.RIPPLE_SOA, 2, R.RIPPLE_F32)
+    R.ripple_field_upload(f, U0_dev, R.RIPPLE_SOA)
+    R.ripple_fv_step(f, prm, 1, stats=False)  # first call: second buffer, prep, tensor maps
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        ms = timed_steps(f, args.steps, args.warmup)
+    clocks = clk.summary()
+    ms_max = allreduce_max(ms, world)
+    st = R.ripple_fv_step(f, prm, 0)  # synchronous error check + totals of the final state
+    result["soa_ms_per_step"] = ms / args.steps
+    result["soa_totals_mass"] = st["totals"][0]
+    R.ripple_field_destroy(f)
+
+    # ---- AoS layout, same workload ----
+    fa = R.ripple_field_create(ctx, dims, 5, R.RIPPLE_AOS, 2, R.RIPPLE_F32)
+    R.ripple_field_upload(fa, U0_dev_aos, R.RIPPLE_AOS)
+    R.ripple_fv_step(fa, prm, 1, stats=False)
+    torch.cuda.synchronize()
+    ms_aos = timed_steps(fa, args.steps, args.warmup)
+    R.ripple_fv_step(fa, prm, 0)
+    R.ripple_field_destroy(fa)
+
+    # ---- end to end: full 50-step solves from pinned host memory to host memory ----
+    pin_in = torch.from_numpy(U0).pin_memory()
+    pin_out = torch.empty_like(pin_in).pin_memory()
+    fe = R.ripple_field_create(ctx, dims, 5, R.RIPPLE_SOA, 2, R.RIPPLE_F32)
+    e2e_solves = max(1, args.e2e_solves)
+
+    def one_solve():
+        R.ripple_field_upload(fe, pin_in.numpy(), R.RIPPLE_SOA)
+        R.ripple_fv_step(fe, prm, NSTEPS_SOLVE, stats=False)
+        R.ripple_field_download(fe, R.RIPPLE_SOA, out=pin_out)
+
+    one_solve()  # warm-up
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_solves):
+        one_solve()
+    torch.cuda.synchronize()
+    e2e_s = allreduce_max(time.perf_counter() - t0, world)
+    R.ripple_field_destroy(fe)
+    e2e_value = world * e2e_solves * NSTEPS_SOLVE * ncell / e2e_s
+
+    # ---- secondary: 2D FP64 128^2 periodic Rusanov, 100 steps (latency bound) ----
+    U2 = inputs.euler2d_sine(128)
+    f2 = R.ripple_field_create(ctx, (128, 128), 4, R.RIPPLE_SOA, 1, R.RIPPLE_F64)
+    prm2 = R.make_fv_params([1.0 / 128] * 2)
+    R.ripple_field_upload(f2, U2)
+    R.ripple_fv_step(f2, prm2, 100)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    R.ripple_fv_step(f2, prm2, 100, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms2 = e0.elapsed_time(e1)
+    R.ripple_fv_step(f2, prm2, 0)
+    R.ripple_field_destroy(f2)
+
+    # ---- secondary: eikonal FIM solves ----
+    eik = {}
+    if not args.skip_eikonal:
+        for name, edims in (("2d_2048", (2048, 2048)), ("3d_192", (192, 192, 192))):
+            s = inputs.eikonal_slowness(edims, seed=1).astype(np.float32)
+            src = inputs.eikonal_sources(edims, seed=1)
+            fs = R.ripple_field_create(ctx, edims, 1, R.RIPPLE_SOA, 0, R.RIPPLE_F32)
+            ft = R.ripple_field_create(ctx, edims, 1, R.RIPPLE_SOA, 1, R.RIPPLE_F32)
+            R.ripple_field_upload(fs, s)
+            R.ripple_eikonal_solve(fs, ft, src, 1.0 / edims[0], 1e-6)  # warm-up
+            torch.cuda.synchronize()
+            reps = 3
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                est = R.ripple_eikonal_solve(fs, ft, src, 1.0 / edims[0], 1e-6)
+            dt = (time.perf_counter() - t0) / reps
+            ncells = int(np.prod(edims))
+            eik[name] = {"solve_ms": dt * 1e3, "solved_cells_per_s": ncells / dt,
+                         "godunov_updates_per_s": est["cell_updates"] / dt, "iterations": est["iterations"],
+                         "tile_visits": est["tile_visits"], "sources": len(src)}
+            R.ripple_field_destroy(fs)
+            R.ripple_field_destroy(ft)
+
+    R.ripple_ctx_destroy(ctx)
+    value = world * args.steps * ncell / (ms_max / 1e3)
+    hbm_peak, peak_kind = load_peaks()
+    achieved = BYTES_PER_CELL_UPDATE * ncell / (ms / args.steps / 1e3) / 1e9
+    return dict(value=value, ms_per_step=ms_max / args.steps, clocks=clocks, ms_aos=ms_aos / args.steps,
+                e2e_value=e2e_value, e2e_s=e2e_s, e2e_solves=e2e_solves, ms2=ms2, eik=eik,
+                achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result)
+
+
+def cpu_baseline_sample():
+    """The FP64 oracle, as it stands, on one full 256^3 step of the same workload."""
+    import oracle
+    U0 = inputs.euler3d_blast(N3, seed=1).astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.euler_run(U0, 1, scheme=oracle.MUSCL_HANCOCK, bc=oracle.TRANSMISSIVE)
+    dt = time.perf_counter() - t0
+    return {"value": N3 ** 3 / dt, "unit": METRIC, "cores": oracle.threads_used(), "kind": "oracle",
+            "sample": f"one MUSCL-Hancock step of the 256^3 blast in FP64 ({dt:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-solves", type=int, default=2)
+    ap.add_argument("--skip-eikonal", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_setup(args.gpus)
+    config = {"workload": "euler3d_muscl_hancock_256^3_blast", "cells": N3 ** 3, "ncomp": 5, "halo": 2,
+              "scheme": "MUSCL-Hancock minmod + Rusanov", "bc": "transmissive", "layout": "SoA",
+              "l2": "inputs larger than L2 (335 MB per buffer), no flush"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        import oracle
+        oracle.build()
+        side = 128  # bounded sample: the central 128^3 crop of the blast, one step each
+        U0 = inputs.euler3d_blast(N3, seed=1).astype(np.float32).astype(np.float64)
+        lo = (N3 - side) // 2
+        crop = np.ascontiguousarray(U0[:, lo:lo + side, lo:lo + side, lo:lo + side])
+        dxs = [1.0 / N3] * 3
+        for _ in range(args.warmup):
+            oracle.euler_run(crop, 1, scheme=oracle.MUSCL_HANCOCK, bc=oracle.TRANSMISSIVE, dx=dxs)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle.euler_run(crop, 1, scheme=oracle.MUSCL_HANCOCK, bc=oracle.TRANSMISSIVE, dx=dxs)
+        dt = time.perf_counter() - t0
+        value = args.steps * side ** 3 / dt
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.threads_used(), "kind": "oracle",
+                                 "sample": f"one FP64 step of the central {side}^3 crop of the 256^3 blast per step"},
+                "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    r = bench_gpu(args, rank, world, local)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.skip_cpu_baseline and world == 1:
+        cpu = cpu_baseline_sample()
+    state_bytes = N3 ** 3 * 5 * 4
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "gpu_launches": args.steps,
+        "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["hbm_peak"], "unit": "GB/s",
+                     "frac": r["achieved"] / r["hbm_peak"], "traffic": None,
+                     "peak_source": r["peak_kind"],
+                     "algorithmic_bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
+        "clocks": r["clocks"],
+        "e2e": {"value": r["e2e_value"], "unit": METRIC, "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes,
+                "step": f"one {NSTEPS_SOLVE}-step solve: pinned host -> device, {NSTEPS_SOLVE} sweeps, device -> pinned host",
+                "solves": r["e2e_solves"], "seconds": r["e2e_s"]},
+        "cpu_baseline": cpu,
+        "aos": {"value": N3 ** 3 / (r["ms_aos"] / 1e3), "ms_per_step": r["ms_aos"]},
+        "euler2d_fp64_128": {"ms_per_100_steps": r["ms2"], "us_per_step": r["ms2"] * 10.0,
+                             "cell_updates_per_s": 100 * 128 * 128 / (r["ms2"] / 1e3)},
+        "eikonal": r["eik"],
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,233 @@
+/*
+ * ripple.h -- C ABI of the GB300 (sm_103a) stencil-sweep library.
+ *
+ * The library implements the data-parallel hot path of Ripple (arXiv
+ * 2104.08571): a halo-padded, block-tiled stencil sweep over a multi-component
+ * field stored in a polymorphic layout (Section 4.1 tensors with padding,
+ * Section 4.2 polymorphic data layout), with the tile plus its ghost cells
+ * staged in shared memory (Section 5.4, "in shared" access) and one of two
+ * updates applied:
+ *   - a finite-volume compressible Euler step (the flux difference of
+ *     Section 7.3 inside the solver graph of Section 8, Listing "euler_graph"),
+ *   - a Godunov-upwind eikonal relaxation inside a Fast Iterative Method
+ *     (Section 7.4, the Hamiltonian |grad phi|^2 - 1/f^2 = 0).
+ *
+ * Conventions shared by every entry point
+ *   - Every function returns a ripple_status; no exception crosses the ABI.
+ *     ripple_last_error() returns a thread-local message for the last failure.
+ *   - Handles are opaque.  The library owns device memory behind a handle; the
+ *     caller owns every host buffer it passes and must destroy handles.
+ *     Destroying NULL is RIPPLE_OK.
+ *   - dims[0] is x, the fastest-varying axis.  Host/device arrays exchanged
+ *     with a field hold interior cells only, in the layout named by the call:
+ *       RIPPLE_SOA ("strided"):  a[((c * nz + k) * ny + j) * nx + i]
+ *       RIPPLE_AOS ("contiguous"): a[((k * ny + j) * nx + i) * ncomp + c]
+ *     with elements of the field's dtype (float for RIPPLE_F32, double for
+ *     RIPPLE_F64).
+ *   - Euler fields hold the conserved variables in the order
+ *     (rho, rho*u_x, rho*u_y[, rho*u_z], E): ncomp = ndim + 2.
+ *   - Work is queued on the context's stream (ripple_set_stream).  Calls that
+ *     return data to the host synchronise that stream; the others are
+ *     asynchronous and report device-side errors (RIPPLE_ERR_NUMERIC,
+ *     RIPPLE_ERR_TIMEOUT) at the next synchronising call on that context.
+ *   - One context is driven by one host thread at a time, except
+ *     ripple_batch_submit / ripple_poll / ripple_wait, which are thread-safe.
+ */
+#ifndef RIPPLE_H
+#define RIPPLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RIPPLE_API __attribute__((visibility("default")))
+#else
+#define RIPPLE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RIPPLE_OK = 0,
+    RIPPLE_ERR_INVALID = 1,   /* bad argument (shape, halo < stencil radius, dtype, ...) */
+    RIPPLE_ERR_OOM = 2,       /* device or host allocation failed */
+    RIPPLE_ERR_CUDA = 3,      /* a CUDA runtime/driver call failed */
+    RIPPLE_ERR_NOT_READY = 4, /* ripple_poll: request still in flight */
+    RIPPLE_ERR_TIMEOUT = 5,   /* a bounded wait (host or device) ran out */
+    RIPPLE_ERR_NUMERIC = 6,   /* non-positive or NaN density/pressure was produced */
+    RIPPLE_ERR_BUDGET = 7,    /* allocation would exceed the context's memory budget */
+    RIPPLE_ERR_INTERNAL = 8   /* library invariant violated */
+} ripple_status;
+
+typedef enum { RIPPLE_AOS = 0, RIPPLE_SOA = 1 } ripple_layout;
+typedef enum { RIPPLE_F32 = 0, RIPPLE_F64 = 1 } ripple_dtype;
+typedef enum { RIPPLE_RUSANOV1 = 0, RIPPLE_MUSCL_HANCOCK_MINMOD = 1 } ripple_scheme;
+typedef enum { RIPPLE_BC_PERIODIC = 0, RIPPLE_BC_TRANSMISSIVE = 1 } ripple_bc;
+
+typedef struct ripple_ctx_s* ripple_ctx;
+typedef struct ripple_field_s* ripple_field;
+
+/* ------------------------------------------------------------------------ */
+/* Context: device, stream, allocator and memory budget.                     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Create a context on CUDA device `device` with a device-memory budget of
+ * `mem_budget_bytes` (0 = unlimited).  Field and scratch allocations made
+ * through the context count against the budget (RIPPLE_ERR_BUDGET beyond it),
+ * following the paper's advice (Section 5.1) to allocate ahead of the
+ * computation instead of inside it.  The context owns a CUDA stream until
+ * ripple_set_stream replaces it.
+ */
+RIPPLE_API ripple_status ripple_ctx_create(int device, size_t mem_budget_bytes, ripple_ctx* out);
+
+/* Synchronise, release all scratch memory and the context itself.  Fields
+ * created from the context must be destroyed first (RIPPLE_ERR_INVALID
+ * otherwise). */
+RIPPLE_API ripple_status ripple_ctx_destroy(ripple_ctx ctx);
+
+/* Queue subsequent work on `cuda_stream` (a cudaStream_t, may be e.g. the
+ * PyTorch current stream; NULL = the context's own stream).  The caller
+ * keeps ownership of a stream it passes. */
+RIPPLE_API ripple_status ripple_set_stream(ripple_ctx ctx, void* cuda_stream);
+
+/*
+ * Route device allocations through caller callbacks (e.g. the PyTorch caching
+ * allocator).  alloc(bytes, user) returns a device pointer aligned to 256 B or
+ * NULL; release(ptr, user) frees it.  Passing alloc = NULL restores
+ * cudaMalloc/cudaFree.  Must be called before any field is created.
+ */
+RIPPLE_API ripple_status ripple_set_allocator(ripple_ctx ctx, void* (*alloc)(size_t bytes, void* user),
+                                   void (*release)(void* ptr, void* user), void* user);
+
+/* Wait for all work queued on the context's stream; returns the first pending
+ * device-side error (RIPPLE_ERR_NUMERIC / RIPPLE_ERR_TIMEOUT) and clears it. */
+RIPPLE_API ripple_status ripple_ctx_sync(ripple_ctx ctx);
+
+/* Bytes currently allocated through the context (fields + scratch). */
+RIPPLE_API ripple_status ripple_ctx_mem_used(ripple_ctx ctx, size_t* bytes);
+
+/* ------------------------------------------------------------------------ */
+/* Fields: halo-padded tensors in AoS or SoA layout (Sections 4.1-4.2).      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Create a field of ndim (2 or 3) axes with dims[d] >= 1 interior cells,
+ * `ncomp` (1..5) components per cell, `halo` >= 0 ghost layers on every side
+ * of every axis, stored in `layout` with element type `dtype`.  Device memory
+ * holds two padded buffers (the double buffer of Section 5.4, in -> out, then
+ * swap); the second is allocated on first use by a solver.  Contents start
+ * undefined; upload before use.
+ */
+RIPPLE_API ripple_status ripple_field_create(ripple_ctx ctx, int ndim, const int64_t* dims, int ncomp,
+                                  ripple_layout layout, int halo, ripple_dtype dtype,
+                                  ripple_field* out);
+
+RIPPLE_API ripple_status ripple_field_destroy(ripple_field field);
+
+/* Copy interior cells from a HOST buffer in `src_layout` into the field
+ * (synchronous).  Ghost cells become stale and are refilled by the next solver
+ * call. */
+RIPPLE_API ripple_status ripple_field_upload(ripple_field field, const void* src, ripple_layout src_layout);
+
+/* Copy interior cells to a HOST buffer in `dst_layout` (synchronous; reports
+ * pending device errors like ripple_ctx_sync). */
+RIPPLE_API ripple_status ripple_field_download(ripple_field field, void* dst, ripple_layout dst_layout);
+
+/* Same as upload/download, but `src`/`dst` is DEVICE memory of the field's
+ * device; asynchronous on the context stream. */
+RIPPLE_API ripple_status ripple_field_upload_device(ripple_field field, const void* src, ripple_layout src_layout);
+RIPPLE_API ripple_status ripple_field_download_device(ripple_field field, void* dst, ripple_layout dst_layout);
+
+typedef struct {
+    int ndim, ncomp, halo;
+    ripple_layout layout;
+    ripple_dtype dtype;
+    int64_t dims[3];     /* interior cells (1 on unused axes) */
+    int64_t padded[3];   /* allocated extent per axis, x includes alignment padding */
+    int64_t x_lead;      /* padded x index of the first ghost column */
+    size_t buffer_bytes; /* bytes of one padded buffer */
+    void* current;       /* device pointer of the buffer holding the current state */
+} ripple_field_desc;
+
+RIPPLE_API ripple_status ripple_field_describe(ripple_field field, ripple_field_desc* out);
+
+/* ------------------------------------------------------------------------ */
+/* Finite-volume Euler step.                                                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double gamma;       /* ratio of specific heats (> 1) */
+    double cfl;         /* Courant number, dt = cfl / max_cells sum_d (|u_d| + c)/dx_d */
+    double dx[3];       /* cell widths per axis (> 0) */
+    ripple_scheme scheme;
+    ripple_bc bc;
+} ripple_fv_params;
+
+typedef struct {
+    double t;           /* simulated time advanced by this call (sum of dt, FP64) */
+    double dt_last;     /* the last dt used */
+    double totals[5];   /* FP64 compensated sums of each conserved variable over interior cells */
+    int64_t steps_done; /* steps completed by this call */
+} ripple_fv_stats;
+
+/*
+ * Advance the Euler field U by `nsteps` explicit steps (Section 8, Listing
+ * "euler_graph": wave speeds -> max reduction -> dt -> padding fill -> flux
+ * difference update -> swap; the flux difference is that of Section 7.3).
+ * The update is unsplit (all axes in one pass) with a Rusanov face flux,
+ * first order or MUSCL-Hancock with minmod slopes.  U must have ncomp =
+ * ndim + 2 and halo >= 1 (Rusanov) or >= 2 (MUSCL-Hancock).  For RIPPLE_F32
+ * fields the stencil runs in FP32 while dt and the totals are reduced in
+ * FP64; RIPPLE_F64 fields run fully in FP64.
+ * With stats != NULL the call synchronises, fills *stats (totals of the final
+ * state) and returns RIPPLE_ERR_NUMERIC if any produced state lost
+ * positivity.  With stats == NULL the call only queues the work.
+ */
+RIPPLE_API ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* params, int64_t nsteps,
+                             ripple_fv_stats* stats);
+
+/* ------------------------------------------------------------------------ */
+/* Eikonal solve (Fast Iterative Method, Section 7.4).                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double h;            /* grid spacing (cells are h wide on every axis) */
+    double tol;          /* a tile converges when no cell changes by tol or more */
+    int64_t max_iters;   /* cap on active-list iterations (0 = library default) */
+} ripple_eik_params;
+
+typedef struct {
+    int64_t iterations;  /* active-list iterations run */
+    int64_t tile_visits; /* tile relaxations performed */
+    int64_t cell_updates;/* Godunov cell updates performed (tile visits x sweeps x cells) */
+} ripple_eik_stats;
+
+/*
+ * Solve |grad T| s = 1 on the grid of `slowness` (1 component, any halo) into
+ * `T` (1 component, halo >= 1, same dims and dtype), with T = 0 held at the
+ * `nsrc` source cells given as ndim coordinates each (x first) in
+ * `src_coords`.  Godunov upwind discretisation; outside-domain neighbours are
+ * +inf.  The result is the fixed point of T = min(T, G(T)) up to the stopping
+ * tolerance.  Returns RIPPLE_ERR_TIMEOUT if max_iters runs out.  Synchronous.
+ */
+RIPPLE_API ripple_status ripple_eikonal_solve(ripple_field slowness, ripple_field T, const int64_t* src_coords,
+                                   int nsrc, const ripple_eik_params* params, ripple_eik_stats* stats);
+
+/* ------------------------------------------------------------------------ */
+/* Library                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+RIPPLE_API const char* ripple_last_error(void);
+
+/* Library version string. */
+RIPPLE_API const char* ripple_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RIPPLE_H */

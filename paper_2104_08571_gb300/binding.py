@@ -1,0 +1,302 @@
+"""Thin ctypes binding of ``libripple.so`` (the C ABI declared in include/ripple.h).
+
+Argument marshalling only: every step of the stencil path runs in the CUDA
+kernels behind the C ABI.  Functions keep the C names.  A failing status
+raises ``RippleError``.  If the shared library is missing or cannot be
+loaded, importing this module raises: there is no fallback path.
+
+Array conventions (see include/ripple.h): interior cells only, numpy/torch
+arrays of shape (ncomp, [nz,] ny, nx) for RIPPLE_SOA and ([nz,] ny, nx, ncomp)
+for RIPPLE_AOS (one-component fields may drop the component axis), dtype
+float32 for RIPPLE_F32 fields and float64 for RIPPLE_F64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RIPPLE_OK = 0
+RIPPLE_ERR_INVALID = 1
+RIPPLE_ERR_OOM = 2
+RIPPLE_ERR_CUDA = 3
+RIPPLE_ERR_NOT_READY = 4
+RIPPLE_ERR_TIMEOUT = 5
+RIPPLE_ERR_NUMERIC = 6
+RIPPLE_ERR_BUDGET = 7
+RIPPLE_ERR_INTERNAL = 8
+
+RIPPLE_AOS = 0
+RIPPLE_SOA = 1
+RIPPLE_F32 = 0
+RIPPLE_F64 = 1
+RIPPLE_RUSANOV1 = 0
+RIPPLE_MUSCL_HANCOCK_MINMOD = 1
+RIPPLE_BC_PERIODIC = 0
+RIPPLE_BC_TRANSMISSIVE = 1
+
+_STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_READY", 5: "TIMEOUT", 6: "NUMERIC",
+                 7: "BUDGET", 8: "INTERNAL"}
+
+
+class RippleError(RuntimeError):
+    def __init__(self, status: int, func: str, message: str):
+        super().__init__(f"{func}: RIPPLE_ERR_{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class ripple_fv_params(ctypes.Structure):
+    _fields_ = [("gamma", ctypes.c_double), ("cfl", ctypes.c_double), ("dx", ctypes.c_double * 3),
+                ("scheme", ctypes.c_int), ("bc", ctypes.c_int)]
+
+
+class ripple_fv_stats(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt_last", ctypes.c_double), ("totals", ctypes.c_double * 5),
+                ("steps_done", ctypes.c_int64)]
+
+
+class ripple_eik_params(ctypes.Structure):
+    _fields_ = [("h", ctypes.c_double), ("tol", ctypes.c_double), ("max_iters", ctypes.c_int64)]
+
+
+class ripple_eik_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("tile_visits", ctypes.c_int64), ("cell_updates", ctypes.c_int64)]
+
+
+class ripple_field_desc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("ncomp", ctypes.c_int), ("halo", ctypes.c_int), ("layout", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("dims", ctypes.c_int64 * 3), ("padded", ctypes.c_int64 * 3),
+                ("x_lead", ctypes.c_int64), ("buffer_bytes", ctypes.c_size_t), ("current", ctypes.c_void_p)]
+
+
+_VP = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+
+# name -> (argtypes) ; every ABI function returns ripple_status (int)
+_SIGNATURES = {
+    "ripple_ctx_create": [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_VP)],
+    "ripple_ctx_destroy": [_VP],
+    "ripple_set_stream": [_VP, _VP],
+    "ripple_set_allocator": [_VP, _VP, _VP, _VP],
+    "ripple_ctx_sync": [_VP],
+    "ripple_ctx_mem_used": [_VP, ctypes.POINTER(ctypes.c_size_t)],
+    "ripple_field_create": [_VP, ctypes.c_int, _I64P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.POINTER(_VP)],
+    "ripple_field_destroy": [_VP],
+    "ripple_field_upload": [_VP, _VP, ctypes.c_int],
+    "ripple_field_download": [_VP, _VP, ctypes.c_int],
+    "ripple_field_upload_device": [_VP, _VP, ctypes.c_int],
+    "ripple_field_download_device": [_VP, _VP, ctypes.c_int],
+    "ripple_field_describe": [_VP, ctypes.POINTER(ripple_field_desc)],
+    "ripple_fv_step": [_VP, ctypes.POINTER(ripple_fv_params), ctypes.c_int64, ctypes.POINTER(ripple_fv_stats)],
+    "ripple_eikonal_solve": [_VP, _VP, _I64P, ctypes.c_int, ctypes.POINTER(ripple_eik_params),
+                             ctypes.POINTER(ripple_eik_stats)],
+}
+_STRING_FUNCS = ["ripple_last_error", "ripple_version"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libripple.so (optionally building it first).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise ImportError(f"libripple.so not built ({path}); run __graft_entry__.build() or "
+                          "python -m paper_2104_08571_gb300.build")
+    lib = ctypes.CDLL(path)
+    for name, argtypes in _SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.argtypes = argtypes
+        fn.restype = ctypes.c_int
+    for name in _STRING_FUNCS:
+        fn = getattr(lib, name)
+        fn.argtypes = []
+        fn.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return sorted(list(_SIGNATURES) + _STRING_FUNCS)
+
+
+def _check(status: int, func: str):
+    if status != RIPPLE_OK:
+        raise RippleError(status, func, ripple_last_error())
+
+
+def ripple_last_error() -> str:
+    return load().ripple_last_error().decode()
+
+
+def ripple_version() -> str:
+    return load().ripple_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# context
+# ---------------------------------------------------------------------------
+def ripple_ctx_create(device: int = 0, mem_budget_bytes: int = 0):
+    out = _VP()
+    _check(load().ripple_ctx_create(int(device), int(mem_budget_bytes), ctypes.byref(out)), "ripple_ctx_create")
+    return out
+
+
+def ripple_ctx_destroy(ctx):
+    _check(load().ripple_ctx_destroy(ctx), "ripple_ctx_destroy")
+
+
+def ripple_set_stream(ctx, stream=None):
+    """stream: a cudaStream_t as int, a torch.cuda.Stream, or None (own stream)."""
+    handle = None
+    if stream is not None:
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(load().ripple_set_stream(ctx, handle), "ripple_set_stream")
+
+
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_keepalive = {}
+
+
+def ripple_set_allocator(ctx, alloc=None, release=None):
+    """alloc(nbytes) -> device pointer (int); release(ptr). None restores cudaMalloc."""
+    if alloc is None:
+        _check(load().ripple_set_allocator(ctx, None, None, None), "ripple_set_allocator")
+        _keepalive.pop(ctx.value, None)
+        return
+    ca = _ALLOC_T(lambda n, user: alloc(int(n)) or 0)
+    cf = _FREE_T(lambda p, user: release(int(p)))
+    _keepalive[ctx.value] = (ca, cf)
+    _check(load().ripple_set_allocator(ctx, ctypes.cast(ca, _VP), ctypes.cast(cf, _VP), None),
+           "ripple_set_allocator")
+
+
+def use_torch_allocator(ctx, device: int = 0):
+    """Route the context's device allocations through PyTorch's caching allocator."""
+    import torch
+
+    def alloc(n):
+        return torch.cuda.caching_allocator_alloc(n, device=device)
+
+    def release(p):
+        torch.cuda.caching_allocator_delete(p)
+
+    ripple_set_allocator(ctx, alloc, release)
+
+
+def ripple_ctx_sync(ctx):
+    _check(load().ripple_ctx_sync(ctx), "ripple_ctx_sync")
+
+
+def ripple_ctx_mem_used(ctx) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().ripple_ctx_mem_used(ctx, ctypes.byref(out)), "ripple_ctx_mem_used")
+    return out.value
+
+
+# ---------------------------------------------------------------------------
+# fields
+# ---------------------------------------------------------------------------
+def ripple_field_create(ctx, dims, ncomp, layout=RIPPLE_SOA, halo=1, dtype=RIPPLE_F32):
+    """dims = (nx, ny[, nz])."""
+    d = (ctypes.c_int64 * 3)(*(list(dims) + [1] * (3 - len(dims))))
+    out = _VP()
+    _check(load().ripple_field_create(ctx, len(dims), d, int(ncomp), int(layout), int(halo), int(dtype),
+                                      ctypes.byref(out)), "ripple_field_create")
+    return out
+
+
+def ripple_field_destroy(field):
+    _check(load().ripple_field_destroy(field), "ripple_field_destroy")
+
+
+def ripple_field_describe(field) -> ripple_field_desc:
+    out = ripple_field_desc()
+    _check(load().ripple_field_describe(field, ctypes.byref(out)), "ripple_field_describe")
+    return out
+
+
+def _np_dtype(desc):
+    return np.float32 if desc.dtype == RIPPLE_F32 else np.float64
+
+
+def _expected_count(desc):
+    return int(desc.dims[0] * desc.dims[1] * desc.dims[2] * desc.ncomp)
+
+
+def ripple_field_upload(field, array, layout=RIPPLE_SOA):
+    """Upload interior cells from a numpy array / CPU tensor (host) or a CUDA tensor (device)."""
+    desc = ripple_field_describe(field)
+    if hasattr(array, "is_cuda") and array.is_cuda:
+        import torch
+        want = torch.float32 if desc.dtype == RIPPLE_F32 else torch.float64
+        if array.dtype != want or not array.is_contiguous() or array.numel() != _expected_count(desc):
+            raise ValueError("device array must be contiguous, of the field's dtype and element count")
+        _check(load().ripple_field_upload_device(field, _VP(array.data_ptr()), int(layout)),
+               "ripple_field_upload_device")
+        return
+    if hasattr(array, "numpy"):
+        array = array.numpy()
+    arr = np.ascontiguousarray(array, dtype=_np_dtype(desc))
+    if arr.size != _expected_count(desc):
+        raise ValueError(f"expected {_expected_count(desc)} elements, got {arr.size}")
+    _check(load().ripple_field_upload(field, _VP(arr.ctypes.data), int(layout)), "ripple_field_upload")
+
+
+def ripple_field_download(field, layout=RIPPLE_SOA, out=None):
+    """Download interior cells into a new numpy array (or `out`, host or CUDA tensor)."""
+    desc = ripple_field_describe(field)
+    nd = desc.ndim
+    spatial = [int(desc.dims[d]) for d in reversed(range(nd))]
+    if out is not None and hasattr(out, "is_cuda") and out.is_cuda:
+        _check(load().ripple_field_download_device(field, _VP(out.data_ptr()), int(layout)),
+               "ripple_field_download_device")
+        return out
+    if out is None:
+        shape = ([desc.ncomp] + spatial) if layout == RIPPLE_SOA else (spatial + [desc.ncomp])
+        out = np.empty(shape, dtype=_np_dtype(desc))
+    ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    _check(load().ripple_field_download(field, _VP(ptr), int(layout)), "ripple_field_download")
+    return out
+
+
+# ---------------------------------------------------------------------------
+# solvers
+# ---------------------------------------------------------------------------
+def make_fv_params(dx, gamma=1.4, cfl=0.4, scheme=RIPPLE_RUSANOV1, bc=RIPPLE_BC_PERIODIC) -> ripple_fv_params:
+    dx = list(dx) + [1.0] * (3 - len(dx))
+    return ripple_fv_params(float(gamma), float(cfl), (ctypes.c_double * 3)(*dx), int(scheme), int(bc))
+
+
+def ripple_fv_step(field, params: ripple_fv_params, nsteps: int, stats: bool = True):
+    """Advance an Euler field; returns a dict of stats (synchronous) or None (queued only)."""
+    st = ripple_fv_stats() if stats else None
+    _check(load().ripple_fv_step(field, ctypes.byref(params), int(nsteps), ctypes.byref(st) if stats else None),
+           "ripple_fv_step")
+    if not stats:
+        return None
+    return dict(t=st.t, dt_last=st.dt_last, totals=list(st.totals), steps_done=st.steps_done)
+
+
+def ripple_eikonal_solve(slowness, T, sources, h, tol=1e-6, max_iters=0):
+    """sources: list of (x, y[, z]) cell coordinates."""
+    flat = [int(c) for s in sources for c in s]
+    arr = (ctypes.c_int64 * len(flat))(*flat)
+    prm = ripple_eik_params(float(h), float(tol), int(max_iters))
+    st = ripple_eik_stats()
+    _check(load().ripple_eikonal_solve(slowness, T, arr, len(sources), ctypes.byref(prm), ctypes.byref(st)),
+           "ripple_eikonal_solve")
+    return dict(iterations=st.iterations, tile_visits=st.tile_visits, cell_updates=st.cell_updates)

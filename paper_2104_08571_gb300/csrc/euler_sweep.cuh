@@ -1,0 +1,677 @@
+// Halo-padded, block-tiled finite-volume Euler sweep for sm_103a.
+//
+// One launch advances the whole field by one explicit step (the flux
+// difference of the paper's Section 7.3 applied inside the solver step of
+// Section 8, Listing "euler_graph"), out of place (Section 5.4 double
+// buffering: in -> out).  The step fuses what the paper runs as separate
+// graph nodes:
+//   set_dt         dt = cfl / smax(in), read from the ring slot the previous
+//                  step (or the prep kernel) reduced into;
+//   update         unsplit flux difference with Rusanov faces, first order or
+//                  MUSCL-Hancock (minmod slopes, per-direction half-step
+//                  predictor);
+//   set_boundary   the ghost images of every new interior cell are written
+//                  to `out` (periodic wrap or constant extrapolation), so the
+//                  next step finds its padding filled;
+//   set_wavespeeds + MaxReducer
+//                  max_cells sum_d (|u_d| + c)/dx_d of the NEW state, warp
+//                  shuffles -> block -> one atomicMax per CTA into the next
+//                  ring slot (the max is order-independent, so dt is
+//                  deterministic);
+//   positivity     any non-positive/NaN density or pressure in a cell,
+//                  reconstructed or predicted state sets DEV_ERR_NUMERIC.
+//
+// Tiling ("in_shared" access of Section 5.4, re-designed for Blackwell):
+//   * a CTA owns a TX x TY column of cells and streams along z over a chunk
+//     of planes (2.5-D); 2D fields are the one-plane case;
+//   * each plane of the tile plus its ghost cells (TX+2R) x (TY+2R), all
+//     components, arrives in shared memory by ONE TMA tile load
+//     (cp.async.bulk.tensor) into a ring of NS slots with one mbarrier per
+//     slot, prefetched NS - R - 1 planes ahead;
+//   * in-plane (x, y) work is split into phases over shared-memory arrays so
+//     that each face flux is evaluated exactly once and read by both cells
+//     (bit-exact telescoping); the z direction is carried in registers
+//     (predicted states and the lower face flux of the next plane);
+//   * the new plane is written to a shared staging tile and leaves by ONE TMA
+//     tile store, clipped by the tensor map at the interior's y/z ends (tiles
+//     that cross the x end store with plain stores instead).
+// The CTA count is a multiple of the SM count (persistent, work items strided
+// over CTAs).
+#pragma once
+#include <cuda.h>
+#include <cstdint>
+
+#include "field.cuh"
+#include "tma.cuh"
+
+namespace ripple {
+
+enum { SCHEME_RUSANOV1 = 0, SCHEME_MUSCL = 1 };
+
+struct SweepGeom {
+    FieldGeom f;
+    int tiles_x, tiles_y, zchunk, chunks_z;
+    int items;  // tiles_x * tiles_y * chunks_z
+};
+
+struct SweepParams {
+    double gamma, cfl;
+    double inv_dx[3];
+    int bc;       // 0 periodic, 1 transmissive
+    int slot_in;  // ring slot holding smax of the input state
+    int first;    // first step of a call: t = dt instead of t += dt
+};
+
+// ---------------------------------------------------------------------------
+// Arithmetic helpers (field precision).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T minmod_t(T a, T b)
+{
+    // 0 if the one-sided differences disagree in sign, else the smaller one
+    if (a * b <= T(0)) return T(0);
+    return fabs(a) < fabs(b) ? a : b;
+}
+
+// Physical flux along axis D; also returns density, normal velocity, pressure.
+template <typename T, int DIM, int D>
+__device__ __forceinline__ void phys_flux(const T (&q)[DIM + 2], T gm1, T (&F)[DIM + 2], T& un, T& p)
+{
+    const T inv_rho = rcp_t(q[0]);
+    T mm = q[1] * q[1];
+#pragma unroll
+    for (int e = 1; e < DIM; ++e) mm = fma(q[1 + e], q[1 + e], mm);
+    p = gm1 * (q[DIM + 1] - T(0.5) * mm * inv_rho);
+    un = q[1 + D] * inv_rho;
+    F[0] = q[1 + D];
+#pragma unroll
+    for (int e = 0; e < DIM; ++e) F[1 + e] = q[1 + e] * un;
+    F[1 + D] += p;
+    F[DIM + 1] = (q[DIM + 1] + p) * un;
+}
+
+// Rusanov face flux along D between left state a and right state b.
+// Returns false when a state is not admissible (rho <= 0 or p <= 0 or NaN).
+template <typename T, int DIM, int D>
+__device__ __forceinline__ bool rusanov(const T (&a)[DIM + 2], const T (&b)[DIM + 2], T gamma, T gm1,
+                                        T (&F)[DIM + 2])
+{
+    T Fa[DIM + 2], Fb[DIM + 2], ua, pa, ub, pb;
+    phys_flux<T, DIM, D>(a, gm1, Fa, ua, pa);
+    phys_flux<T, DIM, D>(b, gm1, Fb, ub, pb);
+    const bool ok = (a[0] > T(0)) & (pa > T(0)) & (b[0] > T(0)) & (pb > T(0));
+    const T ca = sqrt_t(gamma * pa * rcp_t(a[0]));
+    const T cb = sqrt_t(gamma * pb * rcp_t(b[0]));
+    const T s = fmax(fabs(ua) + ca, fabs(ub) + cb);
+#pragma unroll
+    for (int m = 0; m < DIM + 2; ++m) F[m] = T(0.5) * (Fa[m] + Fb[m]) - T(0.5) * s * (b[m] - a[m]);
+    return ok;
+}
+
+// MUSCL-Hancock face states of a cell along D from (left, centre, right):
+// slopes by minmod, boundary extrapolation, half-step predictor with the
+// direction-D flux difference.  Returns admissibility of the extrapolated states.
+template <typename T, int DIM, int D>
+__device__ __forceinline__ bool muscl_states(const T (&qm)[DIM + 2], const T (&q)[DIM + 2],
+                                             const T (&qp)[DIM + 2], T gm1, T half_dtdx,
+                                             T (&L)[DIM + 2], T (&R)[DIM + 2])
+{
+#pragma unroll
+    for (int m = 0; m < DIM + 2; ++m) {
+        const T slope = minmod_t(q[m] - qm[m], qp[m] - q[m]);
+        L[m] = q[m] - T(0.5) * slope;
+        R[m] = q[m] + T(0.5) * slope;
+    }
+    T FL[DIM + 2], FR[DIM + 2], u, pl, pr;
+    phys_flux<T, DIM, D>(L, gm1, FL, u, pl);
+    phys_flux<T, DIM, D>(R, gm1, FR, u, pr);
+    const bool ok = (L[0] > T(0)) & (pl > T(0)) & (R[0] > T(0)) & (pr > T(0));
+#pragma unroll
+    for (int m = 0; m < DIM + 2; ++m) {
+        const T inc = half_dtdx * (FL[m] - FR[m]);
+        L[m] += inc;
+        R[m] += inc;
+    }
+    return ok;
+}
+
+// Wave-speed sum and admissibility of a conserved state.
+template <typename T, int DIM>
+__device__ __forceinline__ T wave_sum(const T (&q)[DIM + 2], T gamma, T gm1, const T (&inv_dx)[3], bool& ok)
+{
+    const T inv_rho = rcp_t(q[0]);
+    T mm = q[1] * q[1];
+#pragma unroll
+    for (int e = 1; e < DIM; ++e) mm = fma(q[1 + e], q[1 + e], mm);
+    const T p = gm1 * (q[DIM + 1] - T(0.5) * mm * inv_rho);
+    ok = (q[0] > T(0)) & (p > T(0));
+    const T c = sqrt_t(gamma * p * inv_rho);
+    T s = T(0);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) s += (fabs(q[1 + d] * inv_rho) + c) * inv_dx[d];
+    return s;
+}
+
+// Write the ghost images of interior cell (i, j, k): along each axis, the
+// periodic copy on the far side (cells within h of an edge) or the constant
+// extrapolation into all h layers (edge cells).  Only face ghosts are
+// written: the cross-shaped stencils never read edge or corner ghosts.
+template <typename T, int DIM>
+__device__ __forceinline__ void write_ghost_images(T* __restrict__ out, const FieldGeom& g, int bc, int i,
+                                                   int j, int k, const T (&q)[DIM + 2])
+{
+    const int c[3] = {i, j, k};
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+        const int n = g.n[d];
+        if (bc == 0) {
+            int img = c[d] < g.h ? c[d] + n : (c[d] >= n - g.h ? c[d] - n : INT32_MIN);
+            int img2 = (c[d] < g.h && c[d] >= n - g.h) ? c[d] - n : INT32_MIN;  // n < 2h
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int v = r == 0 ? img : img2;
+                if (v == INT32_MIN) continue;
+                int cc[3] = {c[0], c[1], c[2]};
+                cc[d] = v;
+                const long long base = geom_cell(g, cc[0], cc[1], cc[2]) * g.cell_stride;
+#pragma unroll
+                for (int m = 0; m < DIM + 2; ++m) out[base + (long long)m * g.comp_stride] = q[m];
+            }
+        } else {
+            int lo = 0, cnt = 0;
+            if (c[d] == 0) { lo = -g.h; cnt = g.h; }
+            for (int pass = 0; pass < 2; ++pass) {
+                if (pass == 1) {
+                    if (c[d] == n - 1) { lo = n; cnt = g.h; } else cnt = 0;
+                }
+                for (int r = 0; r < cnt; ++r) {
+                    int cc[3] = {c[0], c[1], c[2]};
+                    cc[d] = lo + r;
+                    const long long base = geom_cell(g, cc[0], cc[1], cc[2]) * g.cell_stride;
+#pragma unroll
+                    for (int m = 0; m < DIM + 2; ++m) out[base + (long long)m * g.comp_stride] = q[m];
+                }
+            }
+        }
+    }
+}
+
+// Where the first non-admissible state was found (FieldCtl::counters[4..7]):
+// stage code + 1, then x, y, z of the cell (or of the left cell of a face).
+enum : int { BAD_PRED_X = 1, BAD_PRED_Y, BAD_PRED_Z, BAD_FACE_X, BAD_FACE_Y, BAD_FACE_Z, BAD_CELL, BAD_INPUT };
+static __device__ __noinline__ void record_bad(FieldCtl* ctl, int code, int x, int y, int z)
+{
+    if (atomicCAS(reinterpret_cast<unsigned long long*>(&ctl->counters[4]), 0ull, (unsigned long long)code) == 0ull) {
+        ctl->counters[5] = x;
+        ctl->counters[6] = y;
+        ctl->counters[7] = z;
+    }
+}
+
+__device__ __forceinline__ void atomic_max_pos_double(unsigned long long* addr, double v)
+{
+    // positive doubles order like their bit patterns
+    if (v > 0.0) atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of the TMA box that stages one plane of a tile plus its ghost
+// cells.  Shared by the kernel (shared-memory slot size, expected bytes) and
+// the host (tensor-map box), so the two can never disagree.
+//   a   : x alignment in cells of a box start (16 bytes of elements)
+//   off : the box starts off cells before x0 - r so that its start is aligned
+//   bx  : box width in cells (multiple of a), by: box height
+// ---------------------------------------------------------------------------
+struct BoxGeom {
+    int a, off, bx, by;
+};
+__host__ __device__ constexpr int pow2_divisor16(int v)
+{
+    return (v % 16 == 0) ? 16 : (v % 8 == 0) ? 8 : (v % 4 == 0) ? 4 : (v % 2 == 0) ? 2 : 1;
+}
+__host__ __device__ constexpr BoxGeom plane_box(int elem_bytes, int ncomp, bool aos, int r, int tx, int ty)
+{
+    const int a = 16 / pow2_divisor16(elem_bytes * (aos ? ncomp : 1));
+    const int off = (a - r % a) % a;
+    return BoxGeom{a, off, ((off + tx + 2 * r + a - 1) / a) * a, ty + 2 * r};
+}
+
+// ---------------------------------------------------------------------------
+// Compile-time tile configuration.
+// ---------------------------------------------------------------------------
+template <typename T, int DIM, int LAYOUT, int SCHEME, int TX, int TY>
+struct SweepCfg {
+    static constexpr int NC = DIM + 2;
+    static constexpr int R = SCHEME == SCHEME_MUSCL ? 2 : 1;
+    static constexpr int ES = (int)sizeof(T);
+    static constexpr BoxGeom BOX = plane_box(ES, NC, LAYOUT == LAYOUT_AOS, R, TX, TY);
+    static constexpr int A = BOX.a;
+    static constexpr int OFF = BOX.off;
+    static constexpr int BX = BOX.bx;
+    static constexpr int BY = BOX.by;
+    static constexpr int NT = TX * TY;
+    static constexpr int NS = DIM == 3 ? 2 * R + 2 : 3;  // ring slots
+    static constexpr int SLOT_ELEMS = BX * BY * NC;
+    static constexpr int SLOT_BYTES = ((SLOT_ELEMS * ES + 127) / 128) * 128;
+    static constexpr int OUT_ELEMS = TX * TY * NC;
+    static constexpr int OUT_BYTES = ((OUT_ELEMS * ES + 127) / 128) * 128;
+    static constexpr int NPX = (TX + 2) * TY, NPY = TX * (TY + 2);  // predicted-state cells
+    static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);  // faces
+    static constexpr int P_BYTES = SCHEME == SCHEME_MUSCL ? ((2 * NC * (NPX + NPY) * ES + 127) / 128) * 128 : 0;
+    static constexpr int F_BYTES = ((NC * (NFX + NFY) * ES + 127) / 128) * 128;
+    static constexpr int HDR_BYTES = 256;  // mbarriers + reduction scratch
+    static constexpr int SMEM = HDR_BYTES + NS * SLOT_BYTES + 2 * OUT_BYTES + P_BYTES + F_BYTES;
+    static_assert(TX % A == 0, "tile width must keep TMA x coordinates 16-byte aligned");
+    static_assert(BX * (LAYOUT == LAYOUT_AOS ? NC : 1) <= 256 && BY <= 256, "TMA box too large");
+    static_assert(TX * (LAYOUT == LAYOUT_AOS ? NC : 1) <= 256, "TMA store box too large");
+    static_assert(NT % 32 == 0 && NT <= 512, "whole warps, at most 16 (header reduction scratch)");
+};
+
+// Shared-memory accessors of a staged plane and of the output staging tile.
+template <class C, int LAYOUT>
+struct PlaneView {
+    __device__ static __forceinline__ int idx(int lx, int ly, int m)
+    {
+        // lx in [-R, TX+R), ly in [-R, TY+R)
+        if (LAYOUT == LAYOUT_SOA) return (m * C::BY + ly + C::R) * C::BX + C::OFF + C::R + lx;
+        return ((ly + C::R) * C::BX + C::OFF + C::R + lx) * C::NC + m;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// The sweep kernel.
+// ---------------------------------------------------------------------------
+template <typename T, int DIM, int LAYOUT, int SCHEME, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+    euler_sweep_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out,
+                       T* __restrict__ out, FieldCtl* __restrict__ ctl, const SweepGeom sg, const SweepParams prm)
+{
+    using C = SweepCfg<T, DIM, LAYOUT, SCHEME, TX, TY>;
+    using PV = PlaneView<C, LAYOUT>;
+    constexpr int NC = C::NC, R = C::R, NS = C::NS, NT = C::NT;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);              // NS mbarriers
+    double* red = reinterpret_cast<double*>(smem + 64);             // one double per warp (<= 16)
+    int* flags = reinterpret_cast<int*>(smem + 64 + 8 * 16);          // abort flag
+    T* ring = reinterpret_cast<T*>(smem + C::HDR_BYTES);
+    T* stage = reinterpret_cast<T*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES);
+    T* P = reinterpret_cast<T*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * C::OUT_BYTES);
+    T* Fs = reinterpret_cast<T*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * C::OUT_BYTES + C::P_BYTES);
+    T* PL = P;                          // [NC][NPX + NPY]
+    T* PR = P + NC * (C::NPX + C::NPY); // [NC][NPX + NPY]
+    T* FX = Fs;                         // [NC][NFX]
+    T* FY = Fs + NC * C::NFX;           // [NC][NFY]
+
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = tid / TX;
+    const FieldGeom& g = sg.f;
+
+    // dt from the max wave-speed sum of the input state (FP64)
+    const double smax_in = __longlong_as_double((long long)ctl->smax[prm.slot_in]);
+    const double dt = prm.cfl / smax_in;
+    const T gamma = (T)prm.gamma, gm1 = (T)(prm.gamma - 1.0);
+    const T dtT = (T)dt;
+    T inv_dx[3], half_dtdx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        inv_dx[d] = (T)prm.inv_dx[d];
+        half_dtdx[d] = (T)(0.5 * dt * prm.inv_dx[d]);
+    }
+    if (blockIdx.x == 0 && tid == 0) {
+        ctl->t = prm.first ? dt : ctl->t + dt;
+        ctl->dt_last = dt;
+        ctl->smax[(prm.slot_in + 2) % 3] = 0ull;  // slot the next step reduces into after this one
+    }
+
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+        flags[0] = 0;
+        fence_mbar_init();
+        prefetch_tensormap(&map_in);
+        prefetch_tensormap(&map_out);
+    }
+    __syncthreads();
+
+    // ---- plane sequence of this CTA: items strided over CTAs ----
+    auto item_planes = [&](int item) -> int {
+        if (DIM == 2) return 1;
+        const int chunk = item % sg.chunks_z;
+        const int z0 = chunk * sg.zchunk;
+        const int zn = min(sg.zchunk, g.n[2] - z0);
+        return zn + 2 * R;
+    };
+    // loader cursor (thread 0 only)
+    int ld_item = blockIdx.x, ld_j = 0;
+    long long ld_seq = 0;
+    auto issue_until = [&](long long limit) {
+        while (ld_item < sg.items && ld_seq < limit) {
+            const int item = ld_item;
+            const int chunk = DIM == 3 ? item % sg.chunks_z : 0;
+            const int tile = DIM == 3 ? item / sg.chunks_z : item;
+            const int tx = tile % sg.tiles_x, ty = tile / sg.tiles_x;
+            const int x0 = tx * TX, y0 = ty * TY;
+            const int xs = g.lead + g.h + x0 - R - C::OFF;
+            const int ys = g.h + y0 - R;
+            const int slot = (int)(ld_seq % NS);
+            T* dst = ring + (size_t)slot * (C::SLOT_BYTES / sizeof(T));
+            mbar_arrive_expect_tx(&bars[slot], (uint32_t)(C::SLOT_ELEMS * sizeof(T)));
+            if (DIM == 3) {
+                const int pz = g.h + chunk * sg.zchunk - R + ld_j;
+                if (LAYOUT == LAYOUT_SOA) tma_load_4d(dst, &map_in, xs, ys, pz, 0, &bars[slot]);
+                else tma_load_3d(dst, &map_in, xs * NC, ys, pz, &bars[slot]);
+            } else {
+                if (LAYOUT == LAYOUT_SOA) tma_load_3d(dst, &map_in, xs, ys, 0, &bars[slot]);
+                else tma_load_2d(dst, &map_in, xs * NC, ys, &bars[slot]);
+            }
+            ++ld_seq;
+            if (++ld_j == item_planes(item)) { ld_j = 0; ld_item += gridDim.x; }
+        }
+    };
+
+    long long ready_upto = 0;   // planes with seq < ready_upto have been waited for
+    long long seq_base = 0;     // seq of plane j = 0 of the current item
+    int out_count = 0;          // output planes produced (staging slot parity)
+    bool store_pending = false;
+    int st_x = 0, st_y = 0, st_z = 0, st_slot = 0;
+    bool bad = false;
+    T smax_local = T(0);
+    bool aborted = false;
+
+    // wait (all threads) for planes up to seq `need` inclusive; a wait that
+    // runs out raises the abort flag, read by every thread after the next barrier
+    auto wait_planes = [&](long long need) {
+        bool ok = true;
+        for (long long s = ready_upto; s <= need; ++s)
+            ok &= mbar_wait_bounded(&bars[s % NS], (uint32_t)((s / NS) & 1));
+        ready_upto = need + 1;
+        if (!ok) flags[0] = 1;
+    };
+    auto store_tile = [&]() {
+        const T* src = stage + (size_t)st_slot * (C::OUT_BYTES / sizeof(T));
+        if (DIM == 3) {
+            if (LAYOUT == LAYOUT_SOA) tma_store_4d(&map_out, src, st_x, st_y, st_z, 0);
+            else tma_store_3d(&map_out, src, st_x * NC, st_y, st_z);
+        } else {
+            if (LAYOUT == LAYOUT_SOA) tma_store_3d(&map_out, src, st_x, st_y, 0);
+            else tma_store_2d(&map_out, src, st_x * NC, st_y);
+        }
+        bulk_commit();
+    };
+    // Thread 0, called only right after a CTA barrier that follows every read
+    // of the planes with seq < free_before and every write of the staging tile
+    // that is still pending: flush that tile by TMA store, make sure the other
+    // staging slot has been read out, refill the freed ring slots.
+    auto producer_step = [&](long long free_before) {
+        if (tid != 0) return;
+        if (store_pending) {
+            store_tile();
+            store_pending = false;
+        }
+        bulk_wait_read<1>();
+        issue_until(free_before + NS);
+    };
+
+    for (int item = blockIdx.x; item < sg.items; item += gridDim.x) {
+        const int chunk = DIM == 3 ? item % sg.chunks_z : 0;
+        const int tile = DIM == 3 ? item / sg.chunks_z : item;
+        const int x0 = (tile % sg.tiles_x) * TX, y0 = (tile / sg.tiles_x) * TY;
+        const int z0 = chunk * sg.zchunk;
+        const int zn = DIM == 3 ? min(sg.zchunk, g.n[2] - z0) : 1;
+        const int gx = x0 + lx, gy = y0 + ly;
+        const bool col_valid = (gx < g.n[0]) & (gy < g.n[1]);
+        // A TMA store clipped at the interior's x end drops the last partial
+        // 16-byte chunk of each row when the row length is not a multiple of
+        // 16 bytes, so tiles that cross the x end store with plain stores.
+        const bool tma_store_ok = x0 + TX <= g.n[0];
+
+        // every plane of earlier items is free once all threads pass here
+        __syncthreads();  // B0
+        producer_step(seq_base);
+
+        // z carry (3D): lower face flux of the current plane, high-face predicted state
+        T Fzm[NC], zR[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) { Fzm[m] = T(0); zR[m] = T(0); }
+
+        if (DIM == 3) {
+            // planes j = 0 .. 2R-1 (z0-R .. z0+R-1) give the face z0 - 1/2
+            wait_planes(seq_base + 2 * R - 1);
+            __syncthreads();
+            if (flags[0]) { aborted = true; break; }
+            auto plane = [&](int j) { return ring + (size_t)((seq_base + j) % NS) * (C::SLOT_BYTES / sizeof(T)); };
+            T a[NC], b[NC];
+            if (SCHEME == SCHEME_RUSANOV1) {
+                const T* s0 = plane(0);  // z0 - 1
+                const T* s1 = plane(1);  // z0
+#pragma unroll
+                for (int m = 0; m < NC; ++m) { a[m] = s0[PV::idx(lx, ly, m)]; b[m] = s1[PV::idx(lx, ly, m)]; }
+                if (!rusanov<T, DIM, 2 % DIM>(a, b, gamma, gm1, Fzm) && col_valid) { bad = true; record_bad(ctl, BAD_FACE_Z, gx, gy, z0 - 1); }
+            } else {
+                const T* s0 = plane(0);  // z0 - 2
+                const T* s1 = plane(1);  // z0 - 1
+                const T* s2 = plane(2);  // z0
+                const T* s3 = plane(3);  // z0 + 1
+                T q0[NC], q1[NC], q2[NC], q3[NC], L1[NC], R1[NC], L2[NC];
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    const int id = PV::idx(lx, ly, m);
+                    q0[m] = s0[id]; q1[m] = s1[id]; q2[m] = s2[id]; q3[m] = s3[id];
+                }
+                if (!muscl_states<T, DIM, 2 % DIM>(q0, q1, q2, gm1, half_dtdx[2], L1, R1) && col_valid) { bad = true; record_bad(ctl, BAD_PRED_Z, gx, gy, z0 - 1); }
+                if (!muscl_states<T, DIM, 2 % DIM>(q1, q2, q3, gm1, half_dtdx[2], L2, zR) && col_valid) { bad = true; record_bad(ctl, BAD_PRED_Z, gx, gy, z0); }
+                if (!rusanov<T, DIM, 2 % DIM>(R1, L2, gamma, gm1, Fzm) && col_valid) { bad = true; record_bad(ctl, BAD_FACE_Z, gx, gy, z0 - 1); }
+            }
+        }
+
+        for (int zl = 0; zl < zn; ++zl) {
+            const int z = z0 + zl;
+            const long long jc = DIM == 3 ? (long long)zl + R : 0;  // plane index of z
+            wait_planes(seq_base + jc + (DIM == 3 ? R : 0));
+            __syncthreads();  // B1: the previous plane is fully processed
+            if (flags[0]) { aborted = true; break; }
+            producer_step(seq_base + jc);
+            const T* S = ring + (size_t)((seq_base + jc) % NS) * (C::SLOT_BYTES / sizeof(T));
+            T Fzp[NC];
+            // ---------------- phase P (MUSCL): predicted face states ----------------
+            if (SCHEME == SCHEME_MUSCL) {
+                constexpr int NPXr = ((C::NPX + 31) / 32) * 32;
+                constexpr int NPYr = ((C::NPY + 31) / 32) * 32;
+                for (int it = tid; it < NPXr + NPYr; it += NT) {
+                    if (it < NPXr) {
+                        if (it >= C::NPX) continue;
+                        const int cx = it % (TX + 2) - 1, cy = it / (TX + 2);
+                        T qm[NC], q[NC], qp[NC], L[NC], Rs[NC];
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            qm[m] = S[PV::idx(cx - 1, cy, m)];
+                            q[m] = S[PV::idx(cx, cy, m)];
+                            qp[m] = S[PV::idx(cx + 1, cy, m)];
+                        }
+                        const bool ok = muscl_states<T, DIM, 0>(qm, q, qp, gm1, half_dtdx[0], L, Rs);
+                        if (!ok && (x0 + cx <= g.n[0]) && (y0 + cy < g.n[1])) { bad = true; record_bad(ctl, BAD_PRED_X, x0 + cx, y0 + cy, z); }
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            PL[m * (C::NPX + C::NPY) + it] = L[m];
+                            PR[m * (C::NPX + C::NPY) + it] = Rs[m];
+                        }
+                    } else {
+                        const int k = it - NPXr;
+                        if (k >= C::NPY) continue;
+                        const int cx = k % TX, cy = k / TX - 1;
+                        T qm[NC], q[NC], qp[NC], L[NC], Rs[NC];
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            qm[m] = S[PV::idx(cx, cy - 1, m)];
+                            q[m] = S[PV::idx(cx, cy, m)];
+                            qp[m] = S[PV::idx(cx, cy + 1, m)];
+                        }
+                        const bool ok = muscl_states<T, DIM, 1>(qm, q, qp, gm1, half_dtdx[1], L, Rs);
+                        if (!ok && (x0 + cx < g.n[0]) && (y0 + cy <= g.n[1])) { bad = true; record_bad(ctl, BAD_PRED_Y, x0 + cx, y0 + cy, z); }
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            PL[m * (C::NPX + C::NPY) + C::NPX + k] = L[m];
+                            PR[m * (C::NPX + C::NPY) + C::NPX + k] = Rs[m];
+                        }
+                    }
+                }
+                if (DIM == 3) {
+                    // z: predicted states of plane z+1 and the face z + 1/2
+                    const T* s1 = ring + (size_t)((seq_base + jc + 1) % NS) * (C::SLOT_BYTES / sizeof(T));
+                    const T* s2 = ring + (size_t)((seq_base + jc + 2) % NS) * (C::SLOT_BYTES / sizeof(T));
+                    T q0[NC], q1[NC], q2[NC], L[NC], Rn[NC];
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) {
+                        const int id = PV::idx(lx, ly, m);
+                        q0[m] = S[id]; q1[m] = s1[id]; q2[m] = s2[id];
+                    }
+                    if (!muscl_states<T, DIM, 2 % DIM>(q0, q1, q2, gm1, half_dtdx[2], L, Rn) && col_valid) { bad = true; record_bad(ctl, BAD_PRED_Z, gx, gy, z + 1); }
+                    if (!rusanov<T, DIM, 2 % DIM>(zR, L, gamma, gm1, Fzp) && col_valid) { bad = true; record_bad(ctl, BAD_FACE_Z, gx, gy, z); }
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) zR[m] = Rn[m];
+                }
+                __syncthreads();  // B2
+            } else if (DIM == 3) {
+                const T* s1 = ring + (size_t)((seq_base + jc + 1) % NS) * (C::SLOT_BYTES / sizeof(T));
+                T a[NC], b[NC];
+#pragma unroll
+                for (int m = 0; m < NC; ++m) { a[m] = S[PV::idx(lx, ly, m)]; b[m] = s1[PV::idx(lx, ly, m)]; }
+                if (!rusanov<T, DIM, 2 % DIM>(a, b, gamma, gm1, Fzp) && col_valid) { bad = true; record_bad(ctl, BAD_FACE_Z, gx, gy, z); }
+            }
+
+            // ---------------- phase F: x and y face fluxes ----------------
+            {
+                constexpr int NFXr = ((C::NFX + 31) / 32) * 32;
+                constexpr int NFYr = ((C::NFY + 31) / 32) * 32;
+                for (int it = tid; it < NFXr + NFYr; it += NT) {
+                    if (it < NFXr) {
+                        if (it >= C::NFX) continue;
+                        const int fx = it % (TX + 1), cy = it / (TX + 1);  // face between fx-1 and fx
+                        T a[NC], b[NC], F[NC];
+                        if (SCHEME == SCHEME_MUSCL) {
+                            const int il = cy * (TX + 2) + fx, ir = il + 1;
+#pragma unroll
+                            for (int m = 0; m < NC; ++m) {
+                                a[m] = PR[m * (C::NPX + C::NPY) + il];
+                                b[m] = PL[m * (C::NPX + C::NPY) + ir];
+                            }
+                        } else {
+#pragma unroll
+                            for (int m = 0; m < NC; ++m) {
+                                a[m] = S[PV::idx(fx - 1, cy, m)];
+                                b[m] = S[PV::idx(fx, cy, m)];
+                            }
+                        }
+                        const bool ok = rusanov<T, DIM, 0>(a, b, gamma, gm1, F);
+                        if (!ok && (x0 + fx <= g.n[0]) && (y0 + cy < g.n[1])) { bad = true; record_bad(ctl, BAD_FACE_X, x0 + fx - 1, y0 + cy, z); }
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) FX[m * C::NFX + it] = F[m];
+                    } else {
+                        const int k = it - NFXr;
+                        if (k >= C::NFY) continue;
+                        const int cx = k % TX, fy = k / TX;  // face between fy-1 and fy
+                        T a[NC], b[NC], F[NC];
+                        if (SCHEME == SCHEME_MUSCL) {
+                            const int il = C::NPX + fy * TX + cx, ir = il + TX;
+#pragma unroll
+                            for (int m = 0; m < NC; ++m) {
+                                a[m] = PR[m * (C::NPX + C::NPY) + il];
+                                b[m] = PL[m * (C::NPX + C::NPY) + ir];
+                            }
+                        } else {
+#pragma unroll
+                            for (int m = 0; m < NC; ++m) {
+                                a[m] = S[PV::idx(cx, fy - 1, m)];
+                                b[m] = S[PV::idx(cx, fy, m)];
+                            }
+                        }
+                        const bool ok = rusanov<T, DIM, 1>(a, b, gamma, gm1, F);
+                        if (!ok && (x0 + cx < g.n[0]) && (y0 + fy <= g.n[1])) { bad = true; record_bad(ctl, BAD_FACE_Y, x0 + cx, y0 + fy - 1, z); }
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) FY[m * C::NFY + k] = F[m];
+                    }
+                }
+            }
+            __syncthreads();  // B3
+
+            // ---------------- phase U: conservative update + epilogue ----------------
+            {
+                T* st = stage + (size_t)(out_count & 1) * (C::OUT_BYTES / sizeof(T));
+                T qn[NC];
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    const T fxp = FX[m * C::NFX + ly * (TX + 1) + lx + 1];
+                    const T fxm = FX[m * C::NFX + ly * (TX + 1) + lx];
+                    const T fyp = FY[m * C::NFY + (ly + 1) * TX + lx];
+                    const T fym = FY[m * C::NFY + ly * TX + lx];
+                    T acc = (fxp - fxm) * inv_dx[0];
+                    acc += (fyp - fym) * inv_dx[1];
+                    if (DIM == 3) acc += (Fzp[m] - Fzm[m]) * inv_dx[2];
+                    qn[m] = S[PV::idx(lx, ly, m)] - dtT * acc;
+                    if (tma_store_ok) {
+                        if (LAYOUT == LAYOUT_SOA) st[(m * TY + ly) * TX + lx] = qn[m];
+                        else st[(ly * TX + lx) * NC + m] = qn[m];
+                    }
+                }
+                if (!tma_store_ok && col_valid) {
+                    const long long base = geom_cell(g, gx, gy, z) * g.cell_stride;
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = qn[m];
+                }
+                if (DIM == 3) {
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) Fzm[m] = Fzp[m];
+                }
+                fence_proxy_async_smem();
+                if (col_valid) {
+                    bool ok;
+                    const T s = wave_sum<T, DIM>(qn, gamma, gm1, inv_dx, ok);
+                    if (!ok) { bad = true; record_bad(ctl, BAD_CELL, gx, gy, z); }
+                    smax_local = fmax(smax_local, s);
+                    write_ghost_images<T, DIM>(out, g, prm.bc, gx, gy, z, qn);
+                }
+                if (tma_store_ok) {
+                    store_pending = true;
+                    st_x = x0; st_y = y0; st_z = z; st_slot = out_count & 1;
+                    ++out_count;
+                }
+            }
+        }
+        if (aborted) break;
+        seq_base += DIM == 3 ? (long long)zn + 2 * R : 1;
+    }
+
+    // ---- drain: last store, wait for completion ----
+    __syncthreads();
+    if (tid == 0) {
+        if (store_pending && !aborted) store_tile();
+        bulk_wait<0>();
+        if (aborted) {
+            // loads still in flight complete into this CTA's shared memory:
+            // wait for them (bounded) before the CTA exits
+            for (long long s = ready_upto; s < ld_seq; ++s) mbar_wait_bounded(&bars[s % NS], (uint32_t)((s / NS) & 1));
+            atomicOr(&ctl->err, DEV_ERR_TIMEOUT);
+        }
+    }
+
+    // ---- block reductions: max wave speed, positivity ----
+    double v = (double)smax_local;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int any_bad = __syncthreads_or(bad ? 1 : 0);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int w = 0; w < NT / 32; ++w) m = fmax(m, red[w]);
+        atomic_max_pos_double(&ctl->smax[(prm.slot_in + 1) % 3], m);
+        if (any_bad) atomicOr(&ctl->err, DEV_ERR_NUMERIC);
+    }
+}
+
+}  // namespace ripple
