@@ -217,6 +217,42 @@ RIPPLE_API ripple_status ripple_eikonal_solve(ripple_field slowness, ripple_fiel
                                    int nsrc, const ripple_eik_params* params, ripple_eik_stats* stats);
 
 /* ------------------------------------------------------------------------ */
+/* Conserved totals for callers that cannot allocate device memory.          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The paper has no counterpart to this entry point.
+ *
+ * Some callers cannot let a library call cudaMalloc: an application that has
+ * given all device memory to its own pool or budget, or a latency-bound loop
+ * in which the implicit device synchronisation of cudaMalloc/cudaFree would
+ * stall work already queued on the GPU.  This function computes the same FP64
+ * compensated per-component sums as the `totals` of ripple_fv_step, over a
+ * dense DEVICE array the caller owns, and allocates nothing: its only scratch
+ * is a fixed 640 KiB array inside the library's device image, present on every
+ * GPU that loads the library until the process exits.
+ *
+ *   state       device array of interior cells, dims[0] x ... x dims[ndim-1]
+ *               (x fastest), `ncomp` components in `layout` (see the
+ *               conventions above), elements float (RIPPLE_F32) or double
+ *               (RIPPLE_F64).  Read only.
+ *   totals_out  device array of `ncomp` doubles, written.
+ *   cuda_stream the cudaStream_t to queue on (NULL = legacy default stream).
+ * The call is asynchronous on `cuda_stream`; the caller keeps ownership of
+ * every pointer.  At most 33,554,432 cells (RIPPLE_ERR_INVALID beyond that,
+ * or for ncomp outside 1..5) -- the capacity of the fixed scratch.
+ * All calls share the scratch array: calls that overlap on the GPU race and
+ * must be serialised by the caller (e.g. by using one stream).  Each call
+ * writes every scratch entry it reads, so nothing needs clearing in between.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.
+ */
+RIPPLE_API ripple_status ripple_totals_noalloc(const void* state, int ndim, const int64_t* dims, int ncomp,
+                                               ripple_layout layout, ripple_dtype dtype, double* totals_out,
+                                               void* cuda_stream);
+
+/* ------------------------------------------------------------------------ */
 /* Library                                                                   */
 /* ------------------------------------------------------------------------ */
 

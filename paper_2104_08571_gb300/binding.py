@@ -94,6 +94,7 @@ _SIGNATURES = {
     "ripple_fv_step": [_VP, ctypes.POINTER(ripple_fv_params), ctypes.c_int64, ctypes.POINTER(ripple_fv_stats)],
     "ripple_eikonal_solve": [_VP, _VP, _I64P, ctypes.c_int, ctypes.POINTER(ripple_eik_params),
                              ctypes.POINTER(ripple_eik_stats)],
+    "ripple_totals_noalloc": [_VP, ctypes.c_int, _I64P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP],
 }
 _STRING_FUNCS = ["ripple_last_error", "ripple_version"]
 
@@ -300,3 +301,15 @@ def ripple_eikonal_solve(slowness, T, sources, h, tol=1e-6, max_iters=0):
     _check(load().ripple_eikonal_solve(slowness, T, arr, len(sources), ctypes.byref(prm), ctypes.byref(st)),
            "ripple_eikonal_solve")
     return dict(iterations=st.iterations, tile_visits=st.tile_visits, cell_updates=st.cell_updates)
+
+
+def ripple_totals_noalloc(state, dims, ncomp, layout, dtype, totals_out, stream=None):
+    """FP64 compensated totals of a dense CUDA tensor `state` into the CUDA tensor
+    `totals_out` (ncomp doubles) without any device allocation by the library.
+    Asynchronous on `stream` (a torch.cuda.Stream, a cudaStream_t int, or None)."""
+    d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
+    handle = None
+    if stream is not None:
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(load().ripple_totals_noalloc(_VP(state.data_ptr()), len(dims), d, int(ncomp), int(layout), int(dtype),
+                                        _VP(totals_out.data_ptr()), handle), "ripple_totals_noalloc")
