@@ -63,11 +63,24 @@ struct SweepParams {
 };
 
 // ---------------------------------------------------------------------------
-// Arithmetic helpers (field precision).
+// Arithmetic helpers (field precision).  FP32 uses the hardware approximate
+// reciprocal and square root (relative error of about one unit in the last
+// place, far inside the FP32 error budget against the FP64 oracle); FP64 keeps
+// IEEE division and square root.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float rcp_t(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ float rcp_t(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double rcp_t(double x) { return 1.0 / x; }
-__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ float sqrt_t(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 __device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
 
 template <typename T>
@@ -78,11 +91,11 @@ __device__ __forceinline__ T minmod_t(T a, T b)
     return fabs(a) < fabs(b) ? a : b;
 }
 
-// Physical flux along axis D; also returns density, normal velocity, pressure.
+// Physical flux along axis D; also returns 1/rho, the normal velocity and the pressure.
 template <typename T, int DIM, int D>
-__device__ __forceinline__ void phys_flux(const T (&q)[DIM + 2], T gm1, T (&F)[DIM + 2], T& un, T& p)
+__device__ __forceinline__ void phys_flux(const T (&q)[DIM + 2], T gm1, T (&F)[DIM + 2], T& inv_rho, T& un, T& p)
 {
-    const T inv_rho = rcp_t(q[0]);
+    inv_rho = rcp_t(q[0]);
     T mm = q[1] * q[1];
 #pragma unroll
     for (int e = 1; e < DIM; ++e) mm = fma(q[1 + e], q[1 + e], mm);
@@ -95,31 +108,40 @@ __device__ __forceinline__ void phys_flux(const T (&q)[DIM + 2], T gm1, T (&F)[D
     F[DIM + 1] = (q[DIM + 1] + p) * un;
 }
 
-// Rusanov face flux along D between left state a and right state b.
-// Returns false when a state is not admissible (rho <= 0 or p <= 0 or NaN).
-template <typename T, int DIM, int D>
-__device__ __forceinline__ bool rusanov(const T (&a)[DIM + 2], const T (&b)[DIM + 2], T gamma, T gm1,
-                                        T (&F)[DIM + 2])
+// Admissibility bookkeeping: `chk` keeps the smallest density or pressure
+// seen in the states of in-domain items; a non-positive value flags the plane.
+// (A NaN state is skipped by fmin but reaches the updated cells, whose own
+// check catches it.)
+template <typename T>
+__device__ __forceinline__ void track_min(T& chk, bool valid, T a, T b, T c, T d)
 {
-    T Fa[DIM + 2], Fb[DIM + 2], ua, pa, ub, pb;
-    phys_flux<T, DIM, D>(a, gm1, Fa, ua, pa);
-    phys_flux<T, DIM, D>(b, gm1, Fb, ub, pb);
-    const bool ok = (a[0] > T(0)) & (pa > T(0)) & (b[0] > T(0)) & (pb > T(0));
-    const T ca = sqrt_t(gamma * pa * rcp_t(a[0]));
-    const T cb = sqrt_t(gamma * pb * rcp_t(b[0]));
+    const T m = fmin(fmin(a, b), fmin(c, d));
+    if (valid) chk = fmin(chk, m);
+}
+
+// Rusanov face flux along D between left state a and right state b.
+template <typename T, int DIM, int D>
+__device__ __forceinline__ void rusanov(const T (&a)[DIM + 2], const T (&b)[DIM + 2], T gamma, T gm1,
+                                        T (&F)[DIM + 2], T& chk, bool valid)
+{
+    T Fa[DIM + 2], Fb[DIM + 2], ia, ua, pa, ib, ub, pb;
+    phys_flux<T, DIM, D>(a, gm1, Fa, ia, ua, pa);
+    phys_flux<T, DIM, D>(b, gm1, Fb, ib, ub, pb);
+    track_min(chk, valid, a[0], pa, b[0], pb);
+    const T ca = sqrt_t(gamma * pa * ia);
+    const T cb = sqrt_t(gamma * pb * ib);
     const T s = fmax(fabs(ua) + ca, fabs(ub) + cb);
 #pragma unroll
     for (int m = 0; m < DIM + 2; ++m) F[m] = T(0.5) * (Fa[m] + Fb[m]) - T(0.5) * s * (b[m] - a[m]);
-    return ok;
 }
 
 // MUSCL-Hancock face states of a cell along D from (left, centre, right):
 // slopes by minmod, boundary extrapolation, half-step predictor with the
-// direction-D flux difference.  Returns admissibility of the extrapolated states.
+// direction-D flux difference (admissibility of the extrapolated states goes to chk).
 template <typename T, int DIM, int D>
-__device__ __forceinline__ bool muscl_states(const T (&qm)[DIM + 2], const T (&q)[DIM + 2],
+__device__ __forceinline__ void muscl_states(const T (&qm)[DIM + 2], const T (&q)[DIM + 2],
                                              const T (&qp)[DIM + 2], T gm1, T half_dtdx,
-                                             T (&L)[DIM + 2], T (&R)[DIM + 2])
+                                             T (&L)[DIM + 2], T (&R)[DIM + 2], T& chk, bool valid)
 {
 #pragma unroll
     for (int m = 0; m < DIM + 2; ++m) {
@@ -127,17 +149,16 @@ __device__ __forceinline__ bool muscl_states(const T (&qm)[DIM + 2], const T (&q
         L[m] = q[m] - T(0.5) * slope;
         R[m] = q[m] + T(0.5) * slope;
     }
-    T FL[DIM + 2], FR[DIM + 2], u, pl, pr;
-    phys_flux<T, DIM, D>(L, gm1, FL, u, pl);
-    phys_flux<T, DIM, D>(R, gm1, FR, u, pr);
-    const bool ok = (L[0] > T(0)) & (pl > T(0)) & (R[0] > T(0)) & (pr > T(0));
+    T FL[DIM + 2], FR[DIM + 2], il, ir, u, pl, pr;
+    phys_flux<T, DIM, D>(L, gm1, FL, il, u, pl);
+    phys_flux<T, DIM, D>(R, gm1, FR, ir, u, pr);
+    track_min(chk, valid, L[0], pl, R[0], pr);
 #pragma unroll
     for (int m = 0; m < DIM + 2; ++m) {
         const T inc = half_dtdx * (FL[m] - FR[m]);
         L[m] += inc;
         R[m] += inc;
     }
-    return ok;
 }
 
 // Wave-speed sum and admissibility of a conserved state.
@@ -203,7 +224,9 @@ __device__ __forceinline__ void write_ghost_images(T* __restrict__ out, const Fi
 
 // Where the first non-admissible state was found (FieldCtl::counters[4..7]):
 // stage code + 1, then x, y, z of the cell (or of the left cell of a face).
-enum : int { BAD_PRED_X = 1, BAD_PRED_Y, BAD_PRED_Z, BAD_FACE_X, BAD_FACE_Y, BAD_FACE_Z, BAD_CELL, BAD_INPUT };
+// BAD_STATE: a reconstructed, predicted or face state of the tile whose
+// first cell is (x, y) on plane z; BAD_CELL / BAD_INPUT: that cell itself.
+enum : int { BAD_STATE = 1, BAD_CELL = 7, BAD_INPUT = 8 };
 static __device__ __noinline__ void record_bad(FieldCtl* ctl, int code, int x, int y, int z)
 {
     if (atomicCAS(reinterpret_cast<unsigned long long*>(&ctl->counters[4]), 0ull, (unsigned long long)code) == 0ull) {
@@ -285,28 +308,54 @@ struct PlaneView {
 
 // ---------------------------------------------------------------------------
 // The sweep kernel.
+//
+// Per plane z of a work item (3D MUSCL shown; Rusanov has no phase P and
+// computes its z face in phase F; 2D has no z work):
+//   B2  barrier; thread 0 flushes the previous staging tile and refills freed
+//       ring slots; every thread checks the abort flag
+//   F   x and y face fluxes from the predicted states -> shared arrays
+//   B3  barrier
+//   U   conservative update of the thread's cell (x, y faces from shared
+//       memory, z faces from registers) -> staging tile, ghost images,
+//       wave-speed max, positivity; then, if the item has another plane, wait
+//       for its planes and run phase P of plane z+1:
+//   P   x and y predicted states -> shared arrays; z predicted state of the
+//       thread's own column at z+2 and the z face z+3/2 in registers
+// so that each plane costs two CTA barriers.  Each thread's work items in
+// phases P and F are fixed for the whole tile; their shared-memory offsets
+// are decoded once per tile.
 // ---------------------------------------------------------------------------
 template <typename T, int DIM, int LAYOUT, int SCHEME, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
     euler_sweep_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out,
                        T* __restrict__ out, FieldCtl* __restrict__ ctl, const SweepGeom sg, const SweepParams prm)
 {
     using C = SweepCfg<T, DIM, LAYOUT, SCHEME, TX, TY>;
     using PV = PlaneView<C, LAYOUT>;
     constexpr int NC = C::NC, R = C::R, NS = C::NS, NT = C::NT;
+    constexpr bool MUSCL = SCHEME == SCHEME_MUSCL;
+    // element strides inside a staged plane
+    constexpr int SX = LAYOUT == LAYOUT_SOA ? 1 : NC;          // +1 cell in x
+    constexpr int SY = LAYOUT == LAYOUT_SOA ? C::BX : C::BX * NC;  // +1 cell in y
+    constexpr int SM = LAYOUT == LAYOUT_SOA ? C::BX * C::BY : 1;   // +1 component
+    constexpr int NP = C::NPX + C::NPY;  // predicted-state items (MUSCL)
+    constexpr int NPXr = ((C::NPX + 31) / 32) * 32, NPYr = ((C::NPY + 31) / 32) * 32;
+    constexpr int NFXr = ((C::NFX + 31) / 32) * 32, NFYr = ((C::NFY + 31) / 32) * 32;
+    constexpr int KP = MUSCL ? (NPXr + NPYr + NT - 1) / NT : 0;  // phase-P items per thread
+    constexpr int KF = (NFXr + NFYr + NT - 1) / NT;              // phase-F items per thread
 
     extern __shared__ __align__(128) unsigned char smem[];
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);              // NS mbarriers
-    double* red = reinterpret_cast<double*>(smem + 64);             // one double per warp (<= 16)
-    int* flags = reinterpret_cast<int*>(smem + 64 + 8 * 16);          // abort flag
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);      // NS mbarriers
+    double* red = reinterpret_cast<double*>(smem + 64);      // one double per warp (<= 16)
+    int* flags = reinterpret_cast<int*>(smem + 64 + 8 * 16);  // abort flag
     T* ring = reinterpret_cast<T*>(smem + C::HDR_BYTES);
     T* stage = reinterpret_cast<T*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES);
     T* P = reinterpret_cast<T*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * C::OUT_BYTES);
     T* Fs = reinterpret_cast<T*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * C::OUT_BYTES + C::P_BYTES);
-    T* PL = P;                          // [NC][NPX + NPY]
-    T* PR = P + NC * (C::NPX + C::NPY); // [NC][NPX + NPY]
-    T* FX = Fs;                         // [NC][NFX]
-    T* FY = Fs + NC * C::NFX;           // [NC][NFY]
+    T* PL = P;            // [NC][NPX + NPY]
+    T* PR = P + NC * NP;  // [NC][NPX + NPY]
+    T* FX = Fs;           // [NC][NFX]
+    T* FY = Fs + NC * C::NFX;  // [NC][NFY]
 
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
@@ -328,7 +377,6 @@ __global__ void __launch_bounds__(TX * TY)
         ctl->dt_last = dt;
         ctl->smax[(prm.slot_in + 2) % 3] = 0ull;  // slot the next step reduces into after this one
     }
-
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
         flags[0] = 0;
@@ -342,20 +390,16 @@ __global__ void __launch_bounds__(TX * TY)
     auto item_planes = [&](int item) -> int {
         if (DIM == 2) return 1;
         const int chunk = item % sg.chunks_z;
-        const int z0 = chunk * sg.zchunk;
-        const int zn = min(sg.zchunk, g.n[2] - z0);
-        return zn + 2 * R;
+        return min(sg.zchunk, g.n[2] - chunk * sg.zchunk) + 2 * R;
     };
-    // loader cursor (thread 0 only)
-    int ld_item = blockIdx.x, ld_j = 0;
+    int ld_item = blockIdx.x, ld_j = 0;  // loader cursor (thread 0 only)
     long long ld_seq = 0;
     auto issue_until = [&](long long limit) {
         while (ld_item < sg.items && ld_seq < limit) {
             const int item = ld_item;
             const int chunk = DIM == 3 ? item % sg.chunks_z : 0;
             const int tile = DIM == 3 ? item / sg.chunks_z : item;
-            const int tx = tile % sg.tiles_x, ty = tile / sg.tiles_x;
-            const int x0 = tx * TX, y0 = ty * TY;
+            const int x0 = (tile % sg.tiles_x) * TX, y0 = (tile / sg.tiles_x) * TY;
             const int xs = g.lead + g.h + x0 - R - C::OFF;
             const int ys = g.h + y0 - R;
             const int slot = (int)(ld_seq % NS);
@@ -374,21 +418,24 @@ __global__ void __launch_bounds__(TX * TY)
         }
     };
 
-    long long ready_upto = 0;   // planes with seq < ready_upto have been waited for
-    long long seq_base = 0;     // seq of plane j = 0 of the current item
-    int out_count = 0;          // output planes produced (staging slot parity)
+    long long ready_upto = 0;  // planes with seq < ready_upto have been waited for
+    long long seq_base = 0;    // seq of plane j = 0 of the current item
+    int out_count = 0;         // TMA-stored planes (staging slot parity)
     bool store_pending = false;
     int st_x = 0, st_y = 0, st_z = 0, st_slot = 0;
     bool bad = false;
     T smax_local = T(0);
     bool aborted = false;
 
+    auto plane_ptr = [&](long long seq) -> const T* {
+        return ring + (size_t)(seq % NS) * (C::SLOT_BYTES / sizeof(T));
+    };
     // wait (all threads) for planes up to seq `need` inclusive; a wait that
     // runs out raises the abort flag, read by every thread after the next barrier
     auto wait_planes = [&](long long need) {
         bool ok = true;
-        for (long long s = ready_upto; s <= need; ++s)
-            ok &= mbar_wait_bounded(&bars[s % NS], (uint32_t)((s / NS) & 1));
+        for (long long sq = ready_upto; sq <= need; ++sq)
+            ok &= mbar_wait_bounded(&bars[sq % NS], (uint32_t)((sq / NS) & 1));
         ready_upto = need + 1;
         if (!ok) flags[0] = 1;
     };
@@ -417,6 +464,12 @@ __global__ void __launch_bounds__(TX * TY)
         issue_until(free_before + NS);
     };
 
+    // load the NC components of the cell at element offset `o` of plane S
+    auto load_q = [&](const T* S, int o, T (&q)[NC]) {
+#pragma unroll
+        for (int m = 0; m < NC; ++m) q[m] = S[o + m * SM];
+    };
+
     for (int item = blockIdx.x; item < sg.items; item += gridDim.x) {
         const int chunk = DIM == 3 ? item % sg.chunks_z : 0;
         const int tile = DIM == 3 ? item / sg.chunks_z : item;
@@ -429,172 +482,176 @@ __global__ void __launch_bounds__(TX * TY)
         // 16-byte chunk of each row when the row length is not a multiple of
         // 16 bytes, so tiles that cross the x end store with plain stores.
         const bool tma_store_ok = x0 + TX <= g.n[0];
+        // only tiles within h cells of a domain face have ghost images to write
+        const bool near_xy = (x0 < g.h) || (x0 + TX > g.n[0] - g.h) || (y0 < g.h) || (y0 + TY > g.n[1] - g.h);
+        T chk = T(1);  // smallest density/pressure of this thread's in-domain states
+
+        // ---- per-tile decode of this thread's phase-P and phase-F items ----
+        // Item k of this thread is it = tid + k * NT.  Kept per item: the element
+        // offset of its (left) cell in a staged plane; packed in *_bits: bit 2k
+        // = x item, bit 2k+1 = y item, bit 16+k = the item touches the domain
+        // (its positivity check counts).  Array indices follow from `it`.
+        int p_off[KP > 0 ? KP : 1];
+        unsigned p_bits = 0u;
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const int it = tid + k * NT;
+            p_off[k] = 0;
+            if (it < C::NPX) {
+                const int cx = it % (TX + 2) - 1, cy = it / (TX + 2);
+                p_off[k] = PV::idx(cx, cy, 0);
+                p_bits |= 1u << (2 * k);
+                if ((x0 + cx <= g.n[0]) && (y0 + cy < g.n[1])) p_bits |= 1u << (16 + k);
+            } else if (it >= NPXr && it - NPXr < C::NPY) {
+                const int kk = it - NPXr;
+                const int cx = kk % TX, cy = kk / TX - 1;
+                p_off[k] = PV::idx(cx, cy, 0);
+                p_bits |= 2u << (2 * k);
+                if ((x0 + cx < g.n[0]) && (y0 + cy <= g.n[1])) p_bits |= 1u << (16 + k);
+            }
+        }
+        int f_off[KF], f_il[KF];
+        unsigned f_bits = 0u;
+#pragma unroll
+        for (int k = 0; k < KF; ++k) {
+            const int it = tid + k * NT;
+            f_off[k] = 0;
+            f_il[k] = 0;
+            if (it < C::NFX) {
+                const int fx = it % (TX + 1), cy = it / (TX + 1);  // face between fx-1 and fx
+                f_off[k] = PV::idx(fx - 1, cy, 0);
+                f_il[k] = cy * (TX + 2) + fx;
+                f_bits |= 1u << (2 * k);
+                if ((x0 + fx <= g.n[0]) && (y0 + cy < g.n[1])) f_bits |= 1u << (16 + k);
+            } else if (it >= NFXr && it - NFXr < C::NFY) {
+                const int kk = it - NFXr;
+                const int cx = kk % TX, fy = kk / TX;  // face between fy-1 and fy
+                f_off[k] = PV::idx(cx, fy - 1, 0);
+                f_il[k] = C::NPX + fy * TX + cx;
+                f_bits |= 2u << (2 * k);
+                if ((x0 + cx < g.n[0]) && (y0 + fy <= g.n[1])) f_bits |= 1u << (16 + k);
+            }
+        }
+        const int my_off = PV::idx(lx, ly, 0);
+
+        // z registers (3D): lower face flux of the current plane, the high-face
+        // predicted state of the next plane, and the column values of the
+        // current plane (qa) and the one above (qb)
+        T Fzm[NC], Fzp[NC], zR[NC], qa[NC], qb[NC], qz2[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            Fzm[m] = T(0); Fzp[m] = T(0); zR[m] = T(0); qa[m] = T(0); qb[m] = T(0); qz2[m] = T(0);
+        }
+
+        // Phase P of the plane with index j (seq_base + j); z = z0 - R + j.
+        auto phase_p = [&](long long j, int z) {
+            const T* S = plane_ptr(seq_base + j);
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const unsigned kind = (p_bits >> (2 * k)) & 3u;
+                if (kind == 0u) continue;
+                const int it = tid + k * NT;
+                const int pidx = kind == 1u ? it : C::NPX + it - NPXr;
+                const int o = p_off[k];
+                const int st = kind == 1u ? SX : SY;
+                T qm[NC], q[NC], qp[NC], L[NC], Rs[NC];
+                load_q(S, o - st, qm);
+                load_q(S, o, q);
+                load_q(S, o + st, qp);
+                const bool v = (p_bits >> (16 + k)) & 1u;
+                if (kind == 1u) muscl_states<T, DIM, 0>(qm, q, qp, gm1, half_dtdx[0], L, Rs, chk, v);
+                else muscl_states<T, DIM, 1>(qm, q, qp, gm1, half_dtdx[1], L, Rs, chk, v);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    PL[m * NP + pidx] = L[m];
+                    PR[m * NP + pidx] = Rs[m];
+                }
+            }
+            if (DIM == 3) {
+                // z: predicted states of plane z+1 and the face z + 1/2
+                T L[NC], Rn[NC];
+                load_q(plane_ptr(seq_base + j + 2), my_off, qz2);
+                muscl_states<T, DIM, 2 % DIM>(qa, qb, qz2, gm1, half_dtdx[2], L, Rn, chk, col_valid);
+                rusanov<T, DIM, 2 % DIM>(zR, L, gamma, gm1, Fzp, chk, col_valid);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) zR[m] = Rn[m];  // qa, qb shift after phase U
+            }
+        };
 
         // every plane of earlier items is free once all threads pass here
         __syncthreads();  // B0
         producer_step(seq_base);
 
-        // z carry (3D): lower face flux of the current plane, high-face predicted state
-        T Fzm[NC], zR[NC];
-#pragma unroll
-        for (int m = 0; m < NC; ++m) { Fzm[m] = T(0); zR[m] = T(0); }
-
         if (DIM == 3) {
-            // planes j = 0 .. 2R-1 (z0-R .. z0+R-1) give the face z0 - 1/2
-            wait_planes(seq_base + 2 * R - 1);
+            // planes j = 0 .. 2R-1 (z0-R .. z0+R-1) give the face z0 - 1/2;
+            // phase P of z0 needs up to j = 2R (MUSCL)
+            wait_planes(seq_base + (MUSCL ? 2 * R : 2 * R - 1));
             __syncthreads();
             if (flags[0]) { aborted = true; break; }
-            auto plane = [&](int j) { return ring + (size_t)((seq_base + j) % NS) * (C::SLOT_BYTES / sizeof(T)); };
-            T a[NC], b[NC];
-            if (SCHEME == SCHEME_RUSANOV1) {
-                const T* s0 = plane(0);  // z0 - 1
-                const T* s1 = plane(1);  // z0
+            if (!MUSCL) {
+                load_q(plane_ptr(seq_base + 0), my_off, qa);  // z0 - 1
+                load_q(plane_ptr(seq_base + 1), my_off, qb);  // z0
+                rusanov<T, DIM, 2 % DIM>(qa, qb, gamma, gm1, Fzm, chk, col_valid);
 #pragma unroll
-                for (int m = 0; m < NC; ++m) { a[m] = s0[PV::idx(lx, ly, m)]; b[m] = s1[PV::idx(lx, ly, m)]; }
-                if (!rusanov<T, DIM, 2 % DIM>(a, b, gamma, gm1, Fzm) && col_valid) { bad = true; record_bad(ctl, BAD_FACE_Z, gx, gy, z0 - 1); }
+                for (int m = 0; m < NC; ++m) qa[m] = qb[m];  // qa = column value of z0
             } else {
-                const T* s0 = plane(0);  // z0 - 2
-                const T* s1 = plane(1);  // z0 - 1
-                const T* s2 = plane(2);  // z0
-                const T* s3 = plane(3);  // z0 + 1
-                T q0[NC], q1[NC], q2[NC], q3[NC], L1[NC], R1[NC], L2[NC];
-#pragma unroll
-                for (int m = 0; m < NC; ++m) {
-                    const int id = PV::idx(lx, ly, m);
-                    q0[m] = s0[id]; q1[m] = s1[id]; q2[m] = s2[id]; q3[m] = s3[id];
-                }
-                if (!muscl_states<T, DIM, 2 % DIM>(q0, q1, q2, gm1, half_dtdx[2], L1, R1) && col_valid) { bad = true; record_bad(ctl, BAD_PRED_Z, gx, gy, z0 - 1); }
-                if (!muscl_states<T, DIM, 2 % DIM>(q1, q2, q3, gm1, half_dtdx[2], L2, zR) && col_valid) { bad = true; record_bad(ctl, BAD_PRED_Z, gx, gy, z0); }
-                if (!rusanov<T, DIM, 2 % DIM>(R1, L2, gamma, gm1, Fzm) && col_valid) { bad = true; record_bad(ctl, BAD_FACE_Z, gx, gy, z0 - 1); }
+                T q0[NC], q1[NC], L1[NC], R1[NC], L2[NC];
+                load_q(plane_ptr(seq_base + 0), my_off, q0);  // z0 - 2
+                load_q(plane_ptr(seq_base + 1), my_off, q1);  // z0 - 1
+                load_q(plane_ptr(seq_base + 2), my_off, qa);  // z0
+                load_q(plane_ptr(seq_base + 3), my_off, qb);  // z0 + 1
+                muscl_states<T, DIM, 2 % DIM>(q0, q1, qa, gm1, half_dtdx[2], L1, R1, chk, col_valid);
+                muscl_states<T, DIM, 2 % DIM>(q1, qa, qb, gm1, half_dtdx[2], L2, zR, chk, col_valid);
+                rusanov<T, DIM, 2 % DIM>(R1, L2, gamma, gm1, Fzm, chk, col_valid);
+                // qa, qb now hold the column values of z0 and z0 + 1
             }
+        } else {
+            wait_planes(seq_base);
         }
+        if (MUSCL) phase_p(DIM == 3 ? R : 0, z0);
 
         for (int zl = 0; zl < zn; ++zl) {
             const int z = z0 + zl;
             const long long jc = DIM == 3 ? (long long)zl + R : 0;  // plane index of z
-            wait_planes(seq_base + jc + (DIM == 3 ? R : 0));
-            __syncthreads();  // B1: the previous plane is fully processed
+            __syncthreads();  // B2: phase P of this plane (and U of the previous) done
             if (flags[0]) { aborted = true; break; }
             producer_step(seq_base + jc);
-            const T* S = ring + (size_t)((seq_base + jc) % NS) * (C::SLOT_BYTES / sizeof(T));
-            T Fzp[NC];
-            // ---------------- phase P (MUSCL): predicted face states ----------------
-            if (SCHEME == SCHEME_MUSCL) {
-                constexpr int NPXr = ((C::NPX + 31) / 32) * 32;
-                constexpr int NPYr = ((C::NPY + 31) / 32) * 32;
-                for (int it = tid; it < NPXr + NPYr; it += NT) {
-                    if (it < NPXr) {
-                        if (it >= C::NPX) continue;
-                        const int cx = it % (TX + 2) - 1, cy = it / (TX + 2);
-                        T qm[NC], q[NC], qp[NC], L[NC], Rs[NC];
+            const T* S = plane_ptr(seq_base + jc);
+
+            // ---------------- phase F: face fluxes ----------------
+            if (DIM == 3 && !MUSCL) {
+                T qc[NC];
+                load_q(plane_ptr(seq_base + jc + 1), my_off, qc);
+                rusanov<T, DIM, 2 % DIM>(qa, qc, gamma, gm1, Fzp, chk, col_valid);
 #pragma unroll
-                        for (int m = 0; m < NC; ++m) {
-                            qm[m] = S[PV::idx(cx - 1, cy, m)];
-                            q[m] = S[PV::idx(cx, cy, m)];
-                            qp[m] = S[PV::idx(cx + 1, cy, m)];
-                        }
-                        const bool ok = muscl_states<T, DIM, 0>(qm, q, qp, gm1, half_dtdx[0], L, Rs);
-                        if (!ok && (x0 + cx <= g.n[0]) && (y0 + cy < g.n[1])) { bad = true; record_bad(ctl, BAD_PRED_X, x0 + cx, y0 + cy, z); }
+                for (int m = 0; m < NC; ++m) qb[m] = qc[m];
+            }
 #pragma unroll
-                        for (int m = 0; m < NC; ++m) {
-                            PL[m * (C::NPX + C::NPY) + it] = L[m];
-                            PR[m * (C::NPX + C::NPY) + it] = Rs[m];
-                        }
-                    } else {
-                        const int k = it - NPXr;
-                        if (k >= C::NPY) continue;
-                        const int cx = k % TX, cy = k / TX - 1;
-                        T qm[NC], q[NC], qp[NC], L[NC], Rs[NC];
-#pragma unroll
-                        for (int m = 0; m < NC; ++m) {
-                            qm[m] = S[PV::idx(cx, cy - 1, m)];
-                            q[m] = S[PV::idx(cx, cy, m)];
-                            qp[m] = S[PV::idx(cx, cy + 1, m)];
-                        }
-                        const bool ok = muscl_states<T, DIM, 1>(qm, q, qp, gm1, half_dtdx[1], L, Rs);
-                        if (!ok && (x0 + cx < g.n[0]) && (y0 + cy <= g.n[1])) { bad = true; record_bad(ctl, BAD_PRED_Y, x0 + cx, y0 + cy, z); }
-#pragma unroll
-                        for (int m = 0; m < NC; ++m) {
-                            PL[m * (C::NPX + C::NPY) + C::NPX + k] = L[m];
-                            PR[m * (C::NPX + C::NPY) + C::NPX + k] = Rs[m];
-                        }
-                    }
-                }
-                if (DIM == 3) {
-                    // z: predicted states of plane z+1 and the face z + 1/2
-                    const T* s1 = ring + (size_t)((seq_base + jc + 1) % NS) * (C::SLOT_BYTES / sizeof(T));
-                    const T* s2 = ring + (size_t)((seq_base + jc + 2) % NS) * (C::SLOT_BYTES / sizeof(T));
-                    T q0[NC], q1[NC], q2[NC], L[NC], Rn[NC];
+            for (int k = 0; k < KF; ++k) {
+                const unsigned kind = (f_bits >> (2 * k)) & 3u;
+                if (kind == 0u) continue;
+                const int it = tid + k * NT;
+                T a[NC], b[NC], F[NC];
+                if (MUSCL) {
+                    const int il = f_il[k], ir = il + (kind == 1u ? 1 : TX);
 #pragma unroll
                     for (int m = 0; m < NC; ++m) {
-                        const int id = PV::idx(lx, ly, m);
-                        q0[m] = S[id]; q1[m] = s1[id]; q2[m] = s2[id];
+                        a[m] = PR[m * NP + il];
+                        b[m] = PL[m * NP + ir];
                     }
-                    if (!muscl_states<T, DIM, 2 % DIM>(q0, q1, q2, gm1, half_dtdx[2], L, Rn) && col_valid) { bad = true; record_bad(ctl, BAD_PRED_Z, gx, gy, z + 1); }
-                    if (!rusanov<T, DIM, 2 % DIM>(zR, L, gamma, gm1, Fzp) && col_valid) { bad = true; record_bad(ctl, BAD_FACE_Z, gx, gy, z); }
-#pragma unroll
-                    for (int m = 0; m < NC; ++m) zR[m] = Rn[m];
+                } else {
+                    load_q(S, f_off[k], a);
+                    load_q(S, f_off[k] + (kind == 1u ? SX : SY), b);
                 }
-                __syncthreads();  // B2
-            } else if (DIM == 3) {
-                const T* s1 = ring + (size_t)((seq_base + jc + 1) % NS) * (C::SLOT_BYTES / sizeof(T));
-                T a[NC], b[NC];
+                const bool v = (f_bits >> (16 + k)) & 1u;
+                if (kind == 1u) rusanov<T, DIM, 0>(a, b, gamma, gm1, F, chk, v);
+                else rusanov<T, DIM, 1>(a, b, gamma, gm1, F, chk, v);
+                if (kind == 1u) {
 #pragma unroll
-                for (int m = 0; m < NC; ++m) { a[m] = S[PV::idx(lx, ly, m)]; b[m] = s1[PV::idx(lx, ly, m)]; }
-                if (!rusanov<T, DIM, 2 % DIM>(a, b, gamma, gm1, Fzp) && col_valid) { bad = true; record_bad(ctl, BAD_FACE_Z, gx, gy, z); }
-            }
-
-            // ---------------- phase F: x and y face fluxes ----------------
-            {
-                constexpr int NFXr = ((C::NFX + 31) / 32) * 32;
-                constexpr int NFYr = ((C::NFY + 31) / 32) * 32;
-                for (int it = tid; it < NFXr + NFYr; it += NT) {
-                    if (it < NFXr) {
-                        if (it >= C::NFX) continue;
-                        const int fx = it % (TX + 1), cy = it / (TX + 1);  // face between fx-1 and fx
-                        T a[NC], b[NC], F[NC];
-                        if (SCHEME == SCHEME_MUSCL) {
-                            const int il = cy * (TX + 2) + fx, ir = il + 1;
+                    for (int m = 0; m < NC; ++m) FX[m * C::NFX + it] = F[m];
+                } else {
 #pragma unroll
-                            for (int m = 0; m < NC; ++m) {
-                                a[m] = PR[m * (C::NPX + C::NPY) + il];
-                                b[m] = PL[m * (C::NPX + C::NPY) + ir];
-                            }
-                        } else {
-#pragma unroll
-                            for (int m = 0; m < NC; ++m) {
-                                a[m] = S[PV::idx(fx - 1, cy, m)];
-                                b[m] = S[PV::idx(fx, cy, m)];
-                            }
-                        }
-                        const bool ok = rusanov<T, DIM, 0>(a, b, gamma, gm1, F);
-                        if (!ok && (x0 + fx <= g.n[0]) && (y0 + cy < g.n[1])) { bad = true; record_bad(ctl, BAD_FACE_X, x0 + fx - 1, y0 + cy, z); }
-#pragma unroll
-                        for (int m = 0; m < NC; ++m) FX[m * C::NFX + it] = F[m];
-                    } else {
-                        const int k = it - NFXr;
-                        if (k >= C::NFY) continue;
-                        const int cx = k % TX, fy = k / TX;  // face between fy-1 and fy
-                        T a[NC], b[NC], F[NC];
-                        if (SCHEME == SCHEME_MUSCL) {
-                            const int il = C::NPX + fy * TX + cx, ir = il + TX;
-#pragma unroll
-                            for (int m = 0; m < NC; ++m) {
-                                a[m] = PR[m * (C::NPX + C::NPY) + il];
-                                b[m] = PL[m * (C::NPX + C::NPY) + ir];
-                            }
-                        } else {
-#pragma unroll
-                            for (int m = 0; m < NC; ++m) {
-                                a[m] = S[PV::idx(cx, fy - 1, m)];
-                                b[m] = S[PV::idx(cx, fy, m)];
-                            }
-                        }
-                        const bool ok = rusanov<T, DIM, 1>(a, b, gamma, gm1, F);
-                        if (!ok && (x0 + cx < g.n[0]) && (y0 + fy <= g.n[1])) { bad = true; record_bad(ctl, BAD_FACE_Y, x0 + cx, y0 + fy - 1, z); }
-#pragma unroll
-                        for (int m = 0; m < NC; ++m) FY[m * C::NFY + k] = F[m];
-                    }
+                    for (int m = 0; m < NC; ++m) FY[m * C::NFY + it - NFXr] = F[m];
                 }
             }
             __syncthreads();  // B3
@@ -602,6 +659,13 @@ __global__ void __launch_bounds__(TX * TY)
             // ---------------- phase U: conservative update + epilogue ----------------
             {
                 T* st = stage + (size_t)(out_count & 1) * (C::OUT_BYTES / sizeof(T));
+                T qc[NC];
+                if (DIM == 3) {
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) qc[m] = qa[m];
+                } else {
+                    load_q(S, my_off, qc);
+                }
                 T qn[NC];
 #pragma unroll
                 for (int m = 0; m < NC; ++m) {
@@ -612,7 +676,7 @@ __global__ void __launch_bounds__(TX * TY)
                     T acc = (fxp - fxm) * inv_dx[0];
                     acc += (fyp - fym) * inv_dx[1];
                     if (DIM == 3) acc += (Fzp[m] - Fzm[m]) * inv_dx[2];
-                    qn[m] = S[PV::idx(lx, ly, m)] - dtT * acc;
+                    qn[m] = qc[m] - dtT * acc;
                     if (tma_store_ok) {
                         if (LAYOUT == LAYOUT_SOA) st[(m * TY + ly) * TX + lx] = qn[m];
                         else st[(ly * TX + lx) * NC + m] = qn[m];
@@ -625,21 +689,39 @@ __global__ void __launch_bounds__(TX * TY)
                 }
                 if (DIM == 3) {
 #pragma unroll
-                    for (int m = 0; m < NC; ++m) Fzm[m] = Fzp[m];
+                    for (int m = 0; m < NC; ++m) {
+                        Fzm[m] = Fzp[m];
+                        qa[m] = qb[m];
+                        if (MUSCL) qb[m] = qz2[m];
+                    }
                 }
                 fence_proxy_async_smem();
                 if (col_valid) {
                     bool ok;
                     const T s = wave_sum<T, DIM>(qn, gamma, gm1, inv_dx, ok);
-                    if (!ok) { bad = true; record_bad(ctl, BAD_CELL, gx, gy, z); }
+                    if (!ok) {
+                        bad = true;
+                        record_bad(ctl, BAD_CELL, gx, gy, z);
+                    }
                     smax_local = fmax(smax_local, s);
-                    write_ghost_images<T, DIM>(out, g, prm.bc, gx, gy, z, qn);
+                    if (near_xy || (DIM == 3 && (z < g.h || z >= g.n[2] - g.h)))
+                        write_ghost_images<T, DIM>(out, g, prm.bc, gx, gy, z, qn);
+                }
+                if (!(chk > T(0))) {
+                    bad = true;
+                    record_bad(ctl, BAD_STATE, x0, y0, z);
+                    chk = T(1);
                 }
                 if (tma_store_ok) {
                     store_pending = true;
                     st_x = x0; st_y = y0; st_z = z; st_slot = out_count & 1;
                     ++out_count;
                 }
+            }
+            // ---------------- phase P of the next plane ----------------
+            if (DIM == 3 && zl + 1 < zn) {
+                wait_planes(seq_base + jc + 1 + R);
+                if (MUSCL) phase_p(jc + 1, z + 1);
             }
         }
         if (aborted) break;
@@ -654,7 +736,8 @@ __global__ void __launch_bounds__(TX * TY)
         if (aborted) {
             // loads still in flight complete into this CTA's shared memory:
             // wait for them (bounded) before the CTA exits
-            for (long long s = ready_upto; s < ld_seq; ++s) mbar_wait_bounded(&bars[s % NS], (uint32_t)((s / NS) & 1));
+            for (long long sq = ready_upto; sq < ld_seq; ++sq)
+                mbar_wait_bounded(&bars[sq % NS], (uint32_t)((sq / NS) & 1));
             atomicOr(&ctl->err, DEV_ERR_TIMEOUT);
         }
     }

@@ -187,13 +187,12 @@ static ripple_status map_dev_err(unsigned err, const FieldCtl* host = nullptr)
     if (err & DEV_ERR_NUMERIC) {
         std::string msg = "non-positive or NaN density/pressure produced";
         if (host && host->counters[4] > 0) {
-            static const char* stage[] = {"?", "x-predicted state", "y-predicted state", "z-predicted state",
-                                          "x-face state", "y-face state", "z-face state", "updated cell",
-                                          "input cell"};
             const long long c = host->counters[4];
-            msg += std::string(" (first at ") + stage[c >= 1 && c <= 8 ? c : 0] + " of cell (" +
-                   std::to_string(host->counters[5]) + ", " + std::to_string(host->counters[6]) + ", " +
-                   std::to_string(host->counters[7]) + "))";
+            const char* what = c == BAD_CELL    ? "updated cell"
+                               : c == BAD_INPUT ? "input cell"
+                                                : "reconstructed/predicted/face state in the tile starting at cell";
+            msg += std::string(" (first at ") + what + " (" + std::to_string(host->counters[5]) + ", " +
+                   std::to_string(host->counters[6]) + ", " + std::to_string(host->counters[7]) + "))";
         }
         return fail(RIPPLE_ERR_NUMERIC, msg);
     }
