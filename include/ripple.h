@@ -217,6 +217,89 @@ RIPPLE_API ripple_status ripple_eikonal_solve(ripple_field slowness, ripple_fiel
                                    int nsrc, const ripple_eik_params* params, ripple_eik_stats* stats);
 
 /* ------------------------------------------------------------------------ */
+/* Batched and served execution of independent 2D problems.                  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The paper runs one problem per graph (Section 6 scheduling); this runtime
+ * serves many independent problems at once, which the paper does not do.
+ * Requests are admitted while their device memory fits the context budget,
+ * stay resident until done, and every resident problem advances in ONE launch
+ * per global step: a flat work queue over the tiles of all resident problems,
+ * each problem with its own dt (Euler) or iteration counter (eikonal).  New
+ * requests join while others run (continuous batching).  A scheduler thread
+ * per context drives the GPU on its own streams; submit / poll / wait are
+ * thread-safe.
+ */
+typedef enum { RIPPLE_REQ_EULER = 0, RIPPLE_REQ_EIKONAL = 1 } ripple_request_kind;
+
+typedef struct {
+    int kind;                 /* ripple_request_kind */
+    int64_t dims[2];          /* 2D grid (nx, ny) */
+    const void* input;        /* HOST: Euler conserved state (4 components, SoA, dtype of the batch) or
+                                 eikonal slowness (1 component); read until the request is admitted */
+    void* output;             /* HOST: final Euler state / eikonal travel times, same shape; written
+                                 before the ticket completes */
+    ripple_fv_params fv;      /* Euler: gamma, cfl, dx, bc; scheme must be RIPPLE_RUSANOV1 */
+    int64_t nsteps;           /* Euler: steps to run (>= 1) */
+    ripple_eik_params eik;    /* eikonal: h, tol, max_iters */
+    const int64_t* sources;   /* eikonal: nsrc (x, y) cell pairs, copied by ripple_batch_submit */
+    int nsrc;
+} ripple_request;
+
+typedef struct {
+    ripple_status status;     /* RIPPLE_OK, _NUMERIC, _TIMEOUT (eikonal cap), _BUDGET (never fits), ... */
+    double submit_s, admit_s, start_s, finish_s;  /* runtime clock (seconds since the runtime started) */
+    int64_t work;             /* Euler steps / eikonal FIM iterations */
+    int64_t tile_visits, cell_updates;            /* eikonal work counters */
+    double t;                 /* Euler: simulated time reached */
+} ripple_ticket_info;
+
+typedef struct {
+    ripple_layout layout;     /* layout of resident Euler states */
+    int tile_variant;         /* 0: 32x8, 1: 64x4, 2: 16x16 Euler tiles */
+    int steps_per_sync;       /* global steps queued between scheduler checks (latency vs overhead) */
+    int use_graphs;           /* replay queued steps from captured CUDA graphs */
+    ripple_dtype dtype;       /* element type of every request of this context */
+} ripple_batch_config;
+
+typedef struct {
+    int64_t submitted, admitted, completed, failed;
+    int64_t global_steps, launches, graph_replays;
+    double now_s;             /* runtime clock now */
+} ripple_batch_stats;
+
+/* Set the batch configuration (defaults: SoA, 32x8, 8 steps per sync, graphs
+ * on, F32).  Only while no request is in flight. */
+RIPPLE_API ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* cfg);
+
+/* Queue n requests; tickets_out[i] identifies request i.  Validates every
+ * request first (RIPPLE_ERR_INVALID queues nothing).  Never blocks on the GPU. */
+RIPPLE_API ripple_status ripple_batch_submit(ripple_ctx ctx, const ripple_request* reqs, int n,
+                                             uint64_t* tickets_out);
+
+/* RIPPLE_OK and *info filled (ticket retired) once the request finished,
+ * RIPPLE_ERR_NOT_READY while it runs, RIPPLE_ERR_INVALID for an unknown ticket.
+ * The request's own outcome is info->status. */
+RIPPLE_API ripple_status ripple_poll(ripple_ctx ctx, uint64_t ticket, ripple_ticket_info* info);
+
+/* Block until the request finished (RIPPLE_OK, *info filled, ticket retired) or
+ * timeout_ms passed (RIPPLE_ERR_TIMEOUT; timeout_ms < 0 waits forever). */
+RIPPLE_API ripple_status ripple_wait(ripple_ctx ctx, uint64_t ticket, int64_t timeout_ms, ripple_ticket_info* info);
+
+RIPPLE_API ripple_status ripple_batch_get_stats(ripple_ctx ctx, ripple_batch_stats* out);
+
+/*
+ * Autotuner: time the batched step for each layout (SoA, AoS) and tile shape
+ * on n sample Euler problems of the given square sides (dtype `dtype`), and
+ * return the fastest in *chosen (other fields of *chosen are kept).
+ * ms_per_step (nullable) receives 2 x 3 timings, SoA first.  Does not change
+ * the context's configuration (pass *chosen to ripple_batch_configure).
+ */
+RIPPLE_API ripple_status ripple_batch_autotune(ripple_ctx ctx, const int64_t* sides, int n, ripple_dtype dtype,
+                                               ripple_batch_config* chosen, double* ms_per_step);
+
+/* ------------------------------------------------------------------------ */
 /* Conserved totals for callers that cannot allocate device memory.          */
 /* ------------------------------------------------------------------------ */
 

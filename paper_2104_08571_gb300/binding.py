@@ -75,6 +75,32 @@ class ripple_field_desc(ctypes.Structure):
 _VP = ctypes.c_void_p
 _I64P = ctypes.POINTER(ctypes.c_int64)
 
+RIPPLE_REQ_EULER = 0
+RIPPLE_REQ_EIKONAL = 1
+
+
+class ripple_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dims", ctypes.c_int64 * 2), ("input", ctypes.c_void_p),
+                ("output", ctypes.c_void_p), ("fv", ripple_fv_params), ("nsteps", ctypes.c_int64),
+                ("eik", ripple_eik_params), ("sources", _I64P), ("nsrc", ctypes.c_int)]
+
+
+class ripple_ticket_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("submit_s", ctypes.c_double), ("admit_s", ctypes.c_double),
+                ("start_s", ctypes.c_double), ("finish_s", ctypes.c_double), ("work", ctypes.c_int64),
+                ("tile_visits", ctypes.c_int64), ("cell_updates", ctypes.c_int64), ("t", ctypes.c_double)]
+
+
+class ripple_batch_config(ctypes.Structure):
+    _fields_ = [("layout", ctypes.c_int), ("tile_variant", ctypes.c_int), ("steps_per_sync", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("dtype", ctypes.c_int)]
+
+
+class ripple_batch_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("global_steps", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("graph_replays", ctypes.c_int64), ("now_s", ctypes.c_double)]
+
 # name -> (argtypes) ; every ABI function returns ripple_status (int)
 _SIGNATURES = {
     "ripple_ctx_create": [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_VP)],
@@ -95,6 +121,13 @@ _SIGNATURES = {
     "ripple_eikonal_solve": [_VP, _VP, _I64P, ctypes.c_int, ctypes.POINTER(ripple_eik_params),
                              ctypes.POINTER(ripple_eik_stats)],
     "ripple_totals_noalloc": [_VP, ctypes.c_int, _I64P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP],
+    "ripple_batch_configure": [_VP, ctypes.POINTER(ripple_batch_config)],
+    "ripple_batch_submit": [_VP, ctypes.POINTER(ripple_request), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)],
+    "ripple_poll": [_VP, ctypes.c_uint64, ctypes.POINTER(ripple_ticket_info)],
+    "ripple_wait": [_VP, ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ripple_ticket_info)],
+    "ripple_batch_get_stats": [_VP, ctypes.POINTER(ripple_batch_stats)],
+    "ripple_batch_autotune": [_VP, _I64P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ripple_batch_config),
+                              ctypes.POINTER(ctypes.c_double)],
 }
 _STRING_FUNCS = ["ripple_last_error", "ripple_version"]
 
@@ -313,3 +346,109 @@ def ripple_totals_noalloc(state, dims, ncomp, layout, dtype, totals_out, stream=
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     _check(load().ripple_totals_noalloc(_VP(state.data_ptr()), len(dims), d, int(ncomp), int(layout), int(dtype),
                                         _VP(totals_out.data_ptr()), handle), "ripple_totals_noalloc")
+
+
+# ---------------------------------------------------------------------------
+# batched / served execution
+# ---------------------------------------------------------------------------
+_inflight = {}  # ticket -> (input array, output array, sources): kept alive until retired
+
+
+def _info_dict(info):
+    return dict(status=info.status, submit_s=info.submit_s, admit_s=info.admit_s, start_s=info.start_s,
+                finish_s=info.finish_s, work=info.work, tile_visits=info.tile_visits,
+                cell_updates=info.cell_updates, t=info.t)
+
+
+def ripple_batch_configure(ctx, layout=RIPPLE_SOA, tile_variant=0, steps_per_sync=8, use_graphs=True,
+                           dtype=RIPPLE_F32):
+    cfg = ripple_batch_config(int(layout), int(tile_variant), int(steps_per_sync), int(bool(use_graphs)), int(dtype))
+    _check(load().ripple_batch_configure(ctx, ctypes.byref(cfg)), "ripple_batch_configure")
+
+
+def euler_request(U, nsteps, dx, gamma=1.4, cfl=0.4, bc=RIPPLE_BC_PERIODIC, out=None):
+    """A 2D Euler request from a component-major host array U (4, ny, nx)."""
+    U = np.ascontiguousarray(U)
+    out = np.empty_like(U) if out is None else out
+    return dict(kind=RIPPLE_REQ_EULER, input=U, output=out, nsteps=int(nsteps), dx=list(dx), gamma=gamma,
+                cfl=cfl, bc=bc)
+
+
+def eikonal_request(s, sources, h, tol=1e-6, max_iters=0, out=None):
+    """A 2D eikonal request from a host slowness array s (ny, nx) and (x, y) sources."""
+    s = np.ascontiguousarray(s)
+    out = np.empty_like(s) if out is None else out
+    return dict(kind=RIPPLE_REQ_EIKONAL, input=s, output=out, sources=[tuple(c) for c in sources], h=h, tol=tol,
+                max_iters=max_iters)
+
+
+def ripple_batch_submit(ctx, requests):
+    """Queue request dicts (see euler_request / eikonal_request); returns tickets."""
+    n = len(requests)
+    arr = (ripple_request * n)()
+    keep = []
+    for i, r in enumerate(requests):
+        inp, outp = r["input"], r["output"]
+        ny, nx = inp.shape[-2], inp.shape[-1]
+        arr[i].kind = r["kind"]
+        arr[i].dims[0] = nx
+        arr[i].dims[1] = ny
+        arr[i].input = inp.ctypes.data
+        arr[i].output = outp.ctypes.data
+        src = None
+        if r["kind"] == RIPPLE_REQ_EULER:
+            arr[i].fv = make_fv_params(r["dx"], gamma=r.get("gamma", 1.4), cfl=r.get("cfl", 0.4),
+                                       scheme=RIPPLE_RUSANOV1, bc=r.get("bc", RIPPLE_BC_PERIODIC))
+            arr[i].nsteps = r["nsteps"]
+        else:
+            flat = [int(c) for xy in r["sources"] for c in xy]
+            src = (ctypes.c_int64 * len(flat))(*flat)
+            arr[i].sources = src
+            arr[i].nsrc = len(r["sources"])
+            arr[i].eik = ripple_eik_params(float(r["h"]), float(r.get("tol", 1e-6)), int(r.get("max_iters", 0)))
+        keep.append((inp, outp, src))
+    tickets = (ctypes.c_uint64 * n)()
+    _check(load().ripple_batch_submit(ctx, arr, n, tickets), "ripple_batch_submit")
+    out = [int(t) for t in tickets]
+    for t, k in zip(out, keep):
+        _inflight[t] = k
+    return out
+
+
+def ripple_poll(ctx, ticket):
+    """Info dict once the request finished (the ticket is retired), else None."""
+    info = ripple_ticket_info()
+    st = load().ripple_poll(ctx, ctypes.c_uint64(ticket), ctypes.byref(info))
+    if st == RIPPLE_ERR_NOT_READY:
+        return None
+    _check(st, "ripple_poll")
+    _inflight.pop(ticket, None)
+    return _info_dict(info)
+
+
+def ripple_wait(ctx, ticket, timeout_ms=-1):
+    info = ripple_ticket_info()
+    _check(load().ripple_wait(ctx, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(info)), "ripple_wait")
+    _inflight.pop(ticket, None)
+    return _info_dict(info)
+
+
+def ripple_batch_get_stats(ctx):
+    st = ripple_batch_stats()
+    _check(load().ripple_batch_get_stats(ctx, ctypes.byref(st)), "ripple_batch_get_stats")
+    return {f: getattr(st, f) for f, _ in ripple_batch_stats._fields_}
+
+
+def ripple_batch_autotune(ctx, sides, dtype=RIPPLE_F32):
+    """Returns (chosen config dict, {(layout, variant): ms per global step})."""
+    arr = (ctypes.c_int64 * len(sides))(*[int(x) for x in sides])
+    cfg = ripple_batch_config(RIPPLE_SOA, 0, 8, 1, int(dtype))
+    ms = (ctypes.c_double * 6)()
+    _check(load().ripple_batch_autotune(ctx, arr, len(sides), int(dtype), ctypes.byref(cfg), ms),
+           "ripple_batch_autotune")
+    timings = {}
+    for li, lay in enumerate((RIPPLE_SOA, RIPPLE_AOS)):
+        for v in range(3):
+            timings[(lay, v)] = ms[li * 3 + v]
+    return dict(layout=cfg.layout, tile_variant=cfg.tile_variant, steps_per_sync=cfg.steps_per_sync,
+                use_graphs=cfg.use_graphs, dtype=cfg.dtype), timings

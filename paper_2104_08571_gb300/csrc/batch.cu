@@ -1,4 +1,970 @@
-// Batched and served execution (filled in by the batch runtime).
+// Batched and served execution of many independent 2D problems (Euler and
+// eikonal) on one GPU: admission by device-memory budget, resident state,
+// continuous batching of every resident problem into one launch per global
+// step, and completion tickets with timestamps.  The paper has no counterpart
+// (its scheduler runs one graph; this runtime replaces a request loop).
+//
+// A scheduler thread per context owns two streams: the compute stream runs the
+// batched step kernel (batch_kernels.cuh) K global steps at a time (optionally
+// replayed from a CUDA graph), the copy stream runs admissions (host -> device
+// copy, layout scatter, padding fill / FIM initialisation) and completions
+// (device -> host gather and copy).  Device memory comes from the stream-ordered
+// pool (cudaMallocAsync / cudaFreeAsync on the copy stream), counted against
+// the context budget: a request waits while its memory does not fit, so
+// problems join and leave the resident set while others keep running.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <unordered_map>
+
+#include "batch_kernels.cuh"
 #include "runtime.h"
 
-void batch_runtime_destroy(ripple_ctx) {}
+namespace ripple {
+
+template <typename T>
+cudaError_t launch_fim_init(const FimProblem<T>& a, int ts, int grid, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Kernel table (tile shapes are the autotuner's candidates).
+// ---------------------------------------------------------------------------
+struct BatchTileShape {
+    int tx, ty;
+};
+constexpr int kNumBatchVariants = 3;
+constexpr BatchTileShape kBatchVariants[kNumBatchVariants] = {{32, 8}, {64, 4}, {16, 16}};
+
+template <typename T, int LAYOUT, int V>
+static cudaError_t step_v(int grid, cudaStream_t s, const BatchEuler* e, const void* f, const int* table,
+                          BatchCtl* c)
+{
+    constexpr int TX = kBatchVariants[V].tx, TY = kBatchVariants[V].ty;
+    batch_step_kernel<T, LAYOUT, TX, TY><<<grid, 256, 0, s>>>(e, static_cast<const BatchFim<T>*>(f), table, c);
+    return cudaGetLastError();
+}
+template <typename T, int LAYOUT, int V>
+static int occ_v()
+{
+    constexpr int TX = kBatchVariants[V].tx, TY = kBatchVariants[V].ty;
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<T, LAYOUT, TX, TY>, 256, 0);
+    return n;
+}
+template <typename T, int LAYOUT>
+static cudaError_t step_l(int v, int grid, cudaStream_t s, const BatchEuler* e, const void* f, const int* t,
+                          BatchCtl* c)
+{
+    if (v == 1) return step_v<T, LAYOUT, 1>(grid, s, e, f, t, c);
+    if (v == 2) return step_v<T, LAYOUT, 2>(grid, s, e, f, t, c);
+    return step_v<T, LAYOUT, 0>(grid, s, e, f, t, c);
+}
+static cudaError_t launch_batch_step(ripple_dtype dt, int layout, int v, int grid, cudaStream_t s,
+                                     const BatchEuler* e, const void* f, const int* t, BatchCtl* c)
+{
+    if (dt == RIPPLE_F32)
+        return layout == LAYOUT_SOA ? step_l<float, LAYOUT_SOA>(v, grid, s, e, f, t, c)
+                                    : step_l<float, LAYOUT_AOS>(v, grid, s, e, f, t, c);
+    return layout == LAYOUT_SOA ? step_l<double, LAYOUT_SOA>(v, grid, s, e, f, t, c)
+                                : step_l<double, LAYOUT_AOS>(v, grid, s, e, f, t, c);
+}
+static int batch_occupancy(ripple_dtype dt, int layout, int v)
+{
+    auto pick = [&](auto tag) -> int {
+        using T = decltype(tag);
+        if (layout == LAYOUT_SOA) return v == 1 ? occ_v<T, LAYOUT_SOA, 1>() : v == 2 ? occ_v<T, LAYOUT_SOA, 2>() : occ_v<T, LAYOUT_SOA, 0>();
+        return v == 1 ? occ_v<T, LAYOUT_AOS, 1>() : v == 2 ? occ_v<T, LAYOUT_AOS, 2>() : occ_v<T, LAYOUT_AOS, 0>();
+    };
+    return dt == RIPPLE_F32 ? pick(0.0f) : pick(0.0);
+}
+
+// Fill a uniform admissible Euler state (autotuner sample problems).
+template <typename T>
+__global__ void fill_uniform_euler(T* buf, const FieldGeom g)
+{
+    const long long total = (long long)g.px * g.py;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
+         c += (long long)gridDim.x * blockDim.x) {
+        const T q[4] = {T(1), T(0.5), T(0.25), T(2.65625)};
+        for (int m = 0; m < 4; ++m) buf[c * g.cell_stride + m * g.comp_stride] = q[m];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Runtime state
+// ---------------------------------------------------------------------------
+using Clock = std::chrono::steady_clock;
+
+constexpr int kSlots = 4096;  // concurrent problems (admitted, resident or completing)
+
+struct Inst {
+    uint64_t ticket = 0;
+    ripple_request req{};
+    std::vector<int64_t> src;
+    FieldGeom g{}, gs{};
+    size_t buf_bytes = 0, sbuf_bytes = 0, scratch_bytes = 0, total_bytes = 0;
+    void* buf[2] = {nullptr, nullptr};
+    void* sbuf = nullptr;
+    void* scratch = nullptr;
+    int slot = -1;
+    int ntiles = 0, tiles_x = 0, ntx = 0, nty = 0;
+    long long start_step = -1;
+    cudaEvent_t ev = nullptr;
+    ripple_status result = RIPPLE_OK;
+    double t_submit = 0, t_admit = 0, t_start = 0, t_finish = 0;
+};
+
+struct Ticket {
+    bool done = false;
+    ripple_ticket_info info{};
+};
+
+struct BatchRuntime {
+    ripple_ctx ctx = nullptr;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    std::deque<Inst*> pending;                      // guarded by mu
+    std::unordered_map<uint64_t, Ticket> tickets;   // guarded by mu
+    uint64_t next_ticket = 1;                       // guarded by mu
+    ripple_batch_config cfg{RIPPLE_SOA, 0, 8, 1, RIPPLE_F32};
+    ripple_batch_stats stats{};                     // guarded by mu
+    Clock::time_point epoch = Clock::now();
+    // scheduler-thread state
+    std::vector<Inst*> uploading, resident, downloading;
+    cudaStream_t compute = nullptr, copy = nullptr;
+    cudaEvent_t ev_step = nullptr;
+    bool started = false;
+    // slot arrays: device, and pinned mirrors of status/counters/ctl
+    FieldCtl* slot_ctl = nullptr;
+    unsigned long long* slot_status = nullptr;
+    long long* slot_counters = nullptr;
+    FieldCtl* h_ctl = nullptr;
+    unsigned long long* h_status = nullptr;
+    long long* h_counters = nullptr;
+    std::vector<int> free_slots;
+    // tables
+    BatchEuler* d_euler = nullptr;
+    void* d_fim = nullptr;
+    int* d_table = nullptr;
+    BatchCtl* d_bctl = nullptr;
+    BatchEuler* h_euler = nullptr;
+    void* h_fim = nullptr;
+    int* h_table = nullptr;
+    int cap_e = 0, cap_f = 0, cap_t = 0;
+    bool dirty = true;
+    long long gstep = 0;  // global steps issued (== device counter after completion)
+    int grid = 0;
+    std::map<int, cudaGraphExec_t> graphs;
+    int graph_variant = -1, graph_layout = -1;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - epoch).count(); }
+};
+
+static size_t fim_elem_size(ripple_dtype d) { return d == RIPPLE_F64 ? sizeof(BatchFim<double>) : sizeof(BatchFim<float>); }
+
+static ripple_status rt_alloc(BatchRuntime* rt, size_t bytes, void** p)
+{
+    bytes = (bytes + 255) / 256 * 256;
+    if (!budget_reserve(rt->ctx, bytes)) return RIPPLE_ERR_BUDGET;
+    cudaError_t e = cudaMallocAsync(p, bytes, rt->copy);
+    if (e != cudaSuccess) {
+        rt->ctx->used -= bytes;
+        *p = nullptr;
+        return cuda_fail(e, "cudaMallocAsync");
+    }
+    return RIPPLE_OK;
+}
+
+static void rt_free(BatchRuntime* rt, void* p, size_t bytes)
+{
+    if (!p) return;
+    bytes = (bytes + 255) / 256 * 256;
+    cudaFreeAsync(p, rt->copy);
+    rt->ctx->used -= bytes;
+}
+
+static ripple_status rt_start(BatchRuntime* rt);
+
+static void finish(BatchRuntime* rt, Inst* in, ripple_status st)
+{
+    in->result = st;
+    in->t_finish = rt->now();
+    std::lock_guard<std::mutex> lk(rt->mu);
+    Ticket& tk = rt->tickets[in->ticket];
+    tk.done = true;
+    tk.info.status = st;
+    tk.info.submit_s = in->t_submit;
+    tk.info.admit_s = in->t_admit;
+    tk.info.start_s = in->t_start;
+    tk.info.finish_s = in->t_finish;
+    if (in->slot >= 0) {
+        if (in->req.kind == RIPPLE_REQ_EULER) {
+            tk.info.work = in->req.nsteps;
+            tk.info.t = rt->h_ctl[in->slot].t;
+        } else {
+            tk.info.work = rt->h_counters[in->slot * 3 + 0];
+            tk.info.tile_visits = rt->h_counters[in->slot * 3 + 1];
+            tk.info.cell_updates = rt->h_counters[in->slot * 3 + 2];
+        }
+    }
+    if (st == RIPPLE_OK) rt->stats.completed++;
+    else rt->stats.failed++;
+    rt->cv_done.notify_all();
+}
+
+// Free everything an instance holds (stream-ordered after its last use).
+static void release(BatchRuntime* rt, Inst* in)
+{
+    rt_free(rt, in->buf[0], in->buf_bytes);
+    rt_free(rt, in->buf[1], in->buf_bytes);
+    rt_free(rt, in->sbuf, in->sbuf_bytes);
+    rt_free(rt, in->scratch, in->scratch_bytes);
+    in->buf[0] = in->buf[1] = in->sbuf = in->scratch = nullptr;
+    if (in->slot >= 0) rt->free_slots.push_back(in->slot);
+    if (in->ev) cudaEventDestroy(in->ev);
+    in->ev = nullptr;
+}
+
+template <typename T>
+static FimProblem<T> fim_problem(const Inst* in)
+{
+    FimProblem<T> a{};
+    a.buf[0] = static_cast<T*>(in->buf[0]);
+    a.buf[1] = static_cast<T*>(in->buf[1]);
+    a.slow = static_cast<const T*>(in->sbuf);
+    a.gT = in->g;
+    a.gS = in->gs;
+    a.ntx = in->ntx;
+    a.nty = in->nty;
+    a.ntz = 1;
+    a.ntiles = in->ntiles;
+    a.nsrc = (int)(in->src.size() / 2);
+    for (int q = 0; q < a.nsrc; ++q) {
+        a.src[q][0] = (int)in->src[2 * q];
+        a.src[q][1] = (int)in->src[2 * q + 1];
+        a.src[q][2] = 0;
+    }
+    a.h = in->req.eik.h;
+    a.tol = in->req.eik.tol;
+    char* base = static_cast<char*>(in->scratch);
+    a.count = reinterpret_cast<unsigned*>(base);
+    a.act = reinterpret_cast<unsigned*>(base + 64);
+    a.cur = reinterpret_cast<unsigned char*>(base + 64 + (size_t)in->ntiles * 12);
+    return a;
+}
+
+// Allocate and queue the upload of one request.  RIPPLE_ERR_BUDGET: does not fit now.
+static ripple_status admit(BatchRuntime* rt, Inst* in)
+{
+    const ripple_request& r = in->req;
+    const ripple_dtype dt = rt->cfg.dtype;
+    const size_t es = elem_size(dt);
+    const int64_t dims[2] = {r.dims[0], r.dims[1]};
+    const size_t dense = (size_t)dims[0] * dims[1] * es * (r.kind == RIPPLE_REQ_EULER ? 4 : 1);
+    if (r.kind == RIPPLE_REQ_EULER) {
+        in->g = make_field_geom(2, dims, 4, rt->cfg.layout, 1, dt, &in->buf_bytes);
+        in->tiles_x = (int)((dims[0] + kBatchVariants[rt->cfg.tile_variant].tx - 1) /
+                            kBatchVariants[rt->cfg.tile_variant].tx);
+        const int ty = (int)((dims[1] + kBatchVariants[rt->cfg.tile_variant].ty - 1) /
+                             kBatchVariants[rt->cfg.tile_variant].ty);
+        in->ntiles = in->tiles_x * ty;
+        in->total_bytes = 2 * ((in->buf_bytes + 255) / 256 * 256);
+    } else {
+        in->g = make_field_geom(2, dims, 1, RIPPLE_SOA, 0, dt, &in->buf_bytes);
+        in->gs = make_field_geom(2, dims, 1, RIPPLE_SOA, 0, dt, &in->sbuf_bytes);
+        constexpr int TS = EikTile<2>::TS;
+        in->ntx = (int)((dims[0] + TS - 1) / TS);
+        in->nty = (int)((dims[1] + TS - 1) / TS);
+        in->ntiles = in->ntx * in->nty;
+        in->scratch_bytes = 64 + (size_t)in->ntiles * 14;
+        in->total_bytes = 2 * ((in->buf_bytes + 255) / 256 * 256) + (in->sbuf_bytes + 255) / 256 * 256 +
+                          (in->scratch_bytes + 255) / 256 * 256;
+    }
+    if (dense > in->buf_bytes) return fail(RIPPLE_ERR_INTERNAL, "staging buffer too small");
+    if (rt->free_slots.empty()) return RIPPLE_ERR_BUDGET;
+    if (rt->ctx->budget && in->total_bytes > rt->ctx->budget)
+        return fail(RIPPLE_ERR_BUDGET, "request larger than the whole memory budget");
+    ripple_status st = rt_alloc(rt, in->buf_bytes, &in->buf[0]);
+    if (st == RIPPLE_OK) st = rt_alloc(rt, in->buf_bytes, &in->buf[1]);
+    if (st == RIPPLE_OK && r.kind == RIPPLE_REQ_EIKONAL) {
+        st = rt_alloc(rt, in->sbuf_bytes, &in->sbuf);
+        if (st == RIPPLE_OK) st = rt_alloc(rt, in->scratch_bytes, &in->scratch);
+    }
+    if (st != RIPPLE_OK) {
+        rt_free(rt, in->buf[0], in->buf_bytes);
+        rt_free(rt, in->buf[1], in->buf_bytes);
+        rt_free(rt, in->sbuf, in->sbuf_bytes);
+        rt_free(rt, in->scratch, in->scratch_bytes);
+        in->buf[0] = in->buf[1] = in->sbuf = in->scratch = nullptr;
+        return st;
+    }
+    in->slot = rt->free_slots.back();
+    rt->free_slots.pop_back();
+    cudaStream_t s = rt->copy;
+    const long long total = dims[0] * dims[1];
+    const int grid = (int)std::min<long long>((total + 255) / 256, 4LL * rt->ctx->sm_count);
+    RIPPLE_CUDA(cudaEventCreateWithFlags(&in->ev, cudaEventDisableTiming));
+    // the second buffer is the dense staging area of the upload
+    RIPPLE_CUDA(cudaMemcpyAsync(in->buf[1], r.input, dense, cudaMemcpyHostToDevice, s));
+    RIPPLE_CUDA(cudaMemsetAsync(&rt->slot_ctl[in->slot], 0, sizeof(FieldCtl), s));
+    RIPPLE_CUDA(cudaMemsetAsync(&rt->slot_status[in->slot], 0, sizeof(unsigned long long), s));
+    RIPPLE_CUDA(cudaMemsetAsync(&rt->slot_counters[in->slot * 3], 0, 3 * sizeof(long long), s));
+    if (r.kind == RIPPLE_REQ_EULER) {
+        RIPPLE_CUDA(cudaMemsetAsync(in->buf[0], 0, in->buf_bytes, s));
+        RIPPLE_CUDA(launch_interior_copy(dt, in->buf[0], in->g, in->buf[1], LAYOUT_SOA, 0, grid, s));
+        const double inv_dx[3] = {1.0 / r.fv.dx[0], 1.0 / r.fv.dx[1], 0.0};
+        RIPPLE_CUDA(launch_prep(dt, 2, in->buf[0], &rt->slot_ctl[in->slot], in->g, (int)r.fv.bc, r.fv.gamma, inv_dx,
+                                0, grid, s));
+    } else {
+        RIPPLE_CUDA(launch_interior_copy(dt, in->sbuf, in->gs, in->buf[1], LAYOUT_SOA, 0, grid, s));
+        RIPPLE_CUDA(cudaMemsetAsync(in->scratch, 0, in->scratch_bytes, s));
+        if (dt == RIPPLE_F32) RIPPLE_CUDA(launch_fim_init<float>(fim_problem<float>(in), EikTile<2>::TS, grid, s));
+        else RIPPLE_CUDA(launch_fim_init<double>(fim_problem<double>(in), EikTile<2>::TS, grid, s));
+    }
+    RIPPLE_CUDA(cudaEventRecord(in->ev, s));
+    in->t_admit = rt->now();
+    return RIPPLE_OK;
+}
+
+// Queue the download of a finished instance (after the compute work recorded in ev_step).
+static ripple_status start_download(BatchRuntime* rt, Inst* in)
+{
+    const ripple_request& r = in->req;
+    const ripple_dtype dt = rt->cfg.dtype;
+    cudaStream_t s = rt->copy;
+    RIPPLE_CUDA(cudaStreamWaitEvent(s, rt->ev_step, 0));
+    const long long total = r.dims[0] * r.dims[1];
+    const int grid = (int)std::min<long long>((total + 255) / 256, 4LL * rt->ctx->sm_count);
+    const size_t dense = (size_t)total * elem_size(dt) * (r.kind == RIPPLE_REQ_EULER ? 4 : 1);
+    void* fin = in->buf[0];
+    void* stage = in->buf[1];
+    if (r.kind == RIPPLE_REQ_EULER && (r.nsteps & 1)) {
+        fin = in->buf[1];
+        stage = in->buf[0];
+    }
+    RIPPLE_CUDA(launch_interior_copy(dt, fin, in->g, stage, LAYOUT_SOA, 1, grid, s));
+    RIPPLE_CUDA(cudaMemcpyAsync(r.output, stage, dense, cudaMemcpyDeviceToHost, s));
+    RIPPLE_CUDA(cudaMemcpyAsync(&rt->h_ctl[in->slot], &rt->slot_ctl[in->slot], sizeof(FieldCtl),
+                                cudaMemcpyDeviceToHost, s));
+    RIPPLE_CUDA(cudaEventRecord(in->ev, s));
+    return RIPPLE_OK;
+}
+
+template <typename T>
+static void fill_fim_desc(BatchRuntime* rt, Inst* in, void* h_fim, int idx)
+{
+    BatchFim<T>* f = static_cast<BatchFim<T>*>(h_fim) + idx;
+    f->p = fim_problem<T>(in);
+    f->tile_begin = 0;
+    f->start_step = in->start_step;
+    f->max_iters = in->req.eik.max_iters > 0 ? in->req.eik.max_iters : 1000000;
+    f->status = &rt->slot_status[in->slot];
+    f->counters = &rt->slot_counters[in->slot * 3];
+}
+
+static ripple_status grow(BatchRuntime* rt, int ne, int nf, int nt)
+{
+    auto regrow = [&](int need, int& cap, size_t esz, void** d, void** h) -> ripple_status {
+        if (need <= cap) return RIPPLE_OK;
+        int nc = std::max(need, std::max(64, cap * 2));
+        RIPPLE_CUDA(cudaStreamSynchronize(rt->compute));
+        if (*d) cudaFree(*d);
+        if (*h) cudaFreeHost(*h);
+        *d = nullptr;
+        *h = nullptr;
+        RIPPLE_CUDA(cudaMalloc(d, (size_t)nc * esz));
+        RIPPLE_CUDA(cudaMallocHost(h, (size_t)nc * esz));
+        cap = nc;
+        for (auto& g : rt->graphs) cudaGraphExecDestroy(g.second);
+        rt->graphs.clear();
+        return RIPPLE_OK;
+    };
+    ripple_status st = regrow(ne, rt->cap_e, sizeof(BatchEuler), reinterpret_cast<void**>(&rt->d_euler),
+                              reinterpret_cast<void**>(&rt->h_euler));
+    if (st == RIPPLE_OK) st = regrow(nf, rt->cap_f, fim_elem_size(rt->cfg.dtype), &rt->d_fim, &rt->h_fim);
+    if (st == RIPPLE_OK)
+        st = regrow(nt, rt->cap_t, sizeof(int), reinterpret_cast<void**>(&rt->d_table),
+                    reinterpret_cast<void**>(&rt->h_table));
+    return st;
+}
+
+// Rebuild the descriptor arrays and the tile table of the resident set.
+static ripple_status rebuild_tables(BatchRuntime* rt)
+{
+    int ne = 0, nf = 0, nt = 0;
+    for (Inst* in : rt->resident) {
+        if (in->req.kind == RIPPLE_REQ_EULER) ++ne;
+        else ++nf;
+        nt += in->ntiles;
+    }
+    ripple_status st = grow(rt, std::max(ne, 1), std::max(nf, 1), std::max(nt, 1));
+    if (st != RIPPLE_OK) return st;
+    // the previous launches may still read the pinned mirrors' device copies:
+    // the compute stream is idle here (the scheduler synchronises every K steps)
+    int ie = 0, jf = 0, t = 0;
+    for (Inst* in : rt->resident) {
+        if (in->req.kind == RIPPLE_REQ_EULER) {
+            BatchEuler& e = rt->h_euler[ie];
+            e.buf[0] = in->buf[0];
+            e.buf[1] = in->buf[1];
+            e.ctl = &rt->slot_ctl[in->slot];
+            e.g = in->g;
+            e.tiles_x = in->tiles_x;
+            e.tile_begin = t;
+            e.bc = (int)in->req.fv.bc;
+            e.start_step = in->start_step;
+            e.nsteps = in->req.nsteps;
+            e.gamma = in->req.fv.gamma;
+            e.cfl = in->req.fv.cfl;
+            e.inv_dx0 = 1.0 / in->req.fv.dx[0];
+            e.inv_dx1 = 1.0 / in->req.fv.dx[1];
+            for (int k = 0; k < in->ntiles; ++k) rt->h_table[t + k] = (ie << 1) | 0;
+            ++ie;
+        } else {
+            if (rt->cfg.dtype == RIPPLE_F32) fill_fim_desc<float>(rt, in, rt->h_fim, jf);
+            else fill_fim_desc<double>(rt, in, rt->h_fim, jf);
+            if (rt->cfg.dtype == RIPPLE_F32) static_cast<BatchFim<float>*>(rt->h_fim)[jf].tile_begin = t;
+            else static_cast<BatchFim<double>*>(rt->h_fim)[jf].tile_begin = t;
+            for (int k = 0; k < in->ntiles; ++k) rt->h_table[t + k] = (jf << 1) | 1;
+            ++jf;
+        }
+        t += in->ntiles;
+    }
+    cudaStream_t s = rt->compute;
+    if (ne) RIPPLE_CUDA(cudaMemcpyAsync(rt->d_euler, rt->h_euler, ne * sizeof(BatchEuler), cudaMemcpyHostToDevice, s));
+    if (nf)
+        RIPPLE_CUDA(cudaMemcpyAsync(rt->d_fim, rt->h_fim, nf * fim_elem_size(rt->cfg.dtype), cudaMemcpyHostToDevice, s));
+    if (nt) RIPPLE_CUDA(cudaMemcpyAsync(rt->d_table, rt->h_table, nt * sizeof(int), cudaMemcpyHostToDevice, s));
+    RIPPLE_CUDA(cudaMemcpyAsync(&rt->d_bctl->ntiles, &nt, sizeof(int), cudaMemcpyHostToDevice, s));
+    RIPPLE_CUDA(cudaStreamSynchronize(s));  // nt lives on this stack frame
+    rt->dirty = false;
+    return RIPPLE_OK;
+}
+
+static ripple_status launch_steps(BatchRuntime* rt, int K)
+{
+    const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
+    auto one = [&]() {
+        return launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->grid, rt->compute, rt->d_euler,
+                                 rt->d_fim, rt->d_table, rt->d_bctl);
+    };
+    if (!rt->cfg.use_graphs) {
+        for (int k = 0; k < K; ++k) RIPPLE_CUDA(one());
+        std::lock_guard<std::mutex> lk(rt->mu);
+        rt->stats.launches += K;
+        return RIPPLE_OK;
+    }
+    if (rt->graph_variant != rt->cfg.tile_variant || rt->graph_layout != layout) {
+        for (auto& g : rt->graphs) cudaGraphExecDestroy(g.second);
+        rt->graphs.clear();
+        rt->graph_variant = rt->cfg.tile_variant;
+        rt->graph_layout = layout;
+    }
+    // K as a sum of powers of two, each replayed from a captured graph
+    for (int bit = 30; bit >= 0; --bit) {
+        const int n = 1 << bit;
+        if (!(K & n)) continue;
+        auto it = rt->graphs.find(n);
+        if (it == rt->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            RIPPLE_CUDA(cudaStreamBeginCapture(rt->compute, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < n && e == cudaSuccess; ++k) e = one();
+            cudaError_t e2 = cudaStreamEndCapture(rt->compute, &g);
+            if (e != cudaSuccess) return cuda_fail(e, "batched step capture");
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+            it = rt->graphs.emplace(n, ex).first;
+        }
+        RIPPLE_CUDA(cudaGraphLaunch(it->second, rt->compute));
+        std::lock_guard<std::mutex> lk(rt->mu);
+        rt->stats.launches += n;
+        rt->stats.graph_replays += 1;
+    }
+    return RIPPLE_OK;
+}
+
+// One scheduler round of compute: K global steps over the resident set.
+static ripple_status compute_round(BatchRuntime* rt)
+{
+    if (rt->dirty) {
+        ripple_status st = rebuild_tables(rt);
+        if (st != RIPPLE_OK) return st;
+    }
+    long long K = std::max(1, rt->cfg.steps_per_sync);
+    for (Inst* in : rt->resident)
+        if (in->req.kind == RIPPLE_REQ_EULER) K = std::min(K, in->start_step + in->req.nsteps - rt->gstep);
+    K = std::max(1LL, K);
+    ripple_status st = launch_steps(rt, (int)K);
+    if (st != RIPPLE_OK) return st;
+    RIPPLE_CUDA(cudaMemcpyAsync(rt->h_status, rt->slot_status, kSlots * sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, rt->compute));
+    RIPPLE_CUDA(cudaMemcpyAsync(rt->h_counters, rt->slot_counters, kSlots * 3 * sizeof(long long),
+                                cudaMemcpyDeviceToHost, rt->compute));
+    RIPPLE_CUDA(cudaEventRecord(rt->ev_step, rt->compute));
+    RIPPLE_CUDA(cudaEventSynchronize(rt->ev_step));
+    rt->gstep += K;
+    {
+        std::lock_guard<std::mutex> lk(rt->mu);
+        rt->stats.global_steps = rt->gstep;
+    }
+    std::vector<Inst*> keep;
+    for (Inst* in : rt->resident) {
+        bool fin = false;
+        if (in->req.kind == RIPPLE_REQ_EULER) fin = rt->gstep - in->start_step >= in->req.nsteps;
+        else fin = rt->h_status[in->slot] != 0ull;
+        if (!fin) {
+            keep.push_back(in);
+            continue;
+        }
+        st = start_download(rt, in);
+        if (st != RIPPLE_OK) {
+            release(rt, in);
+            finish(rt, in, st);
+            delete in;
+            continue;
+        }
+        rt->downloading.push_back(in);
+        rt->dirty = true;
+    }
+    rt->resident.swap(keep);
+    return RIPPLE_OK;
+}
+
+static void scheduler(BatchRuntime* rt)
+{
+    cudaSetDevice(rt->ctx->device);
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(rt->mu);
+            const bool busy = !rt->resident.empty() || !rt->uploading.empty() || !rt->downloading.empty();
+            if (!busy)
+                rt->cv_work.wait(lk, [&] { return rt->stop || !rt->pending.empty(); });
+            if (rt->stop && rt->resident.empty() && rt->uploading.empty() && rt->downloading.empty()) break;
+            // admission: FIFO while memory fits
+            while (!rt->pending.empty()) {
+                Inst* in = rt->pending.front();
+                lk.unlock();
+                ripple_status st = admit(rt, in);
+                lk.lock();
+                if (st == RIPPLE_ERR_BUDGET) {
+                    const bool nothing_running =
+                        rt->resident.empty() && rt->uploading.empty() && rt->downloading.empty();
+                    const bool never_fits = rt->ctx->budget && in->total_bytes > rt->ctx->budget;
+                    if (never_fits || nothing_running) {
+                        rt->pending.pop_front();
+                        lk.unlock();
+                        release(rt, in);
+                        finish(rt, in, RIPPLE_ERR_BUDGET);
+                        delete in;
+                        lk.lock();
+                        continue;
+                    }
+                    break;  // wait for memory to free up
+                }
+                rt->pending.pop_front();
+                if (st != RIPPLE_OK) {
+                    lk.unlock();
+                    release(rt, in);
+                    finish(rt, in, st);
+                    delete in;
+                    lk.lock();
+                    continue;
+                }
+                rt->stats.admitted++;
+                rt->uploading.push_back(in);  // counts as running for the admissions that follow
+            }
+        }
+        // uploads that completed join the resident set at the next global step
+        for (size_t i = 0; i < rt->uploading.size();) {
+            Inst* in = rt->uploading[i];
+            if (cudaEventQuery(in->ev) == cudaSuccess) {
+                in->start_step = rt->gstep;
+                in->t_start = rt->now();
+                rt->resident.push_back(in);
+                rt->dirty = true;
+                rt->uploading.erase(rt->uploading.begin() + i);
+            } else {
+                ++i;
+            }
+        }
+        if (!rt->resident.empty()) {
+            ripple_status st = compute_round(rt);
+            if (st != RIPPLE_OK) {
+                // a CUDA failure: fail everything resident
+                for (Inst* in : rt->resident) {
+                    release(rt, in);
+                    finish(rt, in, st);
+                    delete in;
+                }
+                rt->resident.clear();
+                rt->dirty = true;
+            }
+        }
+        // completions
+        for (size_t i = 0; i < rt->downloading.size();) {
+            Inst* in = rt->downloading[i];
+            if (cudaEventQuery(in->ev) == cudaSuccess) {
+                ripple_status st = RIPPLE_OK;
+                if (in->req.kind == RIPPLE_REQ_EULER) {
+                    const unsigned err = rt->h_ctl[in->slot].err;
+                    if (err & DEV_ERR_NUMERIC) st = RIPPLE_ERR_NUMERIC;
+                    else if (err) st = RIPPLE_ERR_INTERNAL;
+                } else if ((rt->h_status[in->slot] & 3ull) == 2ull) {
+                    st = RIPPLE_ERR_TIMEOUT;
+                }
+                finish(rt, in, st);
+                release(rt, in);
+                delete in;
+                rt->downloading.erase(rt->downloading.begin() + i);
+            } else {
+                ++i;
+            }
+        }
+        if (rt->resident.empty() && (!rt->uploading.empty() || !rt->downloading.empty()))
+            std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+}
+
+static ripple_status rt_start(BatchRuntime* rt)
+{
+    if (rt->started) return RIPPLE_OK;
+    RIPPLE_CUDA(cudaSetDevice(rt->ctx->device));
+    RIPPLE_CUDA(cudaStreamCreateWithFlags(&rt->compute, cudaStreamNonBlocking));
+    RIPPLE_CUDA(cudaStreamCreateWithFlags(&rt->copy, cudaStreamNonBlocking));
+    RIPPLE_CUDA(cudaEventCreateWithFlags(&rt->ev_step, cudaEventDisableTiming));
+    RIPPLE_CUDA(cudaMalloc(&rt->slot_ctl, kSlots * sizeof(FieldCtl)));
+    RIPPLE_CUDA(cudaMalloc(&rt->slot_status, kSlots * sizeof(unsigned long long)));
+    RIPPLE_CUDA(cudaMalloc(&rt->slot_counters, kSlots * 3 * sizeof(long long)));
+    RIPPLE_CUDA(cudaMemset(rt->slot_status, 0, kSlots * sizeof(unsigned long long)));
+    RIPPLE_CUDA(cudaMallocHost(&rt->h_ctl, kSlots * sizeof(FieldCtl)));
+    RIPPLE_CUDA(cudaMallocHost(&rt->h_status, kSlots * sizeof(unsigned long long)));
+    RIPPLE_CUDA(cudaMallocHost(&rt->h_counters, kSlots * 3 * sizeof(long long)));
+    RIPPLE_CUDA(cudaMalloc(&rt->d_bctl, sizeof(BatchCtl)));
+    RIPPLE_CUDA(cudaMemset(rt->d_bctl, 0, sizeof(BatchCtl)));
+    rt->free_slots.clear();
+    for (int i = kSlots - 1; i >= 0; --i) rt->free_slots.push_back(i);
+    const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
+    const int occ = std::max(1, batch_occupancy(rt->cfg.dtype, layout, rt->cfg.tile_variant));
+    rt->grid = occ * rt->ctx->sm_count;
+    rt->gstep = 0;
+    rt->started = true;
+    rt->th = std::thread(scheduler, rt);
+    return RIPPLE_OK;
+}
+
+static BatchRuntime* runtime_of(ripple_ctx ctx, bool create)
+{
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (!ctx->batch && create) {
+        auto* rt = new BatchRuntime();
+        rt->ctx = ctx;
+        ctx->batch = rt;
+    }
+    return static_cast<BatchRuntime*>(ctx->batch);
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: time each (layout, tile shape) candidate of the batched step on
+// sample Euler problems of the given sides and keep the fastest.
+// ---------------------------------------------------------------------------
+static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, ripple_dtype dt, ripple_batch_config* best,
+                              double* ms)
+{
+    RIPPLE_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s;
+    RIPPLE_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    double best_ms = 1e300;
+    ripple_status status = RIPPLE_OK;
+    for (int li = 0; li < 2 && status == RIPPLE_OK; ++li) {
+        const ripple_layout lay = li == 0 ? RIPPLE_SOA : RIPPLE_AOS;
+        for (int v = 0; v < kNumBatchVariants && status == RIPPLE_OK; ++v) {
+            std::vector<void*> bufs;
+            std::vector<size_t> sizes;
+            std::vector<BatchEuler> h(n);
+            std::vector<int> table;
+            FieldCtl* ctl = nullptr;
+            BatchEuler* d_e = nullptr;
+            int* d_t = nullptr;
+            BatchCtl* d_c = nullptr;
+            auto cleanup = [&]() {
+                cudaStreamSynchronize(s);
+                for (size_t i = 0; i < bufs.size(); ++i) ctx_free(ctx, bufs[i], sizes[i]);
+                cudaFree(ctl);
+                cudaFree(d_e);
+                cudaFree(d_t);
+                cudaFree(d_c);
+            };
+            if (cudaMalloc(&ctl, n * sizeof(FieldCtl)) != cudaSuccess) { status = RIPPLE_ERR_OOM; break; }
+            cudaMemset(ctl, 0, n * sizeof(FieldCtl));
+            for (int i = 0; i < n && status == RIPPLE_OK; ++i) {
+                const int64_t dims[2] = {sides[i], sides[i]};
+                size_t bytes = 0;
+                FieldGeom g = make_field_geom(2, dims, 4, lay, 1, dt, &bytes);
+                void* b[2] = {nullptr, nullptr};
+                for (int k = 0; k < 2 && status == RIPPLE_OK; ++k) {
+                    status = ctx_alloc(ctx, bytes, &b[k]);
+                    if (status == RIPPLE_OK) {
+                        bufs.push_back(b[k]);
+                        sizes.push_back(bytes);
+                        if (dt == RIPPLE_F32) fill_uniform_euler<float><<<64, 256, 0, s>>>(static_cast<float*>(b[k]), g);
+                        else fill_uniform_euler<double><<<64, 256, 0, s>>>(static_cast<double*>(b[k]), g);
+                    }
+                }
+                const int tx = kBatchVariants[v].tx, ty = kBatchVariants[v].ty;
+                h[i].buf[0] = b[0];
+                h[i].buf[1] = b[1];
+                h[i].ctl = ctl + i;
+                h[i].g = g;
+                h[i].tiles_x = (int)((sides[i] + tx - 1) / tx);
+                h[i].tile_begin = (int)table.size();
+                h[i].bc = RIPPLE_BC_PERIODIC;
+                h[i].start_step = 0;
+                h[i].nsteps = 1LL << 40;
+                h[i].gamma = 1.4;
+                h[i].cfl = 0.4;
+                h[i].inv_dx0 = h[i].inv_dx1 = (double)sides[i];
+                const int nt = h[i].tiles_x * (int)((sides[i] + ty - 1) / ty);
+                for (int k = 0; k < nt; ++k) table.push_back(i << 1);
+            }
+            if (status != RIPPLE_OK) { cleanup(); break; }
+            // smax slot 0 of every sample: any positive value
+            std::vector<FieldCtl> hc(n);
+            for (int i = 0; i < n; ++i) {
+                std::memset(&hc[i], 0, sizeof(FieldCtl));
+                const double smax0 = 4.0 * (double)sides[i];
+                std::memcpy(&hc[i].smax[0], &smax0, sizeof(double));
+            }
+            cudaMemcpyAsync(ctl, hc.data(), n * sizeof(FieldCtl), cudaMemcpyHostToDevice, s);
+            cudaMalloc(&d_e, n * sizeof(BatchEuler));
+            cudaMalloc(&d_t, table.size() * sizeof(int));
+            cudaMalloc(&d_c, sizeof(BatchCtl));
+            BatchCtl hb{0ull, 0u, (int)table.size()};
+            cudaMemcpyAsync(d_e, h.data(), n * sizeof(BatchEuler), cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(d_t, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(d_c, &hb, sizeof(BatchCtl), cudaMemcpyHostToDevice, s);
+            const int lay_i = lay == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
+            const int grid = std::max(1, batch_occupancy(dt, lay_i, v)) * ctx->sm_count;
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaError_t ce = cudaSuccess;
+            for (int k = 0; k < 3 && ce == cudaSuccess; ++k)
+                ce = launch_batch_step(dt, lay_i, v, grid, s, d_e, nullptr, d_t, d_c);
+            cudaEventRecord(e0, s);
+            const int reps = 6;
+            for (int k = 0; k < reps && ce == cudaSuccess; ++k)
+                ce = launch_batch_step(dt, lay_i, v, grid, s, d_e, nullptr, d_t, d_c);
+            cudaEventRecord(e1, s);
+            cudaStreamSynchronize(s);
+            float el = 0.f;
+            cudaEventElapsedTime(&el, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cleanup();
+            if (ce != cudaSuccess) return cuda_fail(ce, "autotune launch");
+            const double t = el / reps;
+            if (ms) ms[li * kNumBatchVariants + v] = t;
+            if (t < best_ms) {
+                best_ms = t;
+                best->layout = lay;
+                best->tile_variant = v;
+            }
+        }
+    }
+    cudaStreamDestroy(s);
+    return status;
+}
+
+}  // namespace ripple
+
+using namespace ripple;
+
+void batch_runtime_destroy(ripple_ctx ctx)
+{
+    BatchRuntime* rt = static_cast<BatchRuntime*>(ctx->batch);
+    if (!rt) return;
+    if (rt->started) {
+        {
+            std::lock_guard<std::mutex> lk(rt->mu);
+            rt->stop = true;
+            for (Inst* in : rt->pending) delete in;
+            rt->pending.clear();
+        }
+        rt->cv_work.notify_all();
+        rt->th.join();
+        cudaStreamSynchronize(rt->copy);
+        cudaStreamSynchronize(rt->compute);
+        for (auto& g : rt->graphs) cudaGraphExecDestroy(g.second);
+        cudaFree(rt->slot_ctl);
+        cudaFree(rt->slot_status);
+        cudaFree(rt->slot_counters);
+        cudaFreeHost(rt->h_ctl);
+        cudaFreeHost(rt->h_status);
+        cudaFreeHost(rt->h_counters);
+        cudaFree(rt->d_euler);
+        cudaFree(rt->d_fim);
+        cudaFree(rt->d_table);
+        cudaFree(rt->d_bctl);
+        cudaFreeHost(rt->h_euler);
+        cudaFreeHost(rt->h_fim);
+        cudaFreeHost(rt->h_table);
+        cudaEventDestroy(rt->ev_step);
+        cudaStreamDestroy(rt->compute);
+        cudaStreamDestroy(rt->copy);
+    }
+    delete rt;
+    ctx->batch = nullptr;
+}
+
+extern "C" {
+
+ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* cfg)
+{
+    if (!ctx || !cfg) return fail(RIPPLE_ERR_INVALID, "NULL argument");
+    if (cfg->layout != RIPPLE_AOS && cfg->layout != RIPPLE_SOA) return fail(RIPPLE_ERR_INVALID, "bad layout");
+    if (cfg->tile_variant < 0 || cfg->tile_variant >= kNumBatchVariants) return fail(RIPPLE_ERR_INVALID, "bad tile variant");
+    if (cfg->steps_per_sync < 1) return fail(RIPPLE_ERR_INVALID, "steps_per_sync must be >= 1");
+    if (cfg->dtype != RIPPLE_F32 && cfg->dtype != RIPPLE_F64) return fail(RIPPLE_ERR_INVALID, "bad dtype");
+    BatchRuntime* rt = runtime_of(ctx, true);
+    std::lock_guard<std::mutex> lk(rt->mu);
+    if (rt->started) {
+        const bool idle = rt->stats.submitted == rt->stats.completed + rt->stats.failed;
+        if (!idle) return fail(RIPPLE_ERR_INVALID, "configure only while no request is in flight");
+        if (cfg->dtype != rt->cfg.dtype || cfg->layout != rt->cfg.layout || cfg->tile_variant != rt->cfg.tile_variant) {
+            // the kernel grid depends on the variant; the scheduler re-reads it
+            const int layout = cfg->layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
+            rt->grid = std::max(1, batch_occupancy(cfg->dtype, layout, cfg->tile_variant)) * ctx->sm_count;
+            if (cfg->dtype != rt->cfg.dtype) {
+                // descriptor arrays hold the element type: reallocate on next use
+                cudaFree(rt->d_fim);
+                cudaFreeHost(rt->h_fim);
+                rt->d_fim = nullptr;
+                rt->h_fim = nullptr;
+                rt->cap_f = 0;
+            }
+        }
+    }
+    rt->cfg = *cfg;
+    rt->dirty = true;
+    return RIPPLE_OK;
+}
+
+ripple_status ripple_batch_submit(ripple_ctx ctx, const ripple_request* reqs, int n, uint64_t* tickets)
+{
+    if (!ctx || (!reqs && n > 0) || (!tickets && n > 0) || n < 0) return fail(RIPPLE_ERR_INVALID, "bad arguments");
+    for (int i = 0; i < n; ++i) {
+        const ripple_request& r = reqs[i];
+        if (r.kind != RIPPLE_REQ_EULER && r.kind != RIPPLE_REQ_EIKONAL) return fail(RIPPLE_ERR_INVALID, "bad kind");
+        if (r.dims[0] < 1 || r.dims[1] < 1 || r.dims[0] > 65536 || r.dims[1] > 65536)
+            return fail(RIPPLE_ERR_INVALID, "dims out of range");
+        if (!r.input || !r.output) return fail(RIPPLE_ERR_INVALID, "NULL input/output");
+        if (r.kind == RIPPLE_REQ_EULER) {
+            if (r.nsteps < 1) return fail(RIPPLE_ERR_INVALID, "nsteps must be >= 1");
+            if (r.fv.scheme != RIPPLE_RUSANOV1) return fail(RIPPLE_ERR_INVALID, "batched Euler runs the Rusanov scheme");
+            if (!(r.fv.gamma > 1.0) || !(r.fv.cfl > 0.0) || !(r.fv.dx[0] > 0.0) || !(r.fv.dx[1] > 0.0))
+                return fail(RIPPLE_ERR_INVALID, "bad Euler parameters");
+            if (r.fv.bc != RIPPLE_BC_PERIODIC && r.fv.bc != RIPPLE_BC_TRANSMISSIVE) return fail(RIPPLE_ERR_INVALID, "bad bc");
+        } else {
+            if (r.nsrc < 1 || r.nsrc > kMaxSources || !r.sources) return fail(RIPPLE_ERR_INVALID, "need 1..16 sources");
+            if (!(r.eik.h > 0.0) || !(r.eik.tol > 0.0)) return fail(RIPPLE_ERR_INVALID, "need h > 0 and tol > 0");
+            for (int q = 0; q < r.nsrc; ++q)
+                if (r.sources[2 * q] < 0 || r.sources[2 * q] >= r.dims[0] || r.sources[2 * q + 1] < 0 ||
+                    r.sources[2 * q + 1] >= r.dims[1])
+                    return fail(RIPPLE_ERR_INVALID, "source outside the grid");
+        }
+    }
+    BatchRuntime* rt = runtime_of(ctx, true);
+    {
+        std::lock_guard<std::mutex> lk(rt->mu);
+        if (!rt->started) {
+            ripple_status st = rt_start(rt);
+            if (st != RIPPLE_OK) return st;
+        }
+        const double now = rt->now();
+        for (int i = 0; i < n; ++i) {
+            Inst* in = new Inst();
+            in->req = reqs[i];
+            if (reqs[i].kind == RIPPLE_REQ_EIKONAL) {
+                in->src.assign(reqs[i].sources, reqs[i].sources + 2 * reqs[i].nsrc);
+                in->req.sources = nullptr;
+            }
+            in->ticket = rt->next_ticket++;
+            in->t_submit = now;
+            rt->tickets[in->ticket] = Ticket{};
+            rt->pending.push_back(in);
+            tickets[i] = in->ticket;
+            rt->stats.submitted++;
+        }
+    }
+    rt->cv_work.notify_all();
+    return RIPPLE_OK;
+}
+
+ripple_status ripple_poll(ripple_ctx ctx, uint64_t ticket, ripple_ticket_info* info)
+{
+    if (!ctx) return fail(RIPPLE_ERR_INVALID, "ctx is NULL");
+    BatchRuntime* rt = runtime_of(ctx, false);
+    if (!rt) return fail(RIPPLE_ERR_INVALID, "unknown ticket");
+    std::lock_guard<std::mutex> lk(rt->mu);
+    auto it = rt->tickets.find(ticket);
+    if (it == rt->tickets.end()) return fail(RIPPLE_ERR_INVALID, "unknown ticket");
+    if (!it->second.done) return RIPPLE_ERR_NOT_READY;
+    if (info) *info = it->second.info;
+    rt->tickets.erase(it);
+    return RIPPLE_OK;
+}
+
+ripple_status ripple_wait(ripple_ctx ctx, uint64_t ticket, int64_t timeout_ms, ripple_ticket_info* info)
+{
+    if (!ctx) return fail(RIPPLE_ERR_INVALID, "ctx is NULL");
+    BatchRuntime* rt = runtime_of(ctx, false);
+    if (!rt) return fail(RIPPLE_ERR_INVALID, "unknown ticket");
+    std::unique_lock<std::mutex> lk(rt->mu);
+    auto it = rt->tickets.find(ticket);
+    if (it == rt->tickets.end()) return fail(RIPPLE_ERR_INVALID, "unknown ticket");
+    const auto deadline = Clock::now() + std::chrono::milliseconds(timeout_ms < 0 ? 0 : timeout_ms);
+    while (!rt->tickets[ticket].done) {
+        if (timeout_ms >= 0) {
+            if (rt->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && !rt->tickets[ticket].done)
+                return fail(RIPPLE_ERR_TIMEOUT, "ripple_wait timed out");
+        } else {
+            rt->cv_done.wait(lk);
+        }
+    }
+    if (info) *info = rt->tickets[ticket].info;
+    rt->tickets.erase(ticket);
+    return RIPPLE_OK;
+}
+
+ripple_status ripple_batch_get_stats(ripple_ctx ctx, ripple_batch_stats* out)
+{
+    if (!ctx || !out) return fail(RIPPLE_ERR_INVALID, "NULL argument");
+    BatchRuntime* rt = runtime_of(ctx, true);
+    std::lock_guard<std::mutex> lk(rt->mu);
+    *out = rt->stats;
+    out->now_s = rt->now();
+    return RIPPLE_OK;
+}
+
+ripple_status ripple_batch_autotune(ripple_ctx ctx, const int64_t* sides, int n, ripple_dtype dtype,
+                                    ripple_batch_config* chosen, double* ms_per_step)
+{
+    if (!ctx || !sides || n < 1 || !chosen) return fail(RIPPLE_ERR_INVALID, "bad arguments");
+    for (int i = 0; i < n; ++i)
+        if (sides[i] < 1 || sides[i] > 65536) return fail(RIPPLE_ERR_INVALID, "side out of range");
+    ripple_batch_config best = *chosen;
+    best.dtype = dtype;
+    ripple_status st = autotune(ctx, sides, n, dtype, &best, ms_per_step);
+    if (st != RIPPLE_OK) return st;
+    *chosen = best;
+    return RIPPLE_OK;
+}
+
+}  // extern "C"

@@ -31,25 +31,66 @@ size_t elem_size(ripple_dtype d) { return d == RIPPLE_F64 ? 8 : 4; }
 
 static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+bool budget_reserve(ripple_ctx ctx, size_t bytes)
+{
+    size_t cur = ctx->used.load();
+    for (;;) {
+        if (ctx->budget && cur + bytes > ctx->budget) return false;
+        if (ctx->used.compare_exchange_weak(cur, cur + bytes)) return true;
+    }
+}
+
+FieldGeom make_field_geom(int ndim, const int64_t* dims, int ncomp, ripple_layout layout, int halo,
+                          ripple_dtype dtype, size_t* bytes)
+{
+    const int es = (int)elem_size(dtype);
+    const int a = 16 / es;  // 16-byte x alignment in cells
+    FieldGeom g{};
+    g.ndim = ndim;
+    g.ncomp = ncomp;
+    g.h = halo;
+    g.lead = (a - halo % a) % a;
+    for (int d = 0; d < 3; ++d) g.n[d] = d < ndim ? (int)dims[d] : 1;
+    g.px = (long long)round_up((size_t)(g.lead + g.n[0] + 2 * halo), (size_t)a);
+    g.py = g.n[1] + 2 * halo;
+    g.pz = ndim == 3 ? g.n[2] + 2 * halo : 1;
+    const long long ncell = g.px * g.py * g.pz;
+    if (layout == RIPPLE_SOA) {
+        g.cell_stride = 1;
+        g.comp_stride = ncell;
+    } else {
+        g.cell_stride = ncomp;
+        g.comp_stride = 1;
+    }
+    if (bytes) *bytes = round_up((size_t)ncell * ncomp * es, 256);
+    return g;
+}
+
 ripple_status ctx_alloc(ripple_ctx ctx, size_t bytes, void** out)
 {
     *out = nullptr;
     bytes = round_up(std::max<size_t>(bytes, 256), 256);
-    if (ctx->budget && ctx->used.load() + bytes > ctx->budget)
+    if (!budget_reserve(ctx, bytes))
         return fail(RIPPLE_ERR_BUDGET, "allocation of " + std::to_string(bytes) + " bytes exceeds the memory budget");
     void* p = nullptr;
     if (ctx->alloc_fn) {
         p = ctx->alloc_fn(bytes, ctx->alloc_user);
-        if (!p) return fail(RIPPLE_ERR_OOM, "allocator callback returned NULL");
+        if (!p) {
+            ctx->used -= bytes;
+            return fail(RIPPLE_ERR_OOM, "allocator callback returned NULL");
+        }
         if (reinterpret_cast<uintptr_t>(p) % 256) {
             ctx->free_fn(p, ctx->alloc_user);
+            ctx->used -= bytes;
             return fail(RIPPLE_ERR_INTERNAL, "allocator callback returned memory not aligned to 256 bytes");
         }
     } else {
         cudaError_t e = cudaMalloc(&p, bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+        if (e != cudaSuccess) {
+            ctx->used -= bytes;
+            return cuda_fail(e, "cudaMalloc");
+        }
     }
-    ctx->used += bytes;
     *out = p;
     return RIPPLE_OK;
 }
@@ -343,27 +384,9 @@ ripple_status ripple_field_create(ripple_ctx ctx, int ndim, const int64_t* dims,
     f->halo = halo;
     f->layout = layout;
     f->dtype = dtype;
-    const int es = (int)elem_size(dtype);
-    const int a = 16 / es;  // 16-byte x alignment in cells
-    FieldGeom& g = f->geom;
-    g.ndim = ndim;
-    g.ncomp = ncomp;
-    g.h = halo;
-    g.lead = (a - halo % a) % a;
-    for (int d = 0; d < 3; ++d) g.n[d] = d < ndim ? (int)dims[d] : 1;
-    g.px = (long long)round_up((size_t)(g.lead + g.n[0] + 2 * halo), (size_t)a);
-    g.py = g.n[1] + 2 * halo;
-    g.pz = ndim == 3 ? g.n[2] + 2 * halo : 1;
-    const long long ncell = g.px * g.py * g.pz;
-    if (layout == RIPPLE_SOA) {
-        g.cell_stride = 1;
-        g.comp_stride = ncell;
-    } else {
-        g.cell_stride = ncomp;
-        g.comp_stride = 1;
-    }
-    f->elems = (size_t)ncell * ncomp;
-    f->bytes = round_up(f->elems * es, 256);
+    f->geom = make_field_geom(ndim, dims, ncomp, layout, halo, dtype, &f->bytes);
+    const FieldGeom& g = f->geom;
+    f->elems = (size_t)(g.px * g.py * g.pz) * ncomp;
     ripple_status st = ctx_alloc(ctx, f->bytes, &f->buf[0]);
     if (st == RIPPLE_OK) st = ctx_alloc(ctx, sizeof(FieldCtl), reinterpret_cast<void**>(&f->ctl));
     if (st != RIPPLE_OK) {

@@ -131,6 +131,11 @@ void eik_scratch_free(ripple_field f);
 void batch_runtime_destroy(ripple_ctx ctx);
 
 namespace ripple {
+// Reserve `bytes` of the context's budget (atomic); false if it would overflow.
+bool budget_reserve(ripple_ctx ctx, size_t bytes);
+// Padded geometry of a field (see field.cuh); *bytes = one buffer, 256-byte rounded.
+FieldGeom make_field_geom(int ndim, const int64_t* dims, int ncomp, ripple_layout layout, int halo,
+                          ripple_dtype dtype, size_t* bytes);
 ripple_status ctx_alloc(ripple_ctx ctx, size_t bytes, void** out);
 void ctx_free(ripple_ctx ctx, void* p, size_t bytes);
 ripple_status ensure_second_buffer(ripple_field f);

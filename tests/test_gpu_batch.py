@@ -1,0 +1,191 @@
+"""Batched and served execution (one launch per global step over many
+independent problems) against the FP64 oracle, plus the serving invariants:
+a problem gives the same bits alone and in a mix, requests wait for memory
+under a budget, and requests that arrive while others run are admitted."""
+import time
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+import paper_2104_08571_gb300 as R
+from tests.gpu_util import rel_l1
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture()
+def ctx():
+    import torch
+    assert torch.cuda.is_available()
+    c = R.ripple_ctx_create(0)
+    yield c
+    R.ripple_ctx_destroy(c)
+
+
+def _euler(nx, ny, amp, nsteps, bc=R.RIPPLE_BC_PERIODIC):
+    U = inputs.euler2d_sine(nx, amp=amp, ny=ny).astype(np.float32)
+    return R.euler_request(U, nsteps, [1.0 / nx, 1.0 / ny], bc=bc)
+
+
+def _eik(nx, ny, seed):
+    s = inputs.eikonal_slowness((nx, ny), seed=seed).astype(np.float32)
+    src = inputs.eikonal_sources((nx, ny), seed=seed)
+    return R.eikonal_request(s, src, 1.0 / max(nx, ny))
+
+
+def _run(ctx, reqs, timeout_ms=120000):
+    tickets = R.ripple_batch_submit(ctx, reqs)
+    return [R.ripple_wait(ctx, t, timeout_ms) for t in tickets]
+
+
+def _oracle_euler(req):
+    U0 = req["input"].astype(np.float64)
+    ref, _ = oracle.euler_run(U0, req["nsteps"], dx=req["dx"], bc=req.get("bc", 0))
+    return ref
+
+
+def test_batch_euler_matches_oracle(ctx):
+    reqs = [_euler(32, 32, 0.2, 40), _euler(45, 77, 0.1, 25), _euler(100, 64, 0.3, 60),
+            _euler(33, 129, 0.05, 10, bc=R.RIPPLE_BC_TRANSMISSIVE), _euler(128, 128, 0.2, 100)]
+    infos = _run(ctx, reqs)
+    for req, info in zip(reqs, infos):
+        assert info["status"] == R.RIPPLE_OK
+        assert info["work"] == req["nsteps"]
+        assert rel_l1(req["output"], _oracle_euler(req)) <= 2e-5
+
+
+def test_batch_eikonal_matches_fmm(ctx):
+    reqs = [_eik(100, 100, 1), _eik(64, 150, 2), _eik(257, 97, 3)]
+    infos = _run(ctx, reqs)
+    for req, info in zip(reqs, infos):
+        assert info["status"] == R.RIPPLE_OK and info["work"] > 0
+        ref = oracle.eikonal_fmm(req["input"].astype(np.float64), req["h"], req["sources"])
+        assert rel_l1(req["output"][None], ref[None]) <= 1e-4
+
+
+def test_alone_equals_in_mix_bitwise(ctx):
+    a = _euler(90, 70, 0.25, 37)
+    e = _eik(120, 80, 5)
+    _run(ctx, [a])
+    _run(ctx, [e])
+    alone_a, alone_e = a["output"].copy(), e["output"].copy()
+    a2 = R.euler_request(a["input"], 37, a["dx"])
+    e2 = R.eikonal_request(e["input"], e["sources"], e["h"])
+    mix = [_euler(64, 64, 0.1, 80), a2, _eik(200, 150, 6), _euler(300, 40, 0.2, 15), e2, _euler(33, 33, 0.3, 50)]
+    infos = _run(ctx, mix)
+    assert all(i["status"] == R.RIPPLE_OK for i in infos)
+    assert np.array_equal(a2["output"], alone_a)
+    assert np.array_equal(e2["output"], alone_e)
+
+
+def test_batch_matches_single_field_sweep(ctx):
+    req = _euler(96, 80, 0.2, 30)
+    _run(ctx, [req])
+    f = R.ripple_field_create(ctx, (96, 80), 4, R.RIPPLE_SOA, 1, R.RIPPLE_F32)
+    try:
+        R.ripple_field_upload(f, req["input"])
+        R.ripple_fv_step(f, R.make_fv_params(req["dx"]), 30)
+        single = R.ripple_field_download(f)
+    finally:
+        R.ripple_field_destroy(f)
+    assert rel_l1(req["output"], single) <= 1e-6
+
+
+def test_graphs_and_sync_interval_do_not_change_results(ctx):
+    reqs1 = [_euler(70, 50, 0.2, 33), _eik(90, 90, 7)]
+    _run(ctx, reqs1)
+    R.ripple_batch_configure(ctx, steps_per_sync=3, use_graphs=False)
+    reqs2 = [R.euler_request(reqs1[0]["input"], 33, reqs1[0]["dx"]),
+             R.eikonal_request(reqs1[1]["input"], reqs1[1]["sources"], reqs1[1]["h"])]
+    _run(ctx, reqs2)
+    assert np.array_equal(reqs1[0]["output"], reqs2[0]["output"])
+    assert np.array_equal(reqs1[1]["output"], reqs2[1]["output"])
+
+
+def test_aos_layout_and_tile_variants(ctx):
+    base = _euler(77, 61, 0.2, 21)
+    _run(ctx, [base])
+    for layout in (R.RIPPLE_SOA, R.RIPPLE_AOS):
+        for v in range(3):
+            R.ripple_batch_configure(ctx, layout=layout, tile_variant=v)
+            r = R.euler_request(base["input"], 21, base["dx"])
+            _run(ctx, [r])
+            assert rel_l1(r["output"], base["output"]) <= 1e-6
+
+
+def test_budget_admission_waits_for_memory():
+    c = R.ripple_ctx_create(0, 24 << 20)  # 24 MiB: about two 512^2 FP32 instances at once
+    try:
+        reqs = [_euler(512, 512, 0.1 + 0.02 * i, 20) for i in range(6)]
+        infos = _run(c, reqs)
+        assert all(i["status"] == R.RIPPLE_OK for i in infos)
+        # some request had to wait for an earlier one to finish before admission
+        finishes = sorted(i["finish_s"] for i in infos)
+        assert max(i["admit_s"] for i in infos) >= finishes[0]
+        for req in reqs[:2]:
+            assert rel_l1(req["output"], _oracle_euler(req)) <= 2e-5
+        # a request that can never fit fails with RIPPLE_ERR_BUDGET
+        big = _euler(2048, 2048, 0.1, 1)
+        info = _run(c, [big])[0]
+        assert info["status"] == R.RIPPLE_ERR_BUDGET
+    finally:
+        R.ripple_ctx_destroy(c)
+
+
+def test_requests_arriving_while_others_run(ctx):
+    R.ripple_batch_configure(ctx, steps_per_sync=2)
+    first = [_euler(256, 256, 0.2, 3000), _eik(300, 300, 8)]
+    t_first = R.ripple_batch_submit(ctx, first)
+    time.sleep(0.005)
+    late = [_euler(64, 48, 0.15, 20), _eik(80, 60, 9)]
+    t_late = R.ripple_batch_submit(ctx, late)
+    info_late = [R.ripple_wait(ctx, t, 120000) for t in t_late]
+    info_first = [R.ripple_wait(ctx, t, 120000) for t in t_first]
+    assert all(i["status"] == R.RIPPLE_OK for i in info_first + info_late)
+    # the small late Euler request ran and finished while the long first one was resident
+    assert info_late[0]["start_s"] < info_first[0]["finish_s"]
+    assert info_late[0]["finish_s"] < info_first[0]["finish_s"]
+    assert rel_l1(late[0]["output"], _oracle_euler(late[0])) <= 2e-5
+    ref = oracle.eikonal_fmm(late[1]["input"].astype(np.float64), late[1]["h"], late[1]["sources"])
+    assert rel_l1(late[1]["output"][None], ref[None]) <= 1e-4
+    # the long one equals the same problem on the single-field path
+    f = R.ripple_field_create(ctx, (256, 256), 4, R.RIPPLE_SOA, 1, R.RIPPLE_F32)
+    try:
+        R.ripple_field_upload(f, first[0]["input"])
+        R.ripple_fv_step(f, R.make_fv_params(first[0]["dx"]), 3000)
+        single = R.ripple_field_download(f)
+    finally:
+        R.ripple_field_destroy(f)
+    assert rel_l1(first[0]["output"], single) <= 1e-5
+    stats = R.ripple_batch_get_stats(ctx)
+    assert stats["completed"] == 4 and stats["failed"] == 0
+
+
+def test_poll_and_unknown_ticket(ctx):
+    t = R.ripple_batch_submit(ctx, [_euler(40, 40, 0.2, 200)])[0]
+    seen_not_ready = R.ripple_poll(ctx, t) is None
+    info = R.ripple_wait(ctx, t, 60000)
+    assert info["status"] == R.RIPPLE_OK
+    assert seen_not_ready or info["finish_s"] > 0
+    with pytest.raises(R.RippleError) as ei:
+        R.ripple_poll(ctx, t)  # retired
+    assert ei.value.status == R.RIPPLE_ERR_INVALID
+
+
+def test_numeric_error_reported_per_request(ctx):
+    bad = _euler(40, 40, 0.2, 5)
+    bad["input"][3, 10, 10] = -1.0  # negative energy -> negative pressure
+    good = _euler(40, 40, 0.2, 5)
+    infos = _run(ctx, [bad, good])
+    assert infos[0]["status"] == R.RIPPLE_ERR_NUMERIC
+    assert infos[1]["status"] == R.RIPPLE_OK
+
+
+def test_autotune_picks_a_candidate(ctx):
+    sides = [s for s, _ in inputs.batch_problems(32, seed=2)]
+    cfg, timings = R.ripple_batch_autotune(ctx, sides)
+    assert cfg["layout"] in (R.RIPPLE_SOA, R.RIPPLE_AOS) and 0 <= cfg["tile_variant"] < 3
+    assert all(v > 0 for v in timings.values())
+    assert timings[(cfg["layout"], cfg["tile_variant"])] == min(timings.values())
