@@ -41,6 +41,7 @@ N3 = 256
 NSTEPS_SOLVE = 50
 BYTES_PER_CELL_UPDATE = 40  # FP32, 5 components: 20 B read + 20 B written per cell per step
 METRIC = "cell-updates/s"
+ACTIVE_CELLS = 4 << 20  # serving: per-step cell budget of stepped Euler problems
 
 
 def load_peaks():
@@ -266,12 +267,189 @@ def bench_gpu(args, rank, world, local):
             R.ripple_field_destroy(ft)
 
     R.ripple_ctx_destroy(ctx)
+    batched = None if args.skip_batched else bench_batched(R, torch, local)
+    serve = None if args.skip_serve else bench_serving(R, torch, local)
     value = world * args.steps * ncell / (ms_max / 1e3)
     hbm_peak, peak_kind = load_peaks()
     achieved = BYTES_PER_CELL_UPDATE * ncell / (ms / args.steps / 1e3) / 1e9
     return dict(value=value, ms_per_step=ms_max / args.steps, clocks=clocks, ms_aos=ms_aos / args.steps,
                 e2e_value=e2e_value, e2e_s=e2e_s, e2e_solves=e2e_solves, ms2=ms2, eik=eik,
-                achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result)
+                achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result, batched=batched,
+                serve=serve)
+
+
+def bench_batched(R, torch, local, nsteps=100, count=512):
+    """512 independent 2D Euler problems (sides log-uniform in [32, 512], FP32,
+    sine density with per-instance amplitude, periodic Rusanov, 100 steps):
+    one batched launch per global step (autotuned layout and tile shape, CUDA
+    graphs) against the per-instance launch loop on the same GPU."""
+    probs = inputs.batch_problems(count, seed=1)
+    states = [inputs.euler2d_sine(side, amp=amp).astype(np.float32) for side, amp in probs]
+    sides = [side for side, _ in probs]
+    cells = float(sum(side * side for side in sides))
+    ctx = R.ripple_ctx_create(local)
+    try:
+        cfg, timings = R.ripple_batch_autotune(ctx, sides)
+        R.ripple_batch_configure(ctx, layout=cfg["layout"], tile_variant=cfg["tile_variant"],
+                                 steps_per_sync=nsteps, use_graphs=True)
+
+        def run_batch():
+            reqs = [R.euler_request(U, nsteps, [1.0 / U.shape[2], 1.0 / U.shape[1]]) for U in states]
+            t0 = time.perf_counter()
+            tickets = R.ripple_batch_submit(ctx, reqs)
+            infos = [R.ripple_wait(ctx, t, 600000) for t in tickets]
+            dt = time.perf_counter() - t0
+            assert all(i["status"] == R.RIPPLE_OK for i in infos), "batched run failed"
+            return reqs, infos, dt
+
+        run_batch()  # warm-up: table capacities, graph capture
+        st0 = R.ripple_batch_get_stats(ctx)
+        reqs, infos, t_batch = run_batch()
+        st1 = R.ripple_batch_get_stats(ctx)
+        span = max(i["finish_s"] for i in infos) - min(i["start_s"] for i in infos)
+        # per-instance launch loop over device-resident fields (no transfers timed)
+        fields = []
+        for U in states:
+            f = R.ripple_field_create(ctx, (U.shape[2], U.shape[1]), 4, R.RIPPLE_SOA, 1, R.RIPPLE_F32)
+            R.ripple_field_upload(f, U)
+            fields.append(f)
+        prms = [R.make_fv_params([1.0 / U.shape[2], 1.0 / U.shape[1]]) for U in states]
+        for f, prm in zip(fields, prms):  # warm-up: second buffers, prep, tensor maps
+            R.ripple_fv_step(f, prm, 0)
+        for f, U in zip(fields, states):
+            R.ripple_field_upload(f, U)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for f, prm in zip(fields, prms):
+            R.ripple_fv_step(f, prm, nsteps, stats=False)
+        R.ripple_ctx_sync(ctx)
+        t_loop = time.perf_counter() - t0
+        worst = 0.0
+        for f, req in zip(fields, reqs):
+            loop_out = R.ripple_field_download(f)
+            a = np.abs(req["output"].astype(np.float64) - loop_out).reshape(4, -1).sum(1)
+            b = np.abs(loop_out.astype(np.float64)).reshape(4, -1).sum(1)
+            worst = max(worst, float((a / b).max()))
+            R.ripple_field_destroy(f)
+    finally:
+        R.ripple_ctx_destroy(ctx)
+    return {
+        "workload": f"{count} x 2D Euler FP32 Rusanov, sides log-uniform [32,512], {nsteps} steps",
+        "instances": count, "total_cells": int(cells), "steps": nsteps,
+        "value": cells * nsteps / t_batch, "unit": METRIC,
+        "batched_seconds_end_to_end": t_batch,
+        "batched_compute_span_s": span,
+        "batched_value_compute_span": cells * nsteps / span,
+        "launches": st1["launches"] - st0["launches"], "graph_replays": st1["graph_replays"] - st0["graph_replays"],
+        "per_instance_loop_value": cells * nsteps / t_loop, "per_instance_loop_seconds": t_loop,
+        "per_instance_loop_launches": count * nsteps,
+        "speedup_vs_loop": t_loop / t_batch,
+        "max_rel_l1_vs_loop": worst,
+        "autotune": {"layout": "SoA" if cfg["layout"] == R.RIPPLE_SOA else "AoS",
+                     "tile": ["32x8", "64x4", "16x16"][cfg["tile_variant"]],
+                     "ms_per_global_step": {f"{'SoA' if k[0] == R.RIPPLE_SOA else 'AoS'}/{['32x8', '64x4', '16x16'][k[1]]}": v
+                                            for k, v in timings.items()}},
+    }
+
+
+def _serve_requests(R, reqs_spec):
+    out = []
+    for r in reqs_spec:
+        side = r["side"]
+        if r["kind"] == "euler":
+            U = inputs.euler2d_sine(side, amp=r["amp"]).astype(np.float32)
+            out.append((r, U, None))
+        else:
+            s = inputs.eikonal_slowness((side, side), seed=r["seed"]).astype(np.float32)
+            src = inputs.eikonal_sources((side, side), seed=r["seed"], count=r["nsrc"])
+            out.append((r, s, src))
+    return out
+
+
+def _make_req(R, r, data, src):
+    side = r["side"]
+    if r["kind"] == "euler":
+        return R.euler_request(data, r["steps"], [1.0 / side, 1.0 / side])
+    return R.eikonal_request(data, src, 1.0 / side, tol=1e-6)
+
+
+def bench_serving(R, torch, local, rates=(50, 500, 2000), count=160):
+    """Poisson arrivals of mixed requests (70 % 2D Euler side log-U[64,1024],
+    50-500 steps; 30 % 2D eikonal side log-U[128,1024], 1-4 sources) under a
+    40 GB budget.  Latency = submit -> result in host memory.  Baseline: the
+    same arrival stream served one request at a time through the single-field
+    API (service times measured here, queue replayed)."""
+    spec_all = inputs.serve_stream(1.0, count, seed=1)
+    prepared = _serve_requests(R, spec_all)
+    work_euler = sum(r["side"] ** 2 * r["steps"] for r in spec_all if r["kind"] == "euler")
+    cells_eik = sum(r["side"] ** 2 for r in spec_all if r["kind"] == "eikonal")
+    result = {"requests_per_rate": count, "mix": "70% Euler / 30% eikonal", "budget_gb": 40,
+              "policy": f"least remaining work first, {ACTIVE_CELLS} active cells per step, 4 FIM iterations per step",
+              "euler_cell_updates": int(work_euler), "eikonal_cells": int(cells_eik), "rates": {}}
+    # sequential baseline: service time of every request alone, through fields
+    ctx = R.ripple_ctx_create(local)
+    R.use_torch_allocator(ctx, local)  # cached allocations: no cudaMalloc per request
+    service = []
+    try:
+        for (r, data, src) in prepared:
+            side = r["side"]
+            t0 = time.perf_counter()
+            if r["kind"] == "euler":
+                f = R.ripple_field_create(ctx, (side, side), 4, R.RIPPLE_SOA, 1, R.RIPPLE_F32)
+                R.ripple_field_upload(f, data)
+                R.ripple_fv_step(f, R.make_fv_params([1.0 / side] * 2), r["steps"], stats=False)
+                R.ripple_field_download(f)
+                R.ripple_field_destroy(f)
+            else:
+                fs = R.ripple_field_create(ctx, (side, side), 1, R.RIPPLE_SOA, 0, R.RIPPLE_F32)
+                ft = R.ripple_field_create(ctx, (side, side), 1, R.RIPPLE_SOA, 1, R.RIPPLE_F32)
+                R.ripple_field_upload(fs, data)
+                R.ripple_eikonal_solve(fs, ft, src, 1.0 / side, 1e-6)
+                R.ripple_field_download(ft)
+                R.ripple_field_destroy(fs)
+                R.ripple_field_destroy(ft)
+            service.append(time.perf_counter() - t0)
+    finally:
+        R.ripple_ctx_destroy(ctx)
+    ctx = R.ripple_ctx_create(local, 40 << 30)
+    try:
+        R.ripple_batch_configure(ctx, steps_per_sync=8, use_graphs=True, active_cells=ACTIVE_CELLS)
+        warm = [_make_req(R, r, d, s) for (r, d, s) in prepared[:8]]
+        for t in R.ripple_batch_submit(ctx, warm):
+            R.ripple_wait(ctx, t, 600000)
+        for rate in rates:
+            arrivals = [r["t"] for r in inputs.serve_stream(rate, count, seed=1)]
+            reqs = [_make_req(R, r, d, s) for (r, d, s) in prepared]
+            tickets = []
+            t0 = time.perf_counter()
+            for a, req in zip(arrivals, reqs):
+                delay = t0 + a - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets.append(R.ripple_batch_submit(ctx, [req])[0])
+            infos = [R.ripple_wait(ctx, t, 600000) for t in tickets]
+            makespan = time.perf_counter() - t0
+            ok = sum(1 for i in infos if i["status"] == R.RIPPLE_OK)
+            lat = np.array([i["finish_s"] - i["submit_s"] for i in infos]) * 1e3
+            # baseline queue: one request at a time in arrival order
+            clock, blat = 0.0, []
+            for a, svc in zip(arrivals, service):
+                clock = max(clock, a) + svc
+                blat.append((clock - a) * 1e3)
+            blat = np.array(blat)
+            base_makespan = clock
+            result["rates"][str(rate)] = {
+                "completed": ok, "makespan_s": makespan,
+                "cell_updates_per_s": work_euler / makespan, "eikonal_cells_per_s": cells_eik / makespan,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "baseline_sequential": {"makespan_s": base_makespan,
+                                        "cell_updates_per_s": work_euler / base_makespan,
+                                        "p50_ms": float(np.percentile(blat, 50)),
+                                        "p99_ms": float(np.percentile(blat, 99))},
+            }
+    finally:
+        R.ripple_ctx_destroy(ctx)
+    return result
 
 
 def cpu_baseline_sample():
@@ -294,6 +472,8 @@ def main():
     ap.add_argument("--e2e-solves", type=int, default=2)
     ap.add_argument("--skip-eikonal", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-batched", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_setup(args.gpus)
@@ -354,6 +534,8 @@ def main():
         "euler2d_fp64_128": {"ms_per_100_steps": r["ms2"], "us_per_step": r["ms2"] * 10.0,
                              "cell_updates_per_s": 100 * 128 * 128 / (r["ms2"] / 1e3)},
         "eikonal": r["eik"],
+        "batched": r["batched"],
+        "serve": r["serve"],
     }
     print(json.dumps(line))
 

@@ -258,19 +258,25 @@ typedef struct {
 typedef struct {
     ripple_layout layout;     /* layout of resident Euler states */
     int tile_variant;         /* 0: 32x8, 1: 64x4, 2: 16x16 Euler tiles */
-    int steps_per_sync;       /* global steps queued between scheduler checks (latency vs overhead) */
+    int steps_per_sync;       /* most global steps queued between scheduler checks (fewer when an
+                                 Euler problem ends sooner): latency of joining vs overhead */
     int use_graphs;           /* replay queued steps from captured CUDA graphs */
     ripple_dtype dtype;       /* element type of every request of this context */
+    int fim_iters_per_step;   /* eikonal FIM iterations run per Euler global step (1..64) */
+    int64_t active_cells;     /* per-step cell budget of stepped Euler problems, chosen by least
+                                 remaining work (0 = step every resident problem) */
 } ripple_batch_config;
 
 typedef struct {
     int64_t submitted, admitted, completed, failed;
     int64_t global_steps, launches, graph_replays;
     double now_s;             /* runtime clock now */
+    int64_t fim_iterations;   /* eikonal iterations issued */
 } ripple_batch_stats;
 
-/* Set the batch configuration (defaults: SoA, 32x8, 8 steps per sync, graphs
- * on, F32).  Only while no request is in flight. */
+/* Set the batch configuration (defaults: SoA, 32x8, 16 steps per sync, graphs
+ * on, F32, 4 FIM iterations per step, no cell budget).  Only while no request
+ * is in flight. */
 RIPPLE_API ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* cfg);
 
 /* Queue n requests; tickets_out[i] identifies request i.  Validates every

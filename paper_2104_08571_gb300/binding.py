@@ -93,13 +93,14 @@ class ripple_ticket_info(ctypes.Structure):
 
 class ripple_batch_config(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int), ("tile_variant", ctypes.c_int), ("steps_per_sync", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("dtype", ctypes.c_int)]
+                ("use_graphs", ctypes.c_int), ("dtype", ctypes.c_int), ("fim_iters_per_step", ctypes.c_int),
+                ("active_cells", ctypes.c_int64)]
 
 
 class ripple_batch_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("global_steps", ctypes.c_int64), ("launches", ctypes.c_int64),
-                ("graph_replays", ctypes.c_int64), ("now_s", ctypes.c_double)]
+                ("graph_replays", ctypes.c_int64), ("now_s", ctypes.c_double), ("fim_iterations", ctypes.c_int64)]
 
 # name -> (argtypes) ; every ABI function returns ripple_status (int)
 _SIGNATURES = {
@@ -360,9 +361,10 @@ def _info_dict(info):
                 cell_updates=info.cell_updates, t=info.t)
 
 
-def ripple_batch_configure(ctx, layout=RIPPLE_SOA, tile_variant=0, steps_per_sync=8, use_graphs=True,
-                           dtype=RIPPLE_F32):
-    cfg = ripple_batch_config(int(layout), int(tile_variant), int(steps_per_sync), int(bool(use_graphs)), int(dtype))
+def ripple_batch_configure(ctx, layout=RIPPLE_SOA, tile_variant=0, steps_per_sync=16, use_graphs=True,
+                           dtype=RIPPLE_F32, fim_iters_per_step=4, active_cells=0):
+    cfg = ripple_batch_config(int(layout), int(tile_variant), int(steps_per_sync), int(bool(use_graphs)), int(dtype),
+                              int(fim_iters_per_step), int(active_cells))
     _check(load().ripple_batch_configure(ctx, ctypes.byref(cfg)), "ripple_batch_configure")
 
 
@@ -442,7 +444,7 @@ def ripple_batch_get_stats(ctx):
 def ripple_batch_autotune(ctx, sides, dtype=RIPPLE_F32):
     """Returns (chosen config dict, {(layout, variant): ms per global step})."""
     arr = (ctypes.c_int64 * len(sides))(*[int(x) for x in sides])
-    cfg = ripple_batch_config(RIPPLE_SOA, 0, 8, 1, int(dtype))
+    cfg = ripple_batch_config(RIPPLE_SOA, 0, 16, 1, int(dtype), 4, 0)
     ms = (ctypes.c_double * 6)()
     _check(load().ripple_batch_autotune(ctx, arr, len(sides), int(dtype), ctypes.byref(cfg), ms),
            "ripple_batch_autotune")
@@ -451,4 +453,5 @@ def ripple_batch_autotune(ctx, sides, dtype=RIPPLE_F32):
         for v in range(3):
             timings[(lay, v)] = ms[li * 3 + v]
     return dict(layout=cfg.layout, tile_variant=cfg.tile_variant, steps_per_sync=cfg.steps_per_sync,
-                use_graphs=cfg.use_graphs, dtype=cfg.dtype), timings
+                use_graphs=cfg.use_graphs, dtype=cfg.dtype, fim_iters_per_step=cfg.fim_iters_per_step,
+                active_cells=cfg.active_cells), timings

@@ -38,10 +38,11 @@ constexpr BatchTileShape kBatchVariants[kNumBatchVariants] = {{32, 8}, {64, 4}, 
 
 template <typename T, int LAYOUT, int V>
 static cudaError_t step_v(int grid, cudaStream_t s, const BatchEuler* e, const void* f, const int* table,
-                          BatchCtl* c)
+                          BatchCtl* c, int kind)
 {
     constexpr int TX = kBatchVariants[V].tx, TY = kBatchVariants[V].ty;
-    batch_step_kernel<T, LAYOUT, TX, TY><<<grid, 256, 0, s>>>(e, static_cast<const BatchFim<T>*>(f), table, c);
+    batch_step_kernel<T, LAYOUT, TX, TY><<<grid, 256, 0, s>>>(e, static_cast<const BatchFim<T>*>(f), table, c,
+                                                               kind);
     return cudaGetLastError();
 }
 template <typename T, int LAYOUT, int V>
@@ -54,20 +55,20 @@ static int occ_v()
 }
 template <typename T, int LAYOUT>
 static cudaError_t step_l(int v, int grid, cudaStream_t s, const BatchEuler* e, const void* f, const int* t,
-                          BatchCtl* c)
+                          BatchCtl* c, int kind)
 {
-    if (v == 1) return step_v<T, LAYOUT, 1>(grid, s, e, f, t, c);
-    if (v == 2) return step_v<T, LAYOUT, 2>(grid, s, e, f, t, c);
-    return step_v<T, LAYOUT, 0>(grid, s, e, f, t, c);
+    if (v == 1) return step_v<T, LAYOUT, 1>(grid, s, e, f, t, c, kind);
+    if (v == 2) return step_v<T, LAYOUT, 2>(grid, s, e, f, t, c, kind);
+    return step_v<T, LAYOUT, 0>(grid, s, e, f, t, c, kind);
 }
 static cudaError_t launch_batch_step(ripple_dtype dt, int layout, int v, int grid, cudaStream_t s,
-                                     const BatchEuler* e, const void* f, const int* t, BatchCtl* c)
+                                     const BatchEuler* e, const void* f, const int* t, BatchCtl* c, int kind)
 {
     if (dt == RIPPLE_F32)
-        return layout == LAYOUT_SOA ? step_l<float, LAYOUT_SOA>(v, grid, s, e, f, t, c)
-                                    : step_l<float, LAYOUT_AOS>(v, grid, s, e, f, t, c);
-    return layout == LAYOUT_SOA ? step_l<double, LAYOUT_SOA>(v, grid, s, e, f, t, c)
-                                : step_l<double, LAYOUT_AOS>(v, grid, s, e, f, t, c);
+        return layout == LAYOUT_SOA ? step_l<float, LAYOUT_SOA>(v, grid, s, e, f, t, c, kind)
+                                    : step_l<float, LAYOUT_AOS>(v, grid, s, e, f, t, c, kind);
+    return layout == LAYOUT_SOA ? step_l<double, LAYOUT_SOA>(v, grid, s, e, f, t, c, kind)
+                                : step_l<double, LAYOUT_AOS>(v, grid, s, e, f, t, c, kind);
 }
 static int batch_occupancy(ripple_dtype dt, int layout, int v)
 {
@@ -109,7 +110,9 @@ struct Inst {
     void* scratch = nullptr;
     int slot = -1;
     int ntiles = 0, tiles_x = 0, ntx = 0, nty = 0;
-    long long start_step = -1;
+    long long start_step = -1;  // Euler: launch index of local step 0 (recomputed on resume)
+    long long steps_done = 0;   // Euler steps completed
+    bool active = false;        // Euler: stepped in the current rounds
     cudaEvent_t ev = nullptr;
     ripple_status result = RIPPLE_OK;
     double t_submit = 0, t_admit = 0, t_start = 0, t_finish = 0;
@@ -129,7 +132,7 @@ struct BatchRuntime {
     std::deque<Inst*> pending;                      // guarded by mu
     std::unordered_map<uint64_t, Ticket> tickets;   // guarded by mu
     uint64_t next_ticket = 1;                       // guarded by mu
-    ripple_batch_config cfg{RIPPLE_SOA, 0, 8, 1, RIPPLE_F32};
+    ripple_batch_config cfg{RIPPLE_SOA, 0, 16, 1, RIPPLE_F32, 4, 0};
     ripple_batch_stats stats{};                     // guarded by mu
     Clock::time_point epoch = Clock::now();
     // scheduler-thread state
@@ -155,10 +158,12 @@ struct BatchRuntime {
     int* h_table = nullptr;
     int cap_e = 0, cap_f = 0, cap_t = 0;
     bool dirty = true;
-    long long gstep = 0;  // global steps issued (== device counter after completion)
+    bool has_e = false, has_f = false;  // resident kinds (set by rebuild_tables)
+    long long gstep_e = 0;  // Euler steps issued (== device counter once they completed)
+    long long gstep_f = 0;  // FIM iterations issued
     int grid = 0;
-    std::map<int, cudaGraphExec_t> graphs;
-    int graph_variant = -1, graph_layout = -1;
+    std::map<int, cudaGraphExec_t> graphs;  // key: (steps << 2) | has_euler << 1 | has_fim
+    int graph_variant = -1, graph_layout = -1, graph_fim = -1;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - epoch).count(); }
 };
@@ -349,6 +354,10 @@ static ripple_status start_download(BatchRuntime* rt, Inst* in)
     RIPPLE_CUDA(cudaMemcpyAsync(r.output, stage, dense, cudaMemcpyDeviceToHost, s));
     RIPPLE_CUDA(cudaMemcpyAsync(&rt->h_ctl[in->slot], &rt->slot_ctl[in->slot], sizeof(FieldCtl),
                                 cudaMemcpyDeviceToHost, s));
+    RIPPLE_CUDA(cudaMemcpyAsync(&rt->h_status[in->slot], &rt->slot_status[in->slot], sizeof(unsigned long long),
+                                cudaMemcpyDeviceToHost, s));
+    RIPPLE_CUDA(cudaMemcpyAsync(&rt->h_counters[in->slot * 3], &rt->slot_counters[in->slot * 3], 3 * sizeof(long long),
+                                cudaMemcpyDeviceToHost, s));
     RIPPLE_CUDA(cudaEventRecord(in->ev, s));
     return RIPPLE_OK;
 }
@@ -396,6 +405,7 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
 {
     int ne = 0, nf = 0, nt = 0;
     for (Inst* in : rt->resident) {
+        if (in->req.kind == RIPPLE_REQ_EULER && !in->active) continue;
         if (in->req.kind == RIPPLE_REQ_EULER) ++ne;
         else ++nf;
         nt += in->ntiles;
@@ -405,8 +415,16 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
     // the previous launches may still read the pinned mirrors' device copies:
     // the compute stream is idle here (the scheduler synchronises every K steps)
     int ie = 0, jf = 0, t = 0;
-    for (Inst* in : rt->resident) {
+    // Euler tiles first, then eikonal tiles (each kind has its own launches)
+    std::vector<Inst*> order;
+    for (Inst* in : rt->resident)
+        if (in->req.kind == RIPPLE_REQ_EULER && in->active) order.push_back(in);
+    for (Inst* in : rt->resident)
+        if (in->req.kind != RIPPLE_REQ_EULER) order.push_back(in);
+    int nt_e = 0;
+    for (Inst* in : order) {
         if (in->req.kind == RIPPLE_REQ_EULER) {
+            nt_e += in->ntiles;
             BatchEuler& e = rt->h_euler[ie];
             e.buf[0] = in->buf[0];
             e.buf[1] = in->buf[1];
@@ -438,41 +456,57 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
     if (nf)
         RIPPLE_CUDA(cudaMemcpyAsync(rt->d_fim, rt->h_fim, nf * fim_elem_size(rt->cfg.dtype), cudaMemcpyHostToDevice, s));
     if (nt) RIPPLE_CUDA(cudaMemcpyAsync(rt->d_table, rt->h_table, nt * sizeof(int), cudaMemcpyHostToDevice, s));
-    RIPPLE_CUDA(cudaMemcpyAsync(&rt->d_bctl->ntiles, &nt, sizeof(int), cudaMemcpyHostToDevice, s));
-    RIPPLE_CUDA(cudaStreamSynchronize(s));  // nt lives on this stack frame
+    const int counts[2] = {nt_e, nt};
+    RIPPLE_CUDA(cudaMemcpyAsync(&rt->d_bctl->ntiles_e, counts, sizeof(counts), cudaMemcpyHostToDevice, s));
+    RIPPLE_CUDA(cudaStreamSynchronize(s));  // counts live on this stack frame
+    rt->has_e = ne > 0;
+    rt->has_f = nf > 0;
     rt->dirty = false;
     return RIPPLE_OK;
 }
 
+// Queue K units of work on the compute stream; a unit is one Euler step of
+// every resident Euler problem followed by F FIM iterations of every resident
+// eikonal problem (F = fim_iters_per_step), either kind omitted when absent.
 static ripple_status launch_steps(BatchRuntime* rt, int K)
 {
     const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
-    auto one = [&]() {
-        return launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->grid, rt->compute, rt->d_euler,
-                                 rt->d_fim, rt->d_table, rt->d_bctl);
+    const int F = std::max(1, rt->cfg.fim_iters_per_step);
+    auto unit = [&]() -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        if (rt->has_e)
+            e = launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->grid, rt->compute, rt->d_euler,
+                                  rt->d_fim, rt->d_table, rt->d_bctl, 0);
+        for (int f = 0; f < F && rt->has_f && e == cudaSuccess; ++f)
+            e = launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->grid, rt->compute, rt->d_euler,
+                                  rt->d_fim, rt->d_table, rt->d_bctl, 1);
+        return e;
     };
+    const int per_unit = (rt->has_e ? 1 : 0) + (rt->has_f ? F : 0);
     if (!rt->cfg.use_graphs) {
-        for (int k = 0; k < K; ++k) RIPPLE_CUDA(one());
+        for (int k = 0; k < K; ++k) RIPPLE_CUDA(unit());
         std::lock_guard<std::mutex> lk(rt->mu);
-        rt->stats.launches += K;
+        rt->stats.launches += (int64_t)K * per_unit;
         return RIPPLE_OK;
     }
-    if (rt->graph_variant != rt->cfg.tile_variant || rt->graph_layout != layout) {
+    if (rt->graph_variant != rt->cfg.tile_variant || rt->graph_layout != layout || rt->graph_fim != F) {
         for (auto& g : rt->graphs) cudaGraphExecDestroy(g.second);
         rt->graphs.clear();
         rt->graph_variant = rt->cfg.tile_variant;
         rt->graph_layout = layout;
+        rt->graph_fim = F;
     }
     // K as a sum of powers of two, each replayed from a captured graph
     for (int bit = 30; bit >= 0; --bit) {
         const int n = 1 << bit;
         if (!(K & n)) continue;
-        auto it = rt->graphs.find(n);
+        const int key = (n << 2) | (rt->has_e ? 2 : 0) | (rt->has_f ? 1 : 0);
+        auto it = rt->graphs.find(key);
         if (it == rt->graphs.end()) {
             cudaGraph_t g = nullptr;
             RIPPLE_CUDA(cudaStreamBeginCapture(rt->compute, cudaStreamCaptureModeThreadLocal));
             cudaError_t e = cudaSuccess;
-            for (int k = 0; k < n && e == cudaSuccess; ++k) e = one();
+            for (int k = 0; k < n && e == cudaSuccess; ++k) e = unit();
             cudaError_t e2 = cudaStreamEndCapture(rt->compute, &g);
             if (e != cudaSuccess) return cuda_fail(e, "batched step capture");
             if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
@@ -480,44 +514,74 @@ static ripple_status launch_steps(BatchRuntime* rt, int K)
             e = cudaGraphInstantiate(&ex, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-            it = rt->graphs.emplace(n, ex).first;
+            it = rt->graphs.emplace(key, ex).first;
         }
         RIPPLE_CUDA(cudaGraphLaunch(it->second, rt->compute));
         std::lock_guard<std::mutex> lk(rt->mu);
-        rt->stats.launches += n;
+        rt->stats.launches += (int64_t)n * per_unit;
         rt->stats.graph_replays += 1;
     }
     return RIPPLE_OK;
 }
 
-// One scheduler round of compute: K global steps over the resident set.
+// One scheduler round of compute: K units over the resident set (K is the
+// configured cap, lowered so that no Euler problem runs past its last step).
 static ripple_status compute_round(BatchRuntime* rt)
 {
+    // Active set: resident Euler problems in order of least remaining work
+    // (cells x steps) while their cells fit the per-step budget (at least
+    // one); eikonal problems always iterate.  A problem that (re)joins the
+    // active set continues from its own step count.
+    {
+        std::vector<Inst*> eu;
+        for (Inst* in : rt->resident)
+            if (in->req.kind == RIPPLE_REQ_EULER) eu.push_back(in);
+        std::stable_sort(eu.begin(), eu.end(), [](const Inst* a, const Inst* b) {
+            const double wa = (double)a->req.dims[0] * a->req.dims[1] * (double)(a->req.nsteps - a->steps_done);
+            const double wb = (double)b->req.dims[0] * b->req.dims[1] * (double)(b->req.nsteps - b->steps_done);
+            return wa < wb;
+        });
+        const int64_t budget = rt->cfg.active_cells;
+        int64_t cells = 0;
+        for (Inst* in : eu) {
+            const int64_t c = in->req.dims[0] * in->req.dims[1];
+            const bool take = budget <= 0 || cells == 0 || cells + c <= budget;
+            if (take) cells += c;
+            if (take != in->active) {
+                in->active = take;
+                if (take) in->start_step = rt->gstep_e - in->steps_done;
+                rt->dirty = true;
+            }
+        }
+    }
     if (rt->dirty) {
         ripple_status st = rebuild_tables(rt);
         if (st != RIPPLE_OK) return st;
     }
     long long K = std::max(1, rt->cfg.steps_per_sync);
     for (Inst* in : rt->resident)
-        if (in->req.kind == RIPPLE_REQ_EULER) K = std::min(K, in->start_step + in->req.nsteps - rt->gstep);
+        if (in->req.kind == RIPPLE_REQ_EULER && in->active) K = std::min(K, in->req.nsteps - in->steps_done);
     K = std::max(1LL, K);
     ripple_status st = launch_steps(rt, (int)K);
     if (st != RIPPLE_OK) return st;
-    RIPPLE_CUDA(cudaMemcpyAsync(rt->h_status, rt->slot_status, kSlots * sizeof(unsigned long long),
-                                cudaMemcpyDeviceToHost, rt->compute));
-    RIPPLE_CUDA(cudaMemcpyAsync(rt->h_counters, rt->slot_counters, kSlots * 3 * sizeof(long long),
-                                cudaMemcpyDeviceToHost, rt->compute));
+    if (rt->has_f)
+        RIPPLE_CUDA(cudaMemcpyAsync(rt->h_status, rt->slot_status, kSlots * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, rt->compute));
     RIPPLE_CUDA(cudaEventRecord(rt->ev_step, rt->compute));
     RIPPLE_CUDA(cudaEventSynchronize(rt->ev_step));
-    rt->gstep += K;
+    if (rt->has_e) rt->gstep_e += K;
+    for (Inst* in : rt->resident)
+        if (in->req.kind == RIPPLE_REQ_EULER && in->active) in->steps_done += K;
+    if (rt->has_f) rt->gstep_f += K * std::max(1, rt->cfg.fim_iters_per_step);
     {
         std::lock_guard<std::mutex> lk(rt->mu);
-        rt->stats.global_steps = rt->gstep;
+        rt->stats.global_steps = rt->gstep_e;
+        rt->stats.fim_iterations = rt->gstep_f;
     }
     std::vector<Inst*> keep;
     for (Inst* in : rt->resident) {
         bool fin = false;
-        if (in->req.kind == RIPPLE_REQ_EULER) fin = rt->gstep - in->start_step >= in->req.nsteps;
+        if (in->req.kind == RIPPLE_REQ_EULER) fin = in->steps_done >= in->req.nsteps;
         else fin = rt->h_status[in->slot] != 0ull;
         if (!fin) {
             keep.push_back(in);
@@ -585,7 +649,9 @@ static void scheduler(BatchRuntime* rt)
         for (size_t i = 0; i < rt->uploading.size();) {
             Inst* in = rt->uploading[i];
             if (cudaEventQuery(in->ev) == cudaSuccess) {
-                in->start_step = rt->gstep;
+                in->start_step = in->req.kind == RIPPLE_REQ_EULER ? rt->gstep_e : rt->gstep_f;
+                in->steps_done = 0;
+                in->active = false;  // the next round's active-set pass decides
                 in->t_start = rt->now();
                 rt->resident.push_back(in);
                 rt->dirty = true;
@@ -653,7 +719,8 @@ static ripple_status rt_start(BatchRuntime* rt)
     const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
     const int occ = std::max(1, batch_occupancy(rt->cfg.dtype, layout, rt->cfg.tile_variant));
     rt->grid = occ * rt->ctx->sm_count;
-    rt->gstep = 0;
+    rt->gstep_e = 0;
+    rt->gstep_f = 0;
     rt->started = true;
     rt->th = std::thread(scheduler, rt);
     return RIPPLE_OK;
@@ -745,7 +812,9 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
             cudaMalloc(&d_e, n * sizeof(BatchEuler));
             cudaMalloc(&d_t, table.size() * sizeof(int));
             cudaMalloc(&d_c, sizeof(BatchCtl));
-            BatchCtl hb{0ull, 0u, (int)table.size()};
+            BatchCtl hb{};
+            hb.ntiles_e = (int)table.size();
+            hb.ntiles = (int)table.size();
             cudaMemcpyAsync(d_e, h.data(), n * sizeof(BatchEuler), cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(d_t, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(d_c, &hb, sizeof(BatchCtl), cudaMemcpyHostToDevice, s);
@@ -756,11 +825,11 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
             cudaEventCreate(&e1);
             cudaError_t ce = cudaSuccess;
             for (int k = 0; k < 3 && ce == cudaSuccess; ++k)
-                ce = launch_batch_step(dt, lay_i, v, grid, s, d_e, nullptr, d_t, d_c);
+                ce = launch_batch_step(dt, lay_i, v, grid, s, d_e, nullptr, d_t, d_c, 0);
             cudaEventRecord(e0, s);
             const int reps = 6;
             for (int k = 0; k < reps && ce == cudaSuccess; ++k)
-                ce = launch_batch_step(dt, lay_i, v, grid, s, d_e, nullptr, d_t, d_c);
+                ce = launch_batch_step(dt, lay_i, v, grid, s, d_e, nullptr, d_t, d_c, 0);
             cudaEventRecord(e1, s);
             cudaStreamSynchronize(s);
             float el = 0.f;
@@ -831,6 +900,8 @@ ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* 
     if (cfg->layout != RIPPLE_AOS && cfg->layout != RIPPLE_SOA) return fail(RIPPLE_ERR_INVALID, "bad layout");
     if (cfg->tile_variant < 0 || cfg->tile_variant >= kNumBatchVariants) return fail(RIPPLE_ERR_INVALID, "bad tile variant");
     if (cfg->steps_per_sync < 1) return fail(RIPPLE_ERR_INVALID, "steps_per_sync must be >= 1");
+    if (cfg->fim_iters_per_step < 1 || cfg->fim_iters_per_step > 64)
+        return fail(RIPPLE_ERR_INVALID, "fim_iters_per_step must be 1..64");
     if (cfg->dtype != RIPPLE_F32 && cfg->dtype != RIPPLE_F64) return fail(RIPPLE_ERR_INVALID, "bad dtype");
     BatchRuntime* rt = runtime_of(ctx, true);
     std::lock_guard<std::mutex> lk(rt->mu);

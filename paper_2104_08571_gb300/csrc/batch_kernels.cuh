@@ -44,11 +44,14 @@ struct BatchFim {
     long long* counters;     // [3]: iterations, tile visits, Godunov updates
 };
 
-// Device-side control of a batch.
+// Device-side control of a batch.  Euler steps and FIM iterations advance on
+// separate launches with separate counters, so eikonal problems can iterate
+// several times per Euler step.
 struct BatchCtl {
-    unsigned long long gstep;  // global steps completed
-    unsigned int done;         // CTAs finished in the current launch
-    int ntiles;                // entries of the tile table
+    unsigned long long gstep[2];  // completed launches: [0] Euler steps, [1] FIM iterations
+    unsigned int done[2];         // CTAs finished in the current launch of each kind
+    int ntiles_e;                 // table entries [0, ntiles_e) are Euler tiles
+    int ntiles;                   // entries [ntiles_e, ntiles) are eikonal tiles
 };
 
 // Tile-table entry: (instance index << 1) | kind, kind 0 = Euler, 1 = eikonal.
@@ -204,20 +207,24 @@ __device__ __forceinline__ void batch_fim_tile(FimSmem<T, 2>& sm, const BatchFim
     }
 }
 
+// kind 0: one Euler step of every resident Euler problem; kind 1: one FIM
+// iteration of every resident eikonal problem.
 template <typename T, int LAYOUT, int TX, int TY>
 __global__ void __launch_bounds__(256) batch_step_kernel(const BatchEuler* __restrict__ euler,
                                                          const BatchFim<T>* __restrict__ fim,
-                                                         const int* __restrict__ table, BatchCtl* __restrict__ bctl)
+                                                         const int* __restrict__ table, BatchCtl* __restrict__ bctl,
+                                                         int kind)
 {
     static_assert(TX * TY == 256, "the batched step runs 256 threads (the FIM tile size)");
     __shared__ BatchSmem<T, LAYOUT, TX, TY> sm;
     __shared__ double red[8];
-    const unsigned long long gstep = __ldcg(&bctl->gstep);
-    const int ntiles = __ldcg(&bctl->ntiles);
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const unsigned long long gstep = __ldcg(&bctl->gstep[kind]);
+    const int begin = kind == 0 ? 0 : __ldcg(&bctl->ntiles_e);
+    const int end = kind == 0 ? __ldcg(&bctl->ntiles_e) : __ldcg(&bctl->ntiles);
+    for (int t = begin + blockIdx.x; t < end; t += gridDim.x) {
         const int entry = __ldg(&table[t]);
         const int idx = entry >> 1;
-        if ((entry & 1) == 0) {
+        if (kind == 0) {
             const BatchEuler& d = euler[idx];
             const long long local = (long long)gstep - d.start_step;
             if (local < 0 || local >= d.nsteps) continue;
@@ -231,14 +238,14 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const BatchEuler* __res
             batch_fim_tile<T>(sm.f, d, t - d.tile_begin, k);
         }
     }
-    // the last CTA to finish advances the global step counter
+    // the last CTA to finish advances this kind's counter
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        if (atomicAdd(&bctl->done, 1u) == gridDim.x - 1) {
-            bctl->done = 0u;
+        if (atomicAdd(&bctl->done[kind], 1u) == gridDim.x - 1) {
+            bctl->done[kind] = 0u;
             __threadfence();
-            atomicAdd(&bctl->gstep, 1ull);
+            atomicAdd(&bctl->gstep[kind], 1ull);
         }
     }
 }

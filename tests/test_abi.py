@@ -51,9 +51,9 @@ int main(void) {
          sizeof(ripple_eik_params), sizeof(ripple_eik_stats), sizeof(ripple_field_desc));
   printf("%zu %zu %zu\\n", offsetof(ripple_fv_params, scheme), offsetof(ripple_field_desc, dims),
          offsetof(ripple_field_desc, current));
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(ripple_request), offsetof(ripple_request, fv),
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(ripple_request), offsetof(ripple_request, fv),
          offsetof(ripple_request, nsrc), sizeof(ripple_ticket_info), sizeof(ripple_batch_config),
-         sizeof(ripple_batch_stats));
+         sizeof(ripple_batch_stats), offsetof(ripple_batch_config, active_cells));
   return 0;
 }
 """)
@@ -67,7 +67,7 @@ int main(void) {
             R.ripple_field_desc.dims.offset, R.ripple_field_desc.current.offset,
             ctypes.sizeof(R.ripple_request), R.ripple_request.fv.offset, R.ripple_request.nsrc.offset,
             ctypes.sizeof(R.ripple_ticket_info), ctypes.sizeof(R.ripple_batch_config),
-            ctypes.sizeof(R.ripple_batch_stats)]
+            ctypes.sizeof(R.ripple_batch_stats), R.ripple_batch_config.active_cells.offset]
     assert [int(x) for x in out] == want
 
 

@@ -78,6 +78,13 @@ def test_alone_equals_in_mix_bitwise(ctx):
     assert all(i["status"] == R.RIPPLE_OK for i in infos)
     assert np.array_equal(a2["output"], alone_a)
     assert np.array_equal(e2["output"], alone_e)
+    # with a small per-step cell budget problems are paused and resumed: same bits
+    R.ripple_batch_configure(ctx, active_cells=5000, steps_per_sync=5)
+    a3 = R.euler_request(a["input"], 37, a["dx"])
+    mix = [_euler(64, 64, 0.1, 80), a3, _euler(300, 40, 0.2, 15), _euler(33, 33, 0.3, 50)]
+    infos = _run(ctx, mix)
+    assert all(i["status"] == R.RIPPLE_OK and i["work"] == r["nsteps"] for i, r in zip(infos, mix))
+    assert np.array_equal(a3["output"], alone_a)
 
 
 def test_batch_matches_single_field_sweep(ctx):
@@ -96,7 +103,7 @@ def test_batch_matches_single_field_sweep(ctx):
 def test_graphs_and_sync_interval_do_not_change_results(ctx):
     reqs1 = [_euler(70, 50, 0.2, 33), _eik(90, 90, 7)]
     _run(ctx, reqs1)
-    R.ripple_batch_configure(ctx, steps_per_sync=3, use_graphs=False)
+    R.ripple_batch_configure(ctx, steps_per_sync=3, use_graphs=False, fim_iters_per_step=1)
     reqs2 = [R.euler_request(reqs1[0]["input"], 33, reqs1[0]["dx"]),
              R.eikonal_request(reqs1[1]["input"], reqs1[1]["sources"], reqs1[1]["h"])]
     _run(ctx, reqs2)
