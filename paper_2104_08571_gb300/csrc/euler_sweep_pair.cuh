@@ -1,0 +1,489 @@
+// FP32 Euler sweep on cell pairs (packed f32x2 arithmetic), sm_103a.
+//
+// Same step, staging and fusion as euler_sweep_kernel (see euler_sweep.cuh):
+// one launch = one explicit step, 2.5-D plane streaming through a TMA ring,
+// each face flux evaluated once, fused padding fill / CFL max / positivity.
+// What changes is the unit of work: every work item is a PAIR of x-adjacent
+// cells (or faces), held as f32x2 values, so each multiply, add and fma of
+// the reconstruction, predictor, flux and update arithmetic issues once for
+// two cells.  128 pair threads each own two neighbouring columns: they run
+// the z direction (in phase F) and the update; the x/y predicted states
+// (phase P) are pair items over all 256 threads and the x/y face fluxes
+// (phase F) pair items of the other 128 threads, which balances the phases.
+// The z stencil is read from the resident planes of the ring, so only the
+// high-face predicted state and the z face fluxes stay in registers.
+// Shared arrays are laid out so that every pair access of the SoA layout is
+// one 64-bit shared-memory access.  Tile: 32 x 8 cells.
+#pragma once
+#include <cuda.h>
+#include <cstdint>
+
+#include "euler_sweep.cuh"
+#include "pair_math.cuh"
+
+namespace ripple {
+
+template <int DIM, int LAYOUT, int SCHEME>
+struct PairCfg {
+    static constexpr int TX = 32, TY = 8, NT = 256, NPT = 128;
+    using C = SweepCfg<float, DIM, LAYOUT, SCHEME, TX, TY>;
+    static constexpr int NC = DIM + 2, R = C::R;
+    static constexpr int XR = TX + 2;                  // x-predicted cells per row (-1 .. TX)
+    static constexpr int NPX = XR * TY;                // x-predicted entries
+    static constexpr int NPY = TX * (TY + 2);          // y-predicted entries
+    static constexpr int NP = NPX + NPY;
+    static constexpr int FXR = TX + 2;                 // x-face row stride (TX + 1 faces, padded even)
+    static constexpr int NFX = FXR * TY, NFY = TX * (TY + 1);
+    static constexpr int XP = XR / 2;                  // x pairs per row (17)
+    static constexpr int NXP = XP * TY, NXPr = ((NXP + 31) / 32) * 32;
+    static constexpr int NYP = (TX / 2) * (TY + 2), NYPr = ((NYP + 31) / 32) * 32;
+    static constexpr int NXF = XP * TY, NXFr = ((NXF + 31) / 32) * 32;
+    static constexpr int NYF = (TX / 2) * (TY + 1), NYFr = ((NYF + 31) / 32) * 32;
+    static constexpr int KP = SCHEME == SCHEME_MUSCL ? (NXPr + NYPr + NT - 1) / NT : 0;
+    static constexpr int KF = (NXFr + NYFr + (NT - NPT) - 1) / (NT - NPT);  // on the non-pair threads
+    static constexpr int P_BYTES = SCHEME == SCHEME_MUSCL ? ((2 * NC * NP * 4 + 127) / 128) * 128 : 0;
+    static constexpr int F_BYTES = ((NC * (NFX + NFY) * 4 + 127) / 128) * 128;
+    static constexpr int SMEM = C::HDR_BYTES + C::NS * C::SLOT_BYTES + 2 * C::OUT_BYTES + P_BYTES + F_BYTES;
+    static_assert(C::OFF + R == 4 || LAYOUT == LAYOUT_AOS, "pairs at even x need an even in-slot x offset");
+    static_assert(C::BX % 2 == 0 && NP % 2 == 0 && NFX % 2 == 0 && NFY % 2 == 0, "64-bit aligned pairs");
+};
+
+template <int DIM, int LAYOUT, int SCHEME>
+__global__ void __launch_bounds__(256, 2)
+    euler_sweep_pair_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out,
+                            float* __restrict__ out, FieldCtl* __restrict__ ctl, const SweepGeom sg,
+                            const SweepParams prm)
+{
+    using PC = PairCfg<DIM, LAYOUT, SCHEME>;
+    using C = typename PC::C;
+    using PV = PlaneView<C, LAYOUT>;
+    constexpr int TX = PC::TX, TY = PC::TY, NC = PC::NC, R = PC::R, NS = C::NS, NT = PC::NT;
+    constexpr bool MUSCL = SCHEME == SCHEME_MUSCL;
+    constexpr int SX = LAYOUT == LAYOUT_SOA ? 1 : NC;
+    constexpr int SY = LAYOUT == LAYOUT_SOA ? C::BX : C::BX * NC;
+    constexpr int SM = LAYOUT == LAYOUT_SOA ? C::BX * C::BY : 1;
+    constexpr int NP = PC::NP;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
+    double* red = reinterpret_cast<double*>(smem + 64);
+    int* flags = reinterpret_cast<int*>(smem + 64 + 8 * 16);
+    float* ring = reinterpret_cast<float*>(smem + C::HDR_BYTES);
+    float* stage = reinterpret_cast<float*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES);
+    float* P = reinterpret_cast<float*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * C::OUT_BYTES);
+    float* Fs = reinterpret_cast<float*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * C::OUT_BYTES + PC::P_BYTES);
+    float* PL = P;
+    float* PR = P + NC * NP;
+    float* FX = Fs;
+    float* FY = Fs + NC * PC::NFX;
+
+    const int tid = threadIdx.x;
+    const bool pthr = tid < PC::NPT;        // pair thread: owns columns (lx, lx+1) of row ly
+    const int lx = 2 * (tid % (TX / 2)), ly = (tid / (TX / 2)) % TY;
+    const int rot = (tid + 128) % NT;       // phase-P item rotation: second-pass items land on non-pair threads
+    const int fth = tid - PC::NPT;          // phase-F item index base of non-pair threads
+    const FieldGeom& g = sg.f;
+
+    const double smax_in = __longlong_as_double((long long)ctl->smax[prm.slot_in]);
+    const double dt = prm.cfl / smax_in;
+    const f2 gamma = splat<f2>((float)prm.gamma), gm1 = splat<f2>((float)(prm.gamma - 1.0));
+    const f2 dtv = splat<f2>((float)dt);
+    f2 inv_dx[3], half_dtdx[3];
+    float inv_dx_s[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        inv_dx_s[d] = (float)prm.inv_dx[d];
+        inv_dx[d] = splat<f2>(inv_dx_s[d]);
+        half_dtdx[d] = splat<f2>((float)(0.5 * dt * prm.inv_dx[d]));
+    }
+    const float gamma_s = (float)prm.gamma, gm1_s = (float)(prm.gamma - 1.0);
+    if (blockIdx.x == 0 && tid == 0) {
+        ctl->t = prm.first ? dt : ctl->t + dt;
+        ctl->dt_last = dt;
+        ctl->smax[(prm.slot_in + 2) % 3] = 0ull;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
+        flags[0] = 0;
+        fence_mbar_init();
+        prefetch_tensormap(&map_in);
+        prefetch_tensormap(&map_out);
+    }
+    __syncthreads();
+
+    auto item_planes = [&](int item) -> int {
+        if (DIM == 2) return 1;
+        const int chunk = item % sg.chunks_z;
+        return min(sg.zchunk, g.n[2] - chunk * sg.zchunk) + 2 * R;
+    };
+    int ld_item = blockIdx.x, ld_j = 0;
+    long long ld_seq = 0;
+    auto issue_until = [&](long long limit) {
+        while (ld_item < sg.items && ld_seq < limit) {
+            const int item = ld_item;
+            const int chunk = DIM == 3 ? item % sg.chunks_z : 0;
+            const int tile = DIM == 3 ? item / sg.chunks_z : item;
+            const int x0 = (tile % sg.tiles_x) * TX, y0 = (tile / sg.tiles_x) * TY;
+            const int xs = g.lead + g.h + x0 - R - C::OFF;
+            const int ys = g.h + y0 - R;
+            const int slot = (int)(ld_seq % NS);
+            float* dst = ring + (size_t)slot * (C::SLOT_BYTES / sizeof(float));
+            mbar_arrive_expect_tx(&bars[slot], (uint32_t)(C::SLOT_ELEMS * sizeof(float)));
+            if (DIM == 3) {
+                const int pz = g.h + chunk * sg.zchunk - R + ld_j;
+                if (LAYOUT == LAYOUT_SOA) tma_load_4d(dst, &map_in, xs, ys, pz, 0, &bars[slot]);
+                else tma_load_3d(dst, &map_in, xs * NC, ys, pz, &bars[slot]);
+            } else {
+                if (LAYOUT == LAYOUT_SOA) tma_load_3d(dst, &map_in, xs, ys, 0, &bars[slot]);
+                else tma_load_2d(dst, &map_in, xs * NC, ys, &bars[slot]);
+            }
+            ++ld_seq;
+            if (++ld_j == item_planes(item)) { ld_j = 0; ld_item += gridDim.x; }
+        }
+    };
+
+    long long ready_upto = 0, seq_base = 0;
+    int out_count = 0;
+    bool store_pending = false;
+    int st_x = 0, st_y = 0, st_z = 0, st_slot = 0;
+    bool bad = false;
+    float smax_local = 0.f;
+    bool aborted = false;
+
+    auto plane_ptr = [&](long long seq) -> const float* {
+        return ring + (size_t)(seq % NS) * (C::SLOT_BYTES / sizeof(float));
+    };
+    auto wait_planes = [&](long long need) {
+        bool ok = true;
+        for (long long sq = ready_upto; sq <= need; ++sq)
+            ok &= mbar_wait_bounded(&bars[sq % NS], (uint32_t)((sq / NS) & 1));
+        ready_upto = need + 1;
+        if (!ok) flags[0] = 1;
+    };
+    auto store_tile = [&]() {
+        const float* src = stage + (size_t)st_slot * (C::OUT_BYTES / sizeof(float));
+        if (DIM == 3) {
+            if (LAYOUT == LAYOUT_SOA) tma_store_4d(&map_out, src, st_x, st_y, st_z, 0);
+            else tma_store_3d(&map_out, src, st_x * NC, st_y, st_z);
+        } else {
+            if (LAYOUT == LAYOUT_SOA) tma_store_3d(&map_out, src, st_x, st_y, 0);
+            else tma_store_2d(&map_out, src, st_x * NC, st_y);
+        }
+        bulk_commit();
+    };
+    auto producer_step = [&](long long free_before) {
+        if (tid != 0) return;
+        if (store_pending) {
+            store_tile();
+            store_pending = false;
+        }
+        bulk_wait_read<1>();
+        issue_until(free_before + NS);
+    };
+    // pair of the x-adjacent cells (o, o + SX) of a staged plane, all components
+    auto load_pair = [&](const float* S, int o, f2 (&q)[NC]) {
+#pragma unroll
+        for (int m = 0; m < NC; ++m) {
+            if (LAYOUT == LAYOUT_SOA) q[m] = *reinterpret_cast<const f2*>(S + o + m * SM);
+            else q[m] = f2{S[o + m * SM], S[o + SX + m * SM]};
+        }
+    };
+    auto ld2 = [&](const float* a) -> f2 { return *reinterpret_cast<const f2*>(a); };
+    auto st2 = [&](float* a, f2 v) { *reinterpret_cast<f2*>(a) = v; };
+
+    for (int item = blockIdx.x; item < sg.items; item += gridDim.x) {
+        const int chunk = DIM == 3 ? item % sg.chunks_z : 0;
+        const int tile = DIM == 3 ? item / sg.chunks_z : item;
+        const int x0 = (tile % sg.tiles_x) * TX, y0 = (tile / sg.tiles_x) * TY;
+        const int z0 = chunk * sg.zchunk;
+        const int zn = DIM == 3 ? min(sg.zchunk, g.n[2] - z0) : 1;
+        const int gx = x0 + lx, gy = y0 + ly;
+        const bool vx0 = pthr && (gx < g.n[0]) && (gy < g.n[1]);      // first cell of the pair
+        const bool vx1 = pthr && (gx + 1 < g.n[0]) && (gy < g.n[1]);  // second cell
+        const bool tma_store_ok = x0 + TX <= g.n[0];
+        const bool near_xy = (x0 < g.h) || (x0 + TX > g.n[0] - g.h) || (y0 < g.h) || (y0 + TY > g.n[1] - g.h);
+        float chk = 1.f;
+        const int my_off = PV::idx(lx, ly, 0);
+
+        f2 Fzm[NC], Fzp[NC], zR[NC];
+#pragma unroll
+        for (int m = 0; m < NC; ++m) Fzm[m] = Fzp[m] = zR[m] = f2{0.f, 0.f};
+
+        // phase P of plane j: x/y predicted pairs -> shared arrays; z pairs in registers
+        auto phase_p = [&](long long j, int z) {
+            const float* S = plane_ptr(seq_base + j);
+#pragma unroll
+            for (int k = 0; k < PC::KP; ++k) {
+                const int it = rot + k * NT;
+                if (it < PC::NXPr) {
+                    if (it >= PC::NXP) continue;
+                    // x pair: cells (2q - 1, 2q) of row cy
+                    const int cy = it / PC::XP, q = it % PC::XP;
+                    const int c0 = 2 * q - 1;
+                    f2 qm[NC], qc[NC], qp[NC], L[NC], Rr[NC];
+                    const int o = PV::idx(c0 - 1, cy, 0);  // cell 2q - 2: even x
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) {
+                        f2 A, B;
+                        if (LAYOUT == LAYOUT_SOA) {
+                            A = ld2(S + o + m * SM);
+                            B = ld2(S + o + 2 + m * SM);
+                        } else {
+                            A = f2{S[o + m * SM], S[o + SX + m * SM]};
+                            B = f2{S[o + 2 * SX + m * SM], S[o + 3 * SX + m * SM]};
+                        }
+                        qm[m] = A;
+                        qc[m] = f2{A.y, B.x};
+                        qp[m] = B;
+                    }
+                    const bool vr = y0 + cy < g.n[1];
+                    muscl<f2, DIM, 0>(qm, qc, qp, gm1, half_dtdx[0], L, Rr, chk, vr && x0 + c0 <= g.n[0],
+                                      vr && x0 + c0 + 1 <= g.n[0]);
+                    const int pi = cy * PC::XR + c0 + 1;
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) {
+                        st2(PL + m * NP + pi, L[m]);
+                        st2(PR + m * NP + pi, Rr[m]);
+                    }
+                } else {
+                    const int jj = it - PC::NXPr;
+                    if (jj >= PC::NYP) continue;
+                    // y pair: cells (cx, cy), (cx + 1, cy)
+                    const int cy = jj / (TX / 2) - 1, cx = 2 * (jj % (TX / 2));
+                    f2 qm[NC], qc[NC], qp[NC], L[NC], Rr[NC];
+                    const int o = PV::idx(cx, cy, 0);
+                    load_pair(S, o - SY, qm);
+                    load_pair(S, o, qc);
+                    load_pair(S, o + SY, qp);
+                    muscl<f2, DIM, 1>(qm, qc, qp, gm1, half_dtdx[1], L, Rr, chk,
+                                      (x0 + cx < g.n[0]) && (y0 + cy <= g.n[1]),
+                                      (x0 + cx + 1 < g.n[0]) && (y0 + cy <= g.n[1]));
+                    const int pi = PC::NPX + (cy + 1) * TX + cx;
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) {
+                        st2(PL + m * NP + pi, L[m]);
+                        st2(PR + m * NP + pi, Rr[m]);
+                    }
+                }
+            }
+        };
+
+        __syncthreads();  // B0
+        producer_step(seq_base);
+
+        if (DIM == 3) {
+            wait_planes(seq_base + (MUSCL ? 2 * R : 2 * R - 1));
+            __syncthreads();
+            if (flags[0]) { aborted = true; break; }
+            if (pthr) {
+                if (!MUSCL) {
+                    f2 q0[NC], q1[NC];
+                    load_pair(plane_ptr(seq_base + 0), my_off, q0);
+                    load_pair(plane_ptr(seq_base + 1), my_off, q1);
+                    rus<f2, DIM, 2 % DIM>(q0, q1, gamma, gm1, Fzm, chk, vx0, vx1);
+                } else {
+                    f2 q0[NC], q1[NC], q2[NC], q3[NC], L1[NC], R1[NC], L2[NC];
+                    load_pair(plane_ptr(seq_base + 0), my_off, q0);
+                    load_pair(plane_ptr(seq_base + 1), my_off, q1);
+                    load_pair(plane_ptr(seq_base + 2), my_off, q2);
+                    load_pair(plane_ptr(seq_base + 3), my_off, q3);
+                    muscl<f2, DIM, 2 % DIM>(q0, q1, q2, gm1, half_dtdx[2], L1, R1, chk, vx0, vx1);
+                    muscl<f2, DIM, 2 % DIM>(q1, q2, q3, gm1, half_dtdx[2], L2, zR, chk, vx0, vx1);
+                    rus<f2, DIM, 2 % DIM>(R1, L2, gamma, gm1, Fzm, chk, vx0, vx1);
+                }
+            }
+        } else {
+            wait_planes(seq_base);
+        }
+        if (MUSCL) phase_p(DIM == 3 ? R : 0, z0);
+
+        for (int zl = 0; zl < zn; ++zl) {
+            const int z = z0 + zl;
+            const long long jc = DIM == 3 ? (long long)zl + R : 0;
+            __syncthreads();  // B2
+            if (flags[0]) { aborted = true; break; }
+            producer_step(seq_base + jc);
+            const float* S = plane_ptr(seq_base + jc);
+
+            // ---------------- phase F: z work (pair threads), x/y face pairs (others) ----------------
+            if (DIM == 3 && pthr) {
+                if (!MUSCL) {
+                    f2 q0[NC], q1[NC];
+                    load_pair(S, my_off, q0);
+                    load_pair(plane_ptr(seq_base + jc + 1), my_off, q1);
+                    rus<f2, DIM, 2 % DIM>(q0, q1, gamma, gm1, Fzp, chk, vx0, vx1);
+                } else {
+                    // predicted states of plane z + 1 and the face z + 1/2
+                    f2 q0[NC], q1[NC], q2[NC], L[NC], Rn[NC];
+                    load_pair(S, my_off, q0);
+                    load_pair(plane_ptr(seq_base + jc + 1), my_off, q1);
+                    load_pair(plane_ptr(seq_base + jc + 2), my_off, q2);
+                    muscl<f2, DIM, 2 % DIM>(q0, q1, q2, gm1, half_dtdx[2], L, Rn, chk, vx0, vx1);
+                    rus<f2, DIM, 2 % DIM>(zR, L, gamma, gm1, Fzp, chk, vx0, vx1);
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) zR[m] = Rn[m];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < PC::KF; ++k) {
+                if (pthr) break;
+                const int it = fth + k * (NT - PC::NPT);
+                if (it < PC::NXFr) {
+                    if (it >= PC::NXF) continue;
+                    // x faces (f, f + 1), f = 2q, between cells f - 1 | f and f | f + 1
+                    const int cy = it / PC::XP, f = 2 * (it % PC::XP);
+                    f2 a[NC], b[NC], F[NC];
+                    if (MUSCL) {
+                        const int i0 = cy * PC::XR + f;  // x-predicted index of cell f - 1
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            a[m] = ld2(PR + m * NP + i0);
+                            const f2 u = ld2(PL + m * NP + i0), w = ld2(PL + m * NP + i0 + 2);
+                            b[m] = f2{u.y, w.x};
+                        }
+                    } else {
+                        const int o = PV::idx(f - 2, cy, 0);  // cell f - 2: even x
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            f2 A, B;
+                            if (LAYOUT == LAYOUT_SOA) {
+                                A = ld2(S + o + m * SM);
+                                B = ld2(S + o + 2 + m * SM);
+                            } else {
+                                A = f2{S[o + m * SM], S[o + SX + m * SM]};
+                                B = f2{S[o + 2 * SX + m * SM], S[o + 3 * SX + m * SM]};
+                            }
+                            a[m] = f2{A.y, B.x};
+                            b[m] = B;
+                        }
+                    }
+                    const bool vr = y0 + cy < g.n[1];
+                    rus<f2, DIM, 0>(a, b, gamma, gm1, F, chk, vr && (x0 + f <= g.n[0]),
+                                    vr && (f + 1 <= TX) && (x0 + f + 1 <= g.n[0]));
+                    const int fi = cy * PC::FXR + f;
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) st2(FX + m * PC::NFX + fi, F[m]);
+                } else {
+                    const int jj = it - PC::NXFr;
+                    if (jj >= PC::NYF) continue;
+                    const int fy = jj / (TX / 2), cx = 2 * (jj % (TX / 2));
+                    f2 a[NC], b[NC], F[NC];
+                    if (MUSCL) {
+                        const int il = PC::NPX + fy * TX + cx, ir = il + TX;
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) {
+                            a[m] = ld2(PR + m * NP + il);
+                            b[m] = ld2(PL + m * NP + ir);
+                        }
+                    } else {
+                        const int o = PV::idx(cx, fy - 1, 0);
+                        load_pair(S, o, a);
+                        load_pair(S, o + SY, b);
+                    }
+                    rus<f2, DIM, 1>(a, b, gamma, gm1, F, chk, (x0 + cx < g.n[0]) && (y0 + fy <= g.n[1]),
+                                    (x0 + cx + 1 < g.n[0]) && (y0 + fy <= g.n[1]));
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) st2(FY + m * PC::NFY + fy * TX + cx, F[m]);
+                }
+            }
+            __syncthreads();  // B3
+
+            // ---------------- phase U: pair threads ----------------
+            if (pthr) {
+                float* st = stage + (size_t)(out_count & 1) * (C::OUT_BYTES / sizeof(float));
+                f2 qc[NC];
+                load_pair(S, my_off, qc);
+                f2 qn[NC];
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    const float* fxr = FX + m * PC::NFX + ly * PC::FXR + lx;
+                    const f2 fl = ld2(fxr), fn = ld2(fxr + 2);
+                    const f2 fr = f2{fl.y, fn.x};
+                    const f2 fyl = ld2(FY + m * PC::NFY + ly * TX + lx);
+                    const f2 fyh = ld2(FY + m * PC::NFY + (ly + 1) * TX + lx);
+                    f2 acc = (fr - fl) * inv_dx[0];
+                    acc = fma_v(fyh - fyl, inv_dx[1], acc);
+                    if (DIM == 3) acc = fma_v(Fzp[m] - Fzm[m], inv_dx[2], acc);
+                    qn[m] = fma_v(f2{-dtv.x, -dtv.y}, acc, qc[m]);
+                    if (tma_store_ok) {
+                        if (LAYOUT == LAYOUT_SOA) st2(st + (m * TY + ly) * TX + lx, qn[m]);
+                        else {
+                            st[(ly * TX + lx) * NC + m] = qn[m].x;
+                            st[(ly * TX + lx + 1) * NC + m] = qn[m].y;
+                        }
+                    }
+                }
+                if (DIM == 3) {
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) Fzm[m] = Fzp[m];
+                }
+                fence_proxy_async_smem();
+                // epilogue per cell of the pair
+#pragma unroll
+                for (int lane = 0; lane < 2; ++lane) {
+                    const bool v = lane == 0 ? vx0 : vx1;
+                    if (!v) continue;
+                    float q1[NC];
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) q1[m] = lane == 0 ? qn[m].x : qn[m].y;
+                    if (!tma_store_ok) {
+                        const long long base = geom_cell(g, gx + lane, gy, z) * g.cell_stride;
+#pragma unroll
+                        for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = q1[m];
+                    }
+                    bool ok;
+                    const float s = wave_sum<float, DIM>(q1, gamma_s, gm1_s, inv_dx_s, ok);
+                    if (!ok) {
+                        bad = true;
+                        record_bad(ctl, BAD_CELL, gx + lane, gy, z);
+                    }
+                    smax_local = fmaxf(smax_local, s);
+                    if (near_xy || (DIM == 3 && (z < g.h || z >= g.n[2] - g.h)))
+                        write_ghost_images<float, DIM>(out, g, prm.bc, gx + lane, gy, z, q1);
+                }
+            }
+            if (tma_store_ok) {
+                store_pending = true;
+                st_x = x0; st_y = y0; st_z = z; st_slot = out_count & 1;
+                ++out_count;
+            }
+            if (!(chk > 0.f)) {
+                bad = true;
+                record_bad(ctl, BAD_STATE, x0, y0, z);
+                chk = 1.f;
+            }
+            // ---------------- phase P of the next plane ----------------
+            if (DIM == 3 && zl + 1 < zn) {
+                wait_planes(seq_base + jc + 1 + R);
+                if (MUSCL) phase_p(jc + 1, z + 1);
+            }
+        }
+        if (aborted) break;
+        seq_base += DIM == 3 ? (long long)zn + 2 * R : 1;
+    }
+
+    __syncthreads();
+    if (tid == 0) {
+        if (store_pending && !aborted) store_tile();
+        bulk_wait<0>();
+        if (aborted) {
+            for (long long sq = ready_upto; sq < ld_seq; ++sq)
+                mbar_wait_bounded(&bars[sq % NS], (uint32_t)((sq / NS) & 1));
+            atomicOr(&ctl->err, DEV_ERR_TIMEOUT);
+        }
+    }
+    double v = (double)smax_local;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int any_bad = __syncthreads_or(bad ? 1 : 0);
+    if ((tid & 31) == 0) red[tid >> 5] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int w = 0; w < NT / 32; ++w) m = fmax(m, red[w]);
+        atomic_max_pos_double(&ctl->smax[(prm.slot_in + 1) % 3], m);
+        if (any_bad) atomicOr(&ctl->err, DEV_ERR_NUMERIC);
+    }
+}
+
+}  // namespace ripple

@@ -540,7 +540,8 @@ ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t 
     const int scheme = p->scheme == RIPPLE_MUSCL_HANCOCK_MINMOD ? SCHEME_MUSCL : SCHEME_RUSANOV1;
     int v = U->variant;
     if (v < 0 || sweep_smem(U->dtype, U->ndim, layout, scheme, v) == 0) {
-        v = -1;
+        // default: the packed pair kernel where it exists (FP32), else the first that fits
+        v = sweep_smem(U->dtype, U->ndim, layout, scheme, kPairVariant) > 0 ? kPairVariant : -1;
         for (int c = 0; c < kNumSweepVariants && v < 0; ++c)
             if (sweep_smem(U->dtype, U->ndim, layout, scheme, c) > 0) v = c;
         if (v < 0) return fail(RIPPLE_ERR_INTERNAL, "no sweep kernel fits this configuration");

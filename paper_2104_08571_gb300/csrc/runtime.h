@@ -32,8 +32,11 @@ ripple_status cuda_fail(cudaError_t e, const char* what);
 struct TileShape {
     int tx, ty;
 };
-constexpr int kNumSweepVariants = 2;
-constexpr TileShape kSweepVariants[kNumSweepVariants] = {{32, 8}, {32, 4}};
+// Variants 0, 1: one cell per work item; variant 2 (FP32 only): packed f32x2
+// cell pairs (euler_sweep_pair.cuh).
+constexpr int kNumSweepVariants = 3;
+constexpr int kPairVariant = 2;
+constexpr TileShape kSweepVariants[kNumSweepVariants] = {{32, 8}, {32, 4}, {32, 8}};
 
 // Launch description of one sweep (one explicit step of one field).
 struct SweepLaunch {

@@ -1,25 +1,53 @@
 // Compile-time table of Euler sweep kernels for one element type: every
 // (dim, layout, scheme, tile variant) combination whose shared memory fits.
 #pragma once
+#include <type_traits>
+
+#include "euler_sweep_pair.cuh"
 #include "runtime.h"
 
 namespace ripple {
 
 constexpr int kMaxDynSmem = 227 * 1024;
 
+// The kernel behind a table entry: the one-cell kernel, or for the pair
+// variant with FP32 fields the packed cell-pair kernel.
 template <typename T, int DIM, int LAYOUT, int SCHEME, int V>
-struct SweepEntry {
+struct SweepKernel {
+    static constexpr bool pair = V == kPairVariant;
     static constexpr int TX = kSweepVariants[V].tx;
     static constexpr int TY = kSweepVariants[V].ty;
-    using C = SweepCfg<T, DIM, LAYOUT, SCHEME, TX, TY>;
-    static constexpr bool fits = C::SMEM <= kMaxDynSmem;
+    static constexpr bool exists = !pair || std::is_same<T, float>::value;
+    static constexpr int smem()
+    {
+        if constexpr (pair) return PairCfg<DIM, LAYOUT, SCHEME>::SMEM;
+        else return SweepCfg<T, DIM, LAYOUT, SCHEME, TX, TY>::SMEM;
+    }
+    static auto fn()
+    {
+        if constexpr (pair && std::is_same<T, float>::value) return euler_sweep_pair_kernel<DIM, LAYOUT, SCHEME>;
+        else return euler_sweep_kernel<T, DIM, LAYOUT, SCHEME, TX, TY>;
+    }
+};
+
+template <typename T, int DIM, int LAYOUT, int SCHEME, int V>
+struct SweepEntry {
+    using K = SweepKernel<T, DIM, LAYOUT, SCHEME, V>;
+    static constexpr int TX = K::TX;
+    static constexpr int TY = K::TY;
+    struct SmemOnly {
+        static constexpr int SMEM = K::smem();
+        static constexpr int NT = TX * TY;
+    };
+    using C = SmemOnly;
+    static constexpr bool fits = K::exists && C::SMEM <= kMaxDynSmem;
 
     static cudaError_t launch(const SweepLaunch& L)
     {
         if constexpr (!fits) {
             return cudaErrorInvalidValue;
         } else {
-            auto k = euler_sweep_kernel<T, DIM, LAYOUT, SCHEME, TX, TY>;
+            auto k = K::fn();
             static bool configured = false;
             if (!configured) {
                 cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -37,7 +65,7 @@ struct SweepEntry {
         if constexpr (!fits) {
             return 0;
         } else {
-            auto k = euler_sweep_kernel<T, DIM, LAYOUT, SCHEME, TX, TY>;
+            auto k = K::fn();
             if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
                 return 0;
             int n = 0;
