@@ -156,10 +156,10 @@ def bench_gpu(args, rank, world, local):
     stream = torch.cuda.Stream(device=local)
     R.ripple_set_stream(ctx, stream)
     MUSCL, TRA = R.RIPPLE_MUSCL_HANCOCK_MINMOD, R.RIPPLE_BC_TRANSMISSIVE
-    dims = (N3, N3, N3)
-    ncell = N3 ** 3
+    dims = tuple(args.sweep_dims)
+    ncell = int(np.prod(dims))
     prm = R.make_fv_params([1.0 / N3] * 3, scheme=MUSCL, bc=TRA)
-    U0 = inputs.euler3d_blast(N3, seed=1).astype(np.float32)
+    U0 = inputs.euler3d_blast(N3, seed=1, dims=dims).astype(np.float32)
     U0_dev = torch.from_numpy(U0).to(f"cuda:{local}")
     U0_dev_aos = torch.from_numpy(np.ascontiguousarray(np.moveaxis(U0, 0, -1))).to(f"cuda:{local}")
     result = {}
@@ -194,6 +194,12 @@ def bench_gpu(args, rank, world, local):
     result["soa_ms_per_step"] = ms / args.steps
     result["soa_totals_mass"] = st["totals"][0]
     R.ripple_field_destroy(f)
+    hbm_peak, peak_kind = load_peaks()
+    achieved = BYTES_PER_CELL_UPDATE * ncell / (ms / args.steps / 1e3) / 1e9
+    if args.sweep_only:
+        R.ripple_ctx_destroy(ctx)
+        return dict(value=world * args.steps * ncell / (ms_max / 1e3), ms_per_step=ms_max / args.steps,
+                    clocks=clocks, achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind)
 
     # ---- AoS layout, same workload ----
     fa = R.ripple_field_create(ctx, dims, 5, R.RIPPLE_AOS, 2, R.RIPPLE_F32)
@@ -270,8 +276,6 @@ def bench_gpu(args, rank, world, local):
     batched = None if args.skip_batched else bench_batched(R, torch, local)
     serve = None if args.skip_serve else bench_serving(R, torch, local)
     value = world * args.steps * ncell / (ms_max / 1e3)
-    hbm_peak, peak_kind = load_peaks()
-    achieved = BYTES_PER_CELL_UPDATE * ncell / (ms / args.steps / 1e3) / 1e9
     return dict(value=value, ms_per_step=ms_max / args.steps, clocks=clocks, ms_aos=ms_aos / args.steps,
                 e2e_value=e2e_value, e2e_s=e2e_s, e2e_solves=e2e_solves, ms2=ms2, eik=eik,
                 achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result, batched=batched,
@@ -474,12 +478,19 @@ def main():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="time only the SoA sweep (a small case for profiling; not the headline line)")
+    ap.add_argument("--sweep-dims", type=int, nargs=3, default=[N3, N3, N3], metavar=("NX", "NY", "NZ"))
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_setup(args.gpus)
-    config = {"workload": "euler3d_muscl_hancock_256^3_blast", "cells": N3 ** 3, "ncomp": 5, "halo": 2,
+    ncell = int(np.prod(args.sweep_dims))
+    nx, ny, nz = args.sweep_dims
+    workload = "euler3d_muscl_hancock_256^3_blast" if (nx, ny, nz) == (N3, N3, N3) else \
+        f"euler3d_muscl_hancock_{nx}x{ny}x{nz}_blast"
+    config = {"workload": workload, "cells": ncell, "ncomp": 5, "halo": 2,
               "scheme": "MUSCL-Hancock minmod + Rusanov", "bc": "transmissive", "layout": "SoA",
-              "l2": "inputs larger than L2 (335 MB per buffer), no flush"}
+              "l2": f"inputs larger than L2 ({ncell * 20 / 1e6:.0f} MB per buffer), no flush"}
 
     if args.impl == "reference":
         if rank != 0:
@@ -511,10 +522,19 @@ def main():
     r = bench_gpu(args, rank, world, local)
     if rank != 0:
         return
+    if args.sweep_only:
+        print(json.dumps({
+            "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config, "gpu_launches": args.steps,
+            "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["hbm_peak"], "unit": "GB/s",
+                         "frac": r["achieved"] / r["hbm_peak"], "traffic": None, "peak_source": r["peak_kind"]},
+            "clocks": r["clocks"]}))
+        return
     cpu = None
     if not args.skip_cpu_baseline and world == 1:
         cpu = cpu_baseline_sample()
-    state_bytes = N3 ** 3 * 5 * 4
+    state_bytes = ncell * 5 * 4
     line = {
         "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -530,7 +550,7 @@ def main():
                 "step": f"one {NSTEPS_SOLVE}-step solve: pinned host -> device, {NSTEPS_SOLVE} sweeps, device -> pinned host",
                 "solves": r["e2e_solves"], "seconds": r["e2e_s"]},
         "cpu_baseline": cpu,
-        "aos": {"value": N3 ** 3 / (r["ms_aos"] / 1e3), "ms_per_step": r["ms_aos"]},
+        "aos": {"value": ncell / (r["ms_aos"] / 1e3), "ms_per_step": r["ms_aos"]},
         "euler2d_fp64_128": {"ms_per_100_steps": r["ms2"], "us_per_step": r["ms2"] * 10.0,
                              "cell_updates_per_s": 100 * 128 * 128 / (r["ms2"] / 1e3)},
         "eikonal": r["eik"],

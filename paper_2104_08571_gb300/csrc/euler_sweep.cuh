@@ -112,11 +112,16 @@ __device__ __forceinline__ void phys_flux(const T (&q)[DIM + 2], T gm1, T (&F)[D
 // seen in the states of in-domain items; a non-positive value flags the plane.
 // (A NaN state is skipped by fmin but reaches the updated cells, whose own
 // check catches it.)
-template <typename T>
-__device__ __forceinline__ void track_min(T& chk, bool valid, T a, T b, T c, T d)
+__device__ __forceinline__ void track_min(double& chk, bool valid, double a, double b, double c, double d)
 {
-    const T m = fmin(fmin(a, b), fmin(c, d));
+    const double m = fmin(fmin(a, b), fmin(c, d));
     if (valid) chk = fmin(chk, m);
+}
+__device__ __forceinline__ void track_min(float& chk, bool valid, float a, float b, float c, float d)
+{
+    float m;  // three-operand minimum: one ALU instruction on sm_100 and later
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(a), "f"(b), "f"(c));
+    if (valid) asm("min.f32 %0, %1, %2, %3;" : "=f"(chk) : "f"(chk), "f"(m), "f"(d));
 }
 
 // Rusanov face flux along D between left state a and right state b.
@@ -393,8 +398,8 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
         return min(sg.zchunk, g.n[2] - chunk * sg.zchunk) + 2 * R;
     };
     int ld_item = blockIdx.x, ld_j = 0;  // loader cursor (thread 0 only)
-    long long ld_seq = 0;
-    auto issue_until = [&](long long limit) {
+    unsigned ld_seq = 0;
+    auto issue_until = [&](unsigned limit) {
         while (ld_item < sg.items && ld_seq < limit) {
             const int item = ld_item;
             const int chunk = DIM == 3 ? item % sg.chunks_z : 0;
@@ -418,8 +423,9 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
         }
     };
 
-    long long ready_upto = 0;  // planes with seq < ready_upto have been waited for
-    long long seq_base = 0;    // seq of plane j = 0 of the current item
+    // plane sequence numbers are 32-bit: a CTA streams far fewer than 2^32 planes
+    unsigned ready_upto = 0;  // planes with seq < ready_upto have been waited for
+    unsigned seq_base = 0;    // seq of plane j = 0 of the current item
     int out_count = 0;         // TMA-stored planes (staging slot parity)
     bool store_pending = false;
     int st_x = 0, st_y = 0, st_z = 0, st_slot = 0;
@@ -427,14 +433,14 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
     T smax_local = T(0);
     bool aborted = false;
 
-    auto plane_ptr = [&](long long seq) -> const T* {
-        return ring + (size_t)(seq % NS) * (C::SLOT_BYTES / sizeof(T));
+    auto plane_ptr = [&](unsigned seq) -> const T* {
+        return ring + (seq % NS) * (unsigned)(C::SLOT_BYTES / sizeof(T));
     };
     // wait (all threads) for planes up to seq `need` inclusive; a wait that
     // runs out raises the abort flag, read by every thread after the next barrier
-    auto wait_planes = [&](long long need) {
+    auto wait_planes = [&](unsigned need) {
         bool ok = true;
-        for (long long sq = ready_upto; sq <= need; ++sq)
+        for (unsigned sq = ready_upto; sq <= need; ++sq)
             ok &= mbar_wait_bounded(&bars[sq % NS], (uint32_t)((sq / NS) & 1));
         ready_upto = need + 1;
         if (!ok) flags[0] = 1;
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
     // of the planes with seq < free_before and every write of the staging tile
     // that is still pending: flush that tile by TMA store, make sure the other
     // staging slot has been read out, refill the freed ring slots.
-    auto producer_step = [&](long long free_before) {
+    auto producer_step = [&](unsigned free_before) {
         if (tid != 0) return;
         if (store_pending) {
             store_tile();
@@ -544,7 +550,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
         }
 
         // Phase P of the plane with index j (seq_base + j); z = z0 - R + j.
-        auto phase_p = [&](long long j, int z) {
+        auto phase_p = [&](unsigned j, int z) {
             const T* S = plane_ptr(seq_base + j);
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
@@ -612,7 +618,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
 
         for (int zl = 0; zl < zn; ++zl) {
             const int z = z0 + zl;
-            const long long jc = DIM == 3 ? (long long)zl + R : 0;  // plane index of z
+            const unsigned jc = DIM == 3 ? (unsigned)(zl + R) : 0u;  // plane index of z
             __syncthreads();  // B2: phase P of this plane (and U of the previous) done
             if (flags[0]) { aborted = true; break; }
             producer_step(seq_base + jc);
@@ -725,7 +731,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
             }
         }
         if (aborted) break;
-        seq_base += DIM == 3 ? (long long)zn + 2 * R : 1;
+        seq_base += DIM == 3 ? (unsigned)(zn + 2 * R) : 1u;
     }
 
     // ---- drain: last store, wait for completion ----
@@ -736,7 +742,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
         if (aborted) {
             // loads still in flight complete into this CTA's shared memory:
             // wait for them (bounded) before the CTA exits
-            for (long long sq = ready_upto; sq < ld_seq; ++sq)
+            for (unsigned sq = ready_upto; sq < ld_seq; ++sq)
                 mbar_wait_bounded(&bars[sq % NS], (uint32_t)((sq / NS) & 1));
             atomicOr(&ctl->err, DEV_ERR_TIMEOUT);
         }

@@ -117,8 +117,8 @@ __global__ void __launch_bounds__(256, 2)
         return min(sg.zchunk, g.n[2] - chunk * sg.zchunk) + 2 * R;
     };
     int ld_item = blockIdx.x, ld_j = 0;
-    long long ld_seq = 0;
-    auto issue_until = [&](long long limit) {
+    unsigned ld_seq = 0;
+    auto issue_until = [&](unsigned limit) {
         while (ld_item < sg.items && ld_seq < limit) {
             const int item = ld_item;
             const int chunk = DIM == 3 ? item % sg.chunks_z : 0;
@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(256, 2)
         }
     };
 
-    long long ready_upto = 0, seq_base = 0;
+    unsigned ready_upto = 0, seq_base = 0;  // 32-bit plane sequence numbers
     int out_count = 0;
     bool store_pending = false;
     int st_x = 0, st_y = 0, st_z = 0, st_slot = 0;
@@ -150,12 +150,12 @@ __global__ void __launch_bounds__(256, 2)
     float smax_local = 0.f;
     bool aborted = false;
 
-    auto plane_ptr = [&](long long seq) -> const float* {
-        return ring + (size_t)(seq % NS) * (C::SLOT_BYTES / sizeof(float));
+    auto plane_ptr = [&](unsigned seq) -> const float* {
+        return ring + (seq % NS) * (unsigned)(C::SLOT_BYTES / sizeof(float));
     };
-    auto wait_planes = [&](long long need) {
+    auto wait_planes = [&](unsigned need) {
         bool ok = true;
-        for (long long sq = ready_upto; sq <= need; ++sq)
+        for (unsigned sq = ready_upto; sq <= need; ++sq)
             ok &= mbar_wait_bounded(&bars[sq % NS], (uint32_t)((sq / NS) & 1));
         ready_upto = need + 1;
         if (!ok) flags[0] = 1;
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256, 2)
         }
         bulk_commit();
     };
-    auto producer_step = [&](long long free_before) {
+    auto producer_step = [&](unsigned free_before) {
         if (tid != 0) return;
         if (store_pending) {
             store_tile();
@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(256, 2)
         for (int m = 0; m < NC; ++m) Fzm[m] = Fzp[m] = zR[m] = f2{0.f, 0.f};
 
         // phase P of plane j: x/y predicted pairs -> shared arrays; z pairs in registers
-        auto phase_p = [&](long long j, int z) {
+        auto phase_p = [&](unsigned j, int z) {
             const float* S = plane_ptr(seq_base + j);
 #pragma unroll
             for (int k = 0; k < PC::KP; ++k) {
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(256, 2)
 
         for (int zl = 0; zl < zn; ++zl) {
             const int z = z0 + zl;
-            const long long jc = DIM == 3 ? (long long)zl + R : 0;
+            const unsigned jc = DIM == 3 ? (unsigned)(zl + R) : 0u;
             __syncthreads();  // B2
             if (flags[0]) { aborted = true; break; }
             producer_step(seq_base + jc);
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(256, 2)
             }
         }
         if (aborted) break;
-        seq_base += DIM == 3 ? (long long)zn + 2 * R : 1;
+        seq_base += DIM == 3 ? (unsigned)(zn + 2 * R) : 1u;
     }
 
     __syncthreads();
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(256, 2)
         if (store_pending && !aborted) store_tile();
         bulk_wait<0>();
         if (aborted) {
-            for (long long sq = ready_upto; sq < ld_seq; ++sq)
+            for (unsigned sq = ready_upto; sq < ld_seq; ++sq)
                 mbar_wait_bounded(&bars[sq % NS], (uint32_t)((sq / NS) & 1));
             atomicOr(&ctl->err, DEV_ERR_TIMEOUT);
         }

@@ -91,15 +91,24 @@ __device__ __forceinline__ float minmod_s(float a, float b)
 __device__ __forceinline__ float minmod_v(float a, float b) { return minmod_s(a, b); }
 __device__ __forceinline__ f2 minmod_v(f2 a, f2 b) { return f2{minmod_s(a.x, b.x), minmod_s(a.y, b.y)}; }
 
+// Three-operand minimum (one ALU instruction on sm_100 and later).
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
 // Smallest of four quantities per lane into chk, for the lanes that lie in the domain.
 __device__ __forceinline__ void track4(float& chk, float a, float b, float c, float d, bool v0, bool)
 {
-    if (v0) chk = fminf(chk, fminf(fminf(a, b), fminf(c, d)));
+    if (v0) chk = min3f(chk, min3f(a, b, c), d);
 }
 __device__ __forceinline__ void track4(float& chk, f2 a, f2 b, f2 c, f2 d, bool v0, bool v1)
 {
-    if (v0) chk = fminf(chk, fminf(fminf(a.x, b.x), fminf(c.x, d.x)));
-    if (v1) chk = fminf(chk, fminf(fminf(a.y, b.y), fminf(c.y, d.y)));
+    const float m0 = min3f(a.x, b.x, c.x), m1 = min3f(a.y, b.y, c.y);
+    if (v0) chk = min3f(chk, m0, d.x);
+    if (v1) chk = min3f(chk, m1, d.y);
 }
 
 // Physical flux along axis D; also returns 1/rho, the normal velocity, the pressure.
