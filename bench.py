@@ -40,6 +40,10 @@ import inputs  # noqa: E402
 N3 = 256
 NSTEPS_SOLVE = 50
 BYTES_PER_CELL_UPDATE = 40  # FP32, 5 components: 20 B read + 20 B written per cell per step
+# DRAM bytes per cell update of the sweep kernel as measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum of one 256x256x128 launch, divided by its cells);
+# traffic scales with the cells of a launch.  Re-measure whenever the kernel changes.
+DRAM_BYTES_PER_CELL_UPDATE = 355.013888e6 / (256 * 256 * 128)
 METRIC = "cell-updates/s"
 ACTIVE_CELLS = 4 << 20  # serving: per-step cell budget of stepped Euler problems
 
@@ -350,8 +354,8 @@ def bench_batched(R, torch, local, nsteps=100, count=512):
         "speedup_vs_loop": t_loop / t_batch,
         "max_rel_l1_vs_loop": worst,
         "autotune": {"layout": "SoA" if cfg["layout"] == R.RIPPLE_SOA else "AoS",
-                     "tile": ["32x8", "64x4", "16x16"][cfg["tile_variant"]],
-                     "ms_per_global_step": {f"{'SoA' if k[0] == R.RIPPLE_SOA else 'AoS'}/{['32x8', '64x4', '16x16'][k[1]]}": v
+                     "tile": ["32x8", "8x32", "16x16"][cfg["tile_variant"]],
+                     "ms_per_global_step": {f"{'SoA' if k[0] == R.RIPPLE_SOA else 'AoS'}/{['32x8', '8x32', '16x16'][k[1]]}": v
                                             for k, v in timings.items()}},
     }
 
@@ -481,6 +485,8 @@ def main():
     ap.add_argument("--sweep-only", action="store_true",
                     help="time only the SoA sweep (a small case for profiling; not the headline line)")
     ap.add_argument("--sweep-dims", type=int, nargs=3, default=[N3, N3, N3], metavar=("NX", "NY", "NZ"))
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the 512-instance batched workload (profiling; not the headline line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_setup(args.gpus)
@@ -519,6 +525,15 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.batched_only:
+        import torch
+        import paper_2104_08571_gb300 as R
+        torch.cuda.set_device(local)
+        b = bench_batched(R, torch, local)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": b["value"], "unit": METRIC, "n_gpus": world,
+                              "config": {"workload": b["workload"]}, "batched": b}))
+        return
     r = bench_gpu(args, rank, world, local)
     if rank != 0:
         return
@@ -541,7 +556,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
         "gpu_launches": args.steps,
         "roofline": {"bound": "hbm", "achieved": r["achieved"], "peak": r["hbm_peak"], "unit": "GB/s",
-                     "frac": r["achieved"] / r["hbm_peak"], "traffic": None,
+                     "frac": r["achieved"] / r["hbm_peak"], "traffic": DRAM_BYTES_PER_CELL_UPDATE * ncell,
+                     "traffic_source": "ncu dram bytes of a 256x256x128 launch, scaled by cells",
                      "peak_source": r["peak_kind"],
                      "algorithmic_bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
         "clocks": r["clocks"],

@@ -257,7 +257,7 @@ typedef struct {
 
 typedef struct {
     ripple_layout layout;     /* layout of resident Euler states */
-    int tile_variant;         /* 0: 32x8, 1: 64x4, 2: 16x16 Euler tiles */
+    int tile_variant;         /* 0: 32x8, 1: 8x32, 2: 16x16 Euler tiles */
     int steps_per_sync;       /* most global steps queued between scheduler checks (fewer when an
                                  Euler problem ends sooner): latency of joining vs overhead */
     int use_graphs;           /* replay queued steps from captured CUDA graphs */

@@ -34,23 +34,31 @@ struct BatchTileShape {
     int tx, ty;
 };
 constexpr int kNumBatchVariants = 3;
-constexpr BatchTileShape kBatchVariants[kNumBatchVariants] = {{32, 8}, {64, 4}, {16, 16}};
+constexpr BatchTileShape kBatchVariants[kNumBatchVariants] = {{32, 8}, {8, 32}, {16, 16}};
 
 template <typename T, int LAYOUT, int V>
 static cudaError_t step_v(int grid, cudaStream_t s, const BatchEuler* e, const void* f, const int* table,
                           BatchCtl* c, int kind)
 {
     constexpr int TX = kBatchVariants[V].tx, TY = kBatchVariants[V].ty;
-    batch_step_kernel<T, LAYOUT, TX, TY><<<grid, 256, 0, s>>>(e, static_cast<const BatchFim<T>*>(f), table, c,
-                                                               kind);
+    using BC = BatchEulerCfg<T, LAYOUT, TX, TY>;
+    if (kind == 0)
+        batch_euler_kernel<T, LAYOUT, TX, TY><<<grid, BC::NTHREADS, BC::SMEM, s>>>(e, table, c);
+    else
+        batch_fim_kernel<T><<<grid, 256, 0, s>>>(static_cast<const BatchFim<T>*>(f), table, c);
     return cudaGetLastError();
 }
+// CTAs per SM of the Euler step kernel (which also sets its dynamic shared
+// memory limit: called before any launch of the variant).
 template <typename T, int LAYOUT, int V>
 static int occ_v()
 {
     constexpr int TX = kBatchVariants[V].tx, TY = kBatchVariants[V].ty;
+    using BC = BatchEulerCfg<T, LAYOUT, TX, TY>;
+    auto k = batch_euler_kernel<T, LAYOUT, TX, TY>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, BC::SMEM) != cudaSuccess) return 0;
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_step_kernel<T, LAYOUT, TX, TY>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, BC::NTHREADS, BC::SMEM);
     return n;
 }
 template <typename T, int LAYOUT>
@@ -78,6 +86,17 @@ static int batch_occupancy(ripple_dtype dt, int layout, int v)
         return v == 1 ? occ_v<T, LAYOUT_AOS, 1>() : v == 2 ? occ_v<T, LAYOUT_AOS, 2>() : occ_v<T, LAYOUT_AOS, 0>();
     };
     return dt == RIPPLE_F32 ? pick(0.0f) : pick(0.0);
+}
+
+// TMA maps of both buffers of an Euler instance, staged in boxes of tile variant v.
+static ripple_status encode_batch_maps(BatchEuler& e, ripple_layout layout, ripple_dtype dt, int v)
+{
+    for (int b = 0; b < 2; ++b) {
+        ripple_status st = encode_plane_map(e.buf[b], e.g, layout, dt, 0, 1, kBatchVariants[v].tx,
+                                            kBatchVariants[v].ty, &e.map[b]);
+        if (st != RIPPLE_OK) return st;
+    }
+    return RIPPLE_OK;
 }
 
 // Fill a uniform admissible Euler state (autotuner sample problems).
@@ -113,6 +132,8 @@ struct Inst {
     long long start_step = -1;  // Euler: launch index of local step 0 (recomputed on resume)
     long long steps_done = 0;   // Euler steps completed
     bool active = false;        // Euler: stepped in the current rounds
+    CUtensorMap map[2];         // Euler: TMA maps of buf[0], buf[1] (cached per tile variant and layout)
+    int map_key = -1;
     cudaEvent_t ev = nullptr;
     ripple_status result = RIPPLE_OK;
     double t_submit = 0, t_admit = 0, t_start = 0, t_finish = 0;
@@ -153,6 +174,7 @@ struct BatchRuntime {
     void* d_fim = nullptr;
     int* d_table = nullptr;
     BatchCtl* d_bctl = nullptr;
+    unsigned* h_berr = nullptr;  // pinned mirror of d_bctl->err
     BatchEuler* h_euler = nullptr;
     void* h_fim = nullptr;
     int* h_table = nullptr;
@@ -436,9 +458,19 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
             e.start_step = in->start_step;
             e.nsteps = in->req.nsteps;
             e.gamma = in->req.fv.gamma;
+            e.gm1 = in->req.fv.gamma - 1.0;
             e.cfl = in->req.fv.cfl;
             e.inv_dx0 = 1.0 / in->req.fv.dx[0];
             e.inv_dx1 = 1.0 / in->req.fv.dx[1];
+            const int key = rt->cfg.tile_variant * 2 + (rt->cfg.layout == RIPPLE_SOA ? 1 : 0);
+            if (in->map_key != key) {
+                st = encode_batch_maps(e, rt->cfg.layout, rt->cfg.dtype, rt->cfg.tile_variant);
+                if (st != RIPPLE_OK) return st;
+                std::memcpy(in->map, e.map, sizeof(in->map));
+                in->map_key = key;
+            } else {
+                std::memcpy(e.map, in->map, sizeof(e.map));
+            }
             for (int k = 0; k < in->ntiles; ++k) rt->h_table[t + k] = (ie << 1) | 0;
             ++ie;
         } else {
@@ -567,8 +599,14 @@ static ripple_status compute_round(BatchRuntime* rt)
     if (rt->has_f)
         RIPPLE_CUDA(cudaMemcpyAsync(rt->h_status, rt->slot_status, kSlots * sizeof(unsigned long long),
                                     cudaMemcpyDeviceToHost, rt->compute));
+    RIPPLE_CUDA(cudaMemcpyAsync(rt->h_berr, &rt->d_bctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                rt->compute));
     RIPPLE_CUDA(cudaEventRecord(rt->ev_step, rt->compute));
     RIPPLE_CUDA(cudaEventSynchronize(rt->ev_step));
+    if (*rt->h_berr) {
+        RIPPLE_CUDA(cudaMemsetAsync(&rt->d_bctl->err, 0, sizeof(unsigned), rt->compute));
+        return fail(RIPPLE_ERR_TIMEOUT, "a bounded wait of a batched launch ran out");
+    }
     if (rt->has_e) rt->gstep_e += K;
     for (Inst* in : rt->resident)
         if (in->req.kind == RIPPLE_REQ_EULER && in->active) in->steps_done += K;
@@ -714,6 +752,8 @@ static ripple_status rt_start(BatchRuntime* rt)
     RIPPLE_CUDA(cudaMallocHost(&rt->h_counters, kSlots * 3 * sizeof(long long)));
     RIPPLE_CUDA(cudaMalloc(&rt->d_bctl, sizeof(BatchCtl)));
     RIPPLE_CUDA(cudaMemset(rt->d_bctl, 0, sizeof(BatchCtl)));
+    RIPPLE_CUDA(cudaMallocHost(&rt->h_berr, sizeof(unsigned)));
+    *rt->h_berr = 0u;
     rt->free_slots.clear();
     for (int i = kSlots - 1; i >= 0; --i) rt->free_slots.push_back(i);
     const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
@@ -795,8 +835,10 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
                 h[i].start_step = 0;
                 h[i].nsteps = 1LL << 40;
                 h[i].gamma = 1.4;
+                h[i].gm1 = 1.4 - 1.0;
                 h[i].cfl = 0.4;
                 h[i].inv_dx0 = h[i].inv_dx1 = (double)sides[i];
+                if (status == RIPPLE_OK) status = encode_batch_maps(h[i], lay, dt, v);
                 const int nt = h[i].tiles_x * (int)((sides[i] + ty - 1) / ty);
                 for (int k = 0; k < nt; ++k) table.push_back(i << 1);
             }
@@ -881,6 +923,7 @@ void batch_runtime_destroy(ripple_ctx ctx)
         cudaFree(rt->d_fim);
         cudaFree(rt->d_table);
         cudaFree(rt->d_bctl);
+        if (rt->h_berr) cudaFreeHost(rt->h_berr);
         cudaFreeHost(rt->h_euler);
         cudaFreeHost(rt->h_fim);
         cudaFreeHost(rt->h_table);

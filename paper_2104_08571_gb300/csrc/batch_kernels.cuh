@@ -19,15 +19,19 @@
 
 namespace ripple {
 
-// One resident 2D Euler instance.
-struct BatchEuler {
+// One resident 2D Euler instance.  The TMA maps stage the padded planes of
+// buf[0] and buf[1] in boxes of the configured tile shape; they live in
+// device memory (64-byte aligned) and are acquired before each use because a
+// slot of the descriptor array is reused by later instances.
+struct BatchEuler {  // aligned as CUtensorMap (at least 64 bytes)
+    CUtensorMap map[2];
     void* buf[2];
     FieldCtl* ctl;
     FieldGeom g;
     int tiles_x, tile_begin;
     int bc;
     long long start_step, nsteps;
-    double gamma, cfl, inv_dx0, inv_dx1;
+    double gamma, gm1, cfl, inv_dx0, inv_dx1;  // gm1 = gamma - 1, formed on the host in FP64
 };
 
 // One resident 2D eikonal instance.
@@ -52,120 +56,286 @@ struct BatchCtl {
     unsigned int done[2];         // CTAs finished in the current launch of each kind
     int ntiles_e;                 // table entries [0, ntiles_e) are Euler tiles
     int ntiles;                   // entries [ntiles_e, ntiles) are eikonal tiles
+    unsigned int err;             // DEV_ERR_TIMEOUT: a bounded wait of a batched launch ran out
 };
 
 // Tile-table entry: (instance index << 1) | kind, kind 0 = Euler, 1 = eikonal.
 // The entry's tile index inside its instance is its position minus the
 // instance's tile_begin.
 
-template <typename T, int TX, int TY>
-struct BatchSmemEuler {
-    T S[4][TY + 2][TX + 2];  // staged tile + 1 ghost layer, component-major
-    T FX[4][(TX + 1) * TY];
-    T FY[4][TX * (TY + 1)];
+// Shared-memory plan of the batched Euler step: the full/empty mbarriers of
+// a ring of NS slots, one header of tile parameters per slot, the staged
+// tiles (TMA boxes of the tile plus one ghost layer, all four components;
+// each starts on a 128-byte boundary as TMA requires) and two face-flux
+// buffers (by tile parity).
+template <typename T, int LAYOUT, int TX, int TY>
+struct BatchEulerCfg {
+    using C = SweepCfg<T, 2, LAYOUT, SCHEME_RUSANOV1, TX, TY>;
+    static constexpr int NC = 4, NS = 4;
+    static constexpr int NCT = TX * TY;          // consumer threads: one cell each
+    static constexpr int NTHREADS = NCT + 32;    // plus one producer warp
+    static constexpr int HDRS = 16 * NS;         // after the 2 * NS mbarriers
+    static constexpr int SLOT_HDR = 64;          // per-slot tile parameters
+    static constexpr int RING = ((HDRS + NS * SLOT_HDR + 127) / 128) * 128;
+    static constexpr int FACES = RING + NS * C::SLOT_BYTES;
+    static constexpr int SMEM = FACES + 2 * C::F_BYTES;
+    static_assert(NCT == 256, "the batched step updates 256 cells per tile");
+    static_assert(RING % 128 == 0 && C::SLOT_BYTES % 128 == 0 && C::F_BYTES % 128 == 0, "TMA destinations");
 };
 
-template <typename T, int LAYOUT, int TX, int TY>
-union BatchSmem {
-    BatchSmemEuler<T, TX, TY> e;
-    FimSmem<T, 2> f;
+// Parameters of a staged tile, written by the producer before the slot's
+// full barrier completes.  tile < 0 marks the end of the CTA's work.
+template <typename T>
+struct BatchTileHdr {
+    T gamma, gm1, inv_dx0, inv_dx1, dt;
+    int tile, x0, y0;
+    long long local;
 };
+static_assert(sizeof(BatchTileHdr<double>) <= 64, "tile header fits the slot header");
 
-template <typename T, int LAYOUT, int TX, int TY>
-__device__ __forceinline__ void batch_euler_tile(BatchSmemEuler<T, TX, TY>& sm, double* red,
-                                                 const BatchEuler& d, int lt, long long local)
+// The last CTA of a launch to finish advances the launch counter of its kind.
+__device__ __forceinline__ void batch_finish_launch(BatchCtl* bctl, int kind)
 {
-    constexpr int NC = 4, NT = TX * TY;
-    constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&bctl->done[kind], 1u) == gridDim.x - 1) {
+            bctl->done[kind] = 0u;
+            __threadfence();
+            atomicAdd(&bctl->gstep[kind], 1ull);
+        }
+    }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Barrier among the 256 consumer threads only (the producer warp runs ahead),
+// returning the OR of a predicate over them: every consumer takes the same
+// decision at the same barrier.
+__device__ __forceinline__ bool consumer_sync_or(bool p)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, o;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred o, 1, 256, q;\n\t"
+        "selp.u32 %0, 1, 0, o;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p)
+        : "memory");
+    return r != 0;
+}
+
+// One explicit Rusanov step of every resident Euler problem inside its step
+// window.  The CTAs walk the Euler part of the tile table with a fixed stride.
+// Warp-specialised pipeline: the producer warp (one elected lane) walks the
+// CTA's tiles, forms each tile's parameters (dt from the instance's FP64 ring,
+// constants in the field's precision) into the slot header and issues the
+// slot's TMA load from the instance's own map, up to NS tiles ahead; the 256
+// consumer threads wait on the slot's full barrier, compute the tile's faces
+// into the face buffer of the tile's parity, meet at one named barrier,
+// update one cell each (direct coalesced stores, ghost images), fold the new
+// wave speeds per warp into the instance's next ring slot, and release the
+// slot through its empty barrier.
+template <typename T, int LAYOUT, int TX, int TY>
+__global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __restrict__ euler,
+                                                          const int* __restrict__ table,
+                                                          BatchCtl* __restrict__ bctl)
+{
+    using B = BatchEulerCfg<T, LAYOUT, TX, TY>;
+    using C = typename B::C;
+    using PV = PlaneView<C, LAYOUT>;
+    using Hdr = BatchTileHdr<T>;
+    constexpr int NC = 4, NS = B::NS, NCT = B::NCT;
+    constexpr int NFX = C::NFX, NFY = C::NFY;
+    constexpr int NFXr = ((NFX + 31) / 32) * 32, NFYr = ((NFY + 31) / 32) * 32;
+    constexpr int KF = (NFXr + NFYr + NCT - 1) / NCT;
+    constexpr int SX = LAYOUT == LAYOUT_SOA ? 1 : NC;
+    constexpr int SY = LAYOUT == LAYOUT_SOA ? C::BX : C::BX * NC;
+    constexpr int SM = LAYOUT == LAYOUT_SOA ? C::BX * C::BY : 1;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + NS;
+    auto slot_hdr = [&](unsigned s) { return reinterpret_cast<Hdr*>(smem + B::HDRS + s * B::SLOT_HDR); };
+    auto slot_tile = [&](unsigned s) { return reinterpret_cast<T*>(smem + B::RING + s * C::SLOT_BYTES); };
+    auto faces = [&](unsigned par) { return reinterpret_cast<T*>(smem + B::FACES + par * C::F_BYTES); };
+
     const int tid = threadIdx.x;
-    const int lx = tid % TX, ly = tid / TX;
-    const FieldGeom& g = d.g;
-    const int x0 = (lt % d.tiles_x) * TX, y0 = (lt / d.tiles_x) * TY;
-    const int par = (int)(local & 1);
-    const T* __restrict__ in = static_cast<const T*>(d.buf[par]);
-    T* __restrict__ out = static_cast<T*>(d.buf[par ^ 1]);
-    const int slot = (int)(local % 3);
-    const double dt = d.cfl / __longlong_as_double((long long)__ldcg(&d.ctl->smax[slot]));
-    const T gamma = (T)d.gamma, gm1 = (T)(d.gamma - 1.0), dtT = (T)dt;
-    const T inv_dx[3] = {(T)d.inv_dx0, (T)d.inv_dx1, T(0)};
-    if (lt == 0 && tid == 0) {
-        d.ctl->t = local == 0 ? dt : d.ctl->t + dt;
-        d.ctl->dt_last = dt;
-        d.ctl->smax[(slot + 2) % 3] = 0ull;
-    }
-    // stage the tile with one ghost layer (cells beyond the x/y ghost are not read)
-    constexpr int CELLS = (TY + 2) * (TX + 2);
-    for (int e = tid; e < NC * CELLS; e += NT) {
-        int m, r;
-        if (LAYOUT == LAYOUT_SOA) { m = e / CELLS; r = e % CELLS; }
-        else { m = e % NC; r = e / NC; }
-        const int cy = r / (TX + 2) - 1, cx = r % (TX + 2) - 1;
-        const int gx = x0 + cx, gy = y0 + cy;
-        T v = T(0);
-        if (gx <= g.n[0] && gy <= g.n[1]) v = in[geom_elem(g, gx, gy, 0, m)];
-        sm.S[m][cy + 1][cx + 1] = v;
-    }
-    __syncthreads();
-    T chk = T(1);
-    // face fluxes: x faces between fx-1 and fx, y faces between fy-1 and fy
-    for (int it = tid; it < NFX + NFY; it += NT) {
-        T a[NC], b[NC], F[NC];
-        if (it < NFX) {
-            const int fx = it % (TX + 1), cy = it / (TX + 1);
-#pragma unroll
-            for (int m = 0; m < NC; ++m) { a[m] = sm.S[m][cy + 1][fx]; b[m] = sm.S[m][cy + 1][fx + 1]; }
-            rusanov<T, 2, 0>(a, b, gamma, gm1, F, chk, (x0 + fx <= g.n[0]) && (y0 + cy < g.n[1]));
-#pragma unroll
-            for (int m = 0; m < NC; ++m) sm.FX[m][it] = F[m];
-        } else {
-            const int k = it - NFX;
-            const int cx = k % TX, fy = k / TX;
-#pragma unroll
-            for (int m = 0; m < NC; ++m) { a[m] = sm.S[m][fy][cx + 1]; b[m] = sm.S[m][fy + 1][cx + 1]; }
-            rusanov<T, 2, 1>(a, b, gamma, gm1, F, chk, (x0 + cx < g.n[0]) && (y0 + fy <= g.n[1]));
-#pragma unroll
-            for (int m = 0; m < NC; ++m) sm.FY[m][k] = F[m];
-        }
-    }
-    __syncthreads();
-    const int gx = x0 + lx, gy = y0 + ly;
-    const bool valid = (gx < g.n[0]) & (gy < g.n[1]);
-    T smax = T(0);
-    bool bad = !(chk > T(0));
-    if (valid) {
-        T qn[NC];
-#pragma unroll
-        for (int m = 0; m < NC; ++m) {
-            T acc = (sm.FX[m][ly * (TX + 1) + lx + 1] - sm.FX[m][ly * (TX + 1) + lx]) * inv_dx[0];
-            acc += (sm.FY[m][(ly + 1) * TX + lx] - sm.FY[m][ly * TX + lx]) * inv_dx[1];
-            qn[m] = sm.S[m][ly + 1][lx + 1] - dtT * acc;
-        }
-        const long long base = geom_cell(g, gx, gy, 0) * g.cell_stride;
-#pragma unroll
-        for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = qn[m];
-        bool ok;
-        smax = wave_sum<T, 2>(qn, gamma, gm1, inv_dx, ok);
-        bad |= !ok;
-        if (gx < g.h || gx >= g.n[0] - g.h || gy < g.h || gy >= g.n[1] - g.h)
-            write_ghost_images<T, 2>(out, g, d.bc, gx, gy, 0, qn);
-    }
-    // tile max of the new wave-speed sums -> the instance's next ring slot
-    double v = (double)smax;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    const int any_bad = __syncthreads_or(bad ? 1 : 0);
-    if ((tid & 31) == 0) red[tid >> 5] = v;
-    __syncthreads();
+    const unsigned long long gstep = __ldcg(&bctl->gstep[0]);
+    const int end = __ldcg(&bctl->ntiles_e);
     if (tid == 0) {
-        double m = 0.0;
-        for (int w = 0; w < NT / 32; ++w) m = fmax(m, red[w]);
-        atomic_max_pos_double(&d.ctl->smax[(slot + 1) % 3], m);
-        if (any_bad) {
-            record_bad(d.ctl, BAD_STATE, x0, y0, 0);
-            atomicOr(&d.ctl->err, DEV_ERR_NUMERIC);
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NCT / 32);
         }
+        fence_mbar_init();
     }
     __syncthreads();
+
+    if (tid >= NCT) {
+        // ---------------- producer warp ----------------
+        if (tid == NCT) {
+            unsigned seq = 0;
+            bool ok = true;
+            for (int t = blockIdx.x;; t += gridDim.x) {
+                // next table entry whose instance steps in this launch
+                const BatchEuler* d = nullptr;
+                long long local = 0;
+                for (; t < end; t += gridDim.x) {
+                    d = &euler[__ldg(&table[t]) >> 1];
+                    local = (long long)gstep - d->start_step;
+                    if (local >= 0 && local < d->nsteps) break;
+                }
+                const unsigned s = seq % NS;
+                if (seq >= NS && !mbar_wait_bounded(&empty[s], ((seq / NS) - 1) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                Hdr* h = slot_hdr(s);
+                if (t >= end) {
+                    h->tile = -1;
+                    mbar_arrive(&full[s]);
+                    ++seq;
+                    break;
+                }
+                const int lt = t - d->tile_begin;
+                const int x0 = (lt % d->tiles_x) * TX, y0 = (lt / d->tiles_x) * TY;
+                const int rs = (int)(local % 3);
+                FieldCtl* ctl = d->ctl;
+                const double dt = d->cfl / __longlong_as_double((long long)__ldcg(&ctl->smax[rs]));
+                h->gamma = (T)d->gamma;
+                h->gm1 = (T)d->gm1;
+                h->inv_dx0 = (T)d->inv_dx0;
+                h->inv_dx1 = (T)d->inv_dx1;
+                h->dt = (T)dt;
+                h->tile = t;
+                h->x0 = x0;
+                h->y0 = y0;
+                h->local = local;
+                if (lt == 0) {
+                    ctl->t = local == 0 ? dt : ctl->t + dt;
+                    ctl->dt_last = dt;
+                    ctl->smax[(rs + 2) % 3] = 0ull;
+                }
+                const CUtensorMap* map = &d->map[local & 1];
+                tensormap_acquire(map);
+                const int xs = d->g.lead + d->g.h + x0 - 1 - C::OFF, ys = d->g.h + y0 - 1;
+                mbar_arrive_expect_tx(&full[s], (uint32_t)(C::SLOT_ELEMS * sizeof(T)));
+                if (LAYOUT == LAYOUT_SOA) tma_load_3d(slot_tile(s), map, xs, ys, 0, &full[s]);
+                else tma_load_2d(slot_tile(s), map, xs * NC, ys, &full[s]);
+                ++seq;
+            }
+            // every load this warp issued completes before the CTA exits (bounded)
+            for (unsigned sq = seq > NS ? seq - NS : 0; sq < seq; ++sq)
+                mbar_wait_bounded(&full[sq % NS], (sq / NS) & 1u);
+            if (!ok) atomicOr(&bctl->err, DEV_ERR_TIMEOUT);
+        }
+        __syncwarp();
+        batch_finish_launch(bctl, 0);
+        return;
+    }
+
+    // ---------------- consumer warps ----------------
+    const int lx = tid % TX, ly = tid / TX;
+    bool timed_out = false;
+    for (unsigned seq = 0;; ++seq) {
+        const unsigned s = seq % NS;
+        const bool got = mbar_wait_bounded(&full[s], (seq / NS) & 1u);
+        Hdr h{};
+        if (got) h = *slot_hdr(s);
+        const bool stop = !got || h.tile < 0;  // taken by all consumers together at the barrier below
+        timed_out |= !got;
+        const BatchEuler& d = euler[stop ? 0 : (__ldg(&table[h.tile]) >> 1)];  // entry 0 always exists
+        const FieldGeom g = d.g;
+        const int x0 = h.x0, y0 = h.y0;
+        const T gamma = h.gamma, gm1 = h.gm1, dtT = h.dt;
+        const T inv_dx[3] = {h.inv_dx0, h.inv_dx1, T(0)};
+        const T* S = slot_tile(s);
+        T* FX = faces(seq & 1u);
+        T* FY = FX + NC * NFX;
+
+        // face fluxes: x faces between cells fx-1 | fx, y faces between fy-1 | fy
+        T chk = T(1);
+#pragma unroll 1
+        for (int k = 0; k < (stop ? 0 : KF); ++k) {
+            const int it = tid + k * NCT;
+            T a[NC], b[NC], F[NC];
+            if (it < NFXr) {
+                if (it >= NFX) continue;
+                const int fx = it % (TX + 1), cy = it / (TX + 1);
+                const int o = PV::idx(fx - 1, cy, 0);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    a[m] = S[o + m * SM];
+                    b[m] = S[o + SX + m * SM];
+                }
+                rusanov<T, 2, 0>(a, b, gamma, gm1, F, chk, (x0 + fx <= g.n[0]) && (y0 + cy < g.n[1]));
+#pragma unroll
+                for (int m = 0; m < NC; ++m) FX[m * NFX + it] = F[m];
+            } else {
+                const int kk = it - NFXr;
+                if (kk >= NFY) continue;
+                const int cx = kk % TX, fy = kk / TX;
+                const int o = PV::idx(cx, fy - 1, 0);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    a[m] = S[o + m * SM];
+                    b[m] = S[o + SY + m * SM];
+                }
+                rusanov<T, 2, 1>(a, b, gamma, gm1, F, chk, (x0 + cx < g.n[0]) && (y0 + fy <= g.n[1]));
+#pragma unroll
+                for (int m = 0; m < NC; ++m) FY[m * NFY + kk] = F[m];
+            }
+        }
+        __syncwarp();
+        if (consumer_sync_or(stop)) break;  // faces of this tile written, unless a consumer stopped
+        const int gx = x0 + lx, gy = y0 + ly;
+        const bool valid = (gx < g.n[0]) & (gy < g.n[1]);
+        T smax = T(0);
+        bool bad = !(chk > T(0));
+        if (valid) {
+            T* __restrict__ out = static_cast<T*>(d.buf[(h.local & 1) ^ 1]);
+            const int o = PV::idx(lx, ly, 0);
+            T qn[NC];
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                T acc = (FX[m * NFX + ly * (TX + 1) + lx + 1] - FX[m * NFX + ly * (TX + 1) + lx]) * inv_dx[0];
+                acc += (FY[m * NFY + (ly + 1) * TX + lx] - FY[m * NFY + ly * TX + lx]) * inv_dx[1];
+                qn[m] = S[o + m * SM] - dtT * acc;
+            }
+            const long long base = geom_cell(g, gx, gy, 0) * g.cell_stride;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = qn[m];
+            bool ok;
+            smax = wave_sum<T, 2>(qn, gamma, gm1, inv_dx, ok);
+            bad |= !ok;
+            if (gx < g.h || gx >= g.n[0] - g.h || gy < g.h || gy >= g.n[1] - g.h)
+                write_ghost_images<T, 2>(out, g, d.bc, gx, gy, 0, qn);
+        }
+        // this thread's reads of the slot are done: the warp releases it
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+        // warp max of the new wave-speed sums -> the instance's next ring slot
+        T v = smax;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        const bool wbad = __any_sync(0xffffffffu, bad);
+        if ((tid & 31) == 0) {
+            FieldCtl* ctl = d.ctl;
+            const int rs = (int)(h.local % 3);
+            atomic_max_pos_double(&ctl->smax[(rs + 1) % 3], (double)v);
+            if (wbad) {
+                record_bad(ctl, BAD_STATE, x0, y0, 0);
+                atomicOr(&ctl->err, DEV_ERR_NUMERIC);
+            }
+        }
+    }
+    if (timed_out) atomicOr(&bctl->err, DEV_ERR_TIMEOUT);  // the runtime fails the resident set
+    __syncwarp();
+    batch_finish_launch(bctl, 0);
 }
 
 template <typename T>
@@ -207,47 +377,24 @@ __device__ __forceinline__ void batch_fim_tile(FimSmem<T, 2>& sm, const BatchFim
     }
 }
 
-// kind 0: one Euler step of every resident Euler problem; kind 1: one FIM
-// iteration of every resident eikonal problem.
-template <typename T, int LAYOUT, int TX, int TY>
-__global__ void __launch_bounds__(256) batch_step_kernel(const BatchEuler* __restrict__ euler,
-                                                         const BatchFim<T>* __restrict__ fim,
-                                                         const int* __restrict__ table, BatchCtl* __restrict__ bctl,
-                                                         int kind)
+// One FIM iteration of every resident eikonal problem.
+template <typename T>
+__global__ void __launch_bounds__(256) batch_fim_kernel(const BatchFim<T>* __restrict__ fim,
+                                                        const int* __restrict__ table, BatchCtl* __restrict__ bctl)
 {
-    static_assert(TX * TY == 256, "the batched step runs 256 threads (the FIM tile size)");
-    __shared__ BatchSmem<T, LAYOUT, TX, TY> sm;
-    __shared__ double red[8];
-    const unsigned long long gstep = __ldcg(&bctl->gstep[kind]);
-    const int begin = kind == 0 ? 0 : __ldcg(&bctl->ntiles_e);
-    const int end = kind == 0 ? __ldcg(&bctl->ntiles_e) : __ldcg(&bctl->ntiles);
+    __shared__ FimSmem<T, 2> sm;
+    const unsigned long long gstep = __ldcg(&bctl->gstep[1]);
+    const int begin = __ldcg(&bctl->ntiles_e);
+    const int end = __ldcg(&bctl->ntiles);
     for (int t = begin + blockIdx.x; t < end; t += gridDim.x) {
-        const int entry = __ldg(&table[t]);
-        const int idx = entry >> 1;
-        if (kind == 0) {
-            const BatchEuler& d = euler[idx];
-            const long long local = (long long)gstep - d.start_step;
-            if (local < 0 || local >= d.nsteps) continue;
-            batch_euler_tile<T, LAYOUT, TX, TY>(sm.e, red, d, t - d.tile_begin, local);
-        } else {
-            const BatchFim<T>& d = fim[idx];
-            const long long k = (long long)gstep - d.start_step;
-            if (k < 0) continue;
-            const unsigned long long st = __ldcg(d.status);
-            if (st != 0ull && (unsigned long long)k > (st >> 2)) continue;
-            batch_fim_tile<T>(sm.f, d, t - d.tile_begin, k);
-        }
+        const BatchFim<T>& d = fim[__ldg(&table[t]) >> 1];
+        const long long k = (long long)gstep - d.start_step;
+        if (k < 0) continue;
+        const unsigned long long st = __ldcg(d.status);
+        if (st != 0ull && (unsigned long long)k > (st >> 2)) continue;
+        batch_fim_tile<T>(sm, d, t - d.tile_begin, k);
     }
-    // the last CTA to finish advances this kind's counter
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (atomicAdd(&bctl->done[kind], 1u) == gridDim.x - 1) {
-            bctl->done[kind] = 0u;
-            __threadfence();
-            atomicAdd(&bctl->gstep[kind], 1ull);
-        }
-    }
+    batch_finish_launch(bctl, 1);
 }
 
 }  // namespace ripple

@@ -119,31 +119,25 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-const CUtensorMap* field_map(ripple_field f, int buffer, int kind, int r, int tx, int ty, ripple_status* st)
+ripple_status encode_plane_map(void* buffer, const FieldGeom& g, ripple_layout layout, ripple_dtype dtype, int kind,
+                               int r, int tx, int ty, CUtensorMap* out)
 {
-    *st = RIPPLE_OK;
-    for (auto& m : f->maps)
-        if (m.buffer == buffer && m.kind == kind && m.r == r && m.tx == tx && m.ty == ty) return &m.map;
     auto enc = encode_fn();
-    if (!enc) {
-        *st = fail(RIPPLE_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
-        return nullptr;
-    }
-    const FieldGeom& g = f->geom;
-    const int es = (int)elem_size(f->dtype);
-    const int nc = f->ncomp;
-    const bool soa = f->layout == RIPPLE_SOA;
+    if (!enc) return fail(RIPPLE_ERR_CUDA, "cuTensorMapEncodeTiled is unavailable");
+    const int es = (int)elem_size(dtype);
+    const int nc = g.ncomp;
+    const bool soa = layout == RIPPLE_SOA;
     cuuint64_t dims[4], strides[3];
     cuuint32_t box[4], estr[4] = {1, 1, 1, 1};
     cuuint32_t rank;
-    char* base = static_cast<char*>(f->buf[buffer]);
-    const BoxGeom bg = plane_box(es, nc, f->layout == RIPPLE_AOS, r, tx, ty);
+    char* base = static_cast<char*>(buffer);
+    const BoxGeom bg = plane_box(es, nc, !soa, r, tx, ty);
     if (kind == 0) {
         if (soa) {
             dims[0] = g.px; dims[1] = g.py;
             strides[0] = g.px * es; strides[1] = g.px * g.py * es;
             box[0] = bg.bx; box[1] = bg.by;
-            if (f->ndim == 3) {
+            if (g.ndim == 3) {
                 rank = 4;
                 dims[2] = g.pz; dims[3] = nc;
                 strides[2] = g.px * g.py * g.pz * es;
@@ -157,7 +151,7 @@ const CUtensorMap* field_map(ripple_field f, int buffer, int kind, int r, int tx
             dims[0] = g.px * nc; dims[1] = g.py;
             strides[0] = g.px * nc * es;
             box[0] = bg.bx * nc; box[1] = bg.by;
-            if (f->ndim == 3) {
+            if (g.ndim == 3) {
                 rank = 3;
                 dims[2] = g.pz;
                 strides[1] = g.px * nc * g.py * es;
@@ -172,7 +166,7 @@ const CUtensorMap* field_map(ripple_field f, int buffer, int kind, int r, int tx
             dims[0] = g.n[0]; dims[1] = g.n[1];
             strides[0] = g.px * es; strides[1] = g.px * g.py * es;
             box[0] = tx; box[1] = ty;
-            if (f->ndim == 3) {
+            if (g.ndim == 3) {
                 rank = 4;
                 dims[2] = g.n[2]; dims[3] = nc;
                 strides[2] = g.px * g.py * g.pz * es;
@@ -186,7 +180,7 @@ const CUtensorMap* field_map(ripple_field f, int buffer, int kind, int r, int tx
             dims[0] = (cuuint64_t)g.n[0] * nc; dims[1] = g.n[1];
             strides[0] = g.px * nc * es;
             box[0] = tx * nc; box[1] = ty;
-            if (f->ndim == 3) {
+            if (g.ndim == 3) {
                 rank = 3;
                 dims[2] = g.n[2];
                 strides[1] = g.px * nc * g.py * es;
@@ -196,15 +190,23 @@ const CUtensorMap* field_map(ripple_field f, int buffer, int kind, int r, int tx
             }
         }
     }
-    MapEntry e{};
-    e.buffer = buffer; e.kind = kind; e.r = r; e.tx = tx; e.ty = ty;
-    CUresult cr = enc(&e.map, f->dtype == RIPPLE_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+    CUresult cr = enc(out, dtype == RIPPLE_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                       rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) {
-        *st = fail(RIPPLE_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)cr) + ")");
-        return nullptr;
-    }
+    if (cr != CUDA_SUCCESS)
+        return fail(RIPPLE_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)cr) + ")");
+    return RIPPLE_OK;
+}
+
+const CUtensorMap* field_map(ripple_field f, int buffer, int kind, int r, int tx, int ty, ripple_status* st)
+{
+    *st = RIPPLE_OK;
+    for (auto& m : f->maps)
+        if (m.buffer == buffer && m.kind == kind && m.r == r && m.tx == tx && m.ty == ty) return &m.map;
+    MapEntry e{};
+    e.buffer = buffer; e.kind = kind; e.r = r; e.tx = tx; e.ty = ty;
+    *st = encode_plane_map(f->buf[buffer], f->geom, f->layout, f->dtype, kind, r, tx, ty, &e.map);
+    if (*st != RIPPLE_OK) return nullptr;
     f->maps.push_back(e);
     return &f->maps.back().map;
 }

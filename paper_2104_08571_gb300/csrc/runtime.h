@@ -142,6 +142,10 @@ FieldGeom make_field_geom(int ndim, const int64_t* dims, int ncomp, ripple_layou
 ripple_status ctx_alloc(ripple_ctx ctx, size_t bytes, void** out);
 void ctx_free(ripple_ctx ctx, void* p, size_t bytes);
 ripple_status ensure_second_buffer(ripple_field f);
+// TMA map of a padded buffer of geometry g: kind 0 stages planes of a tile plus
+// r ghost cells (box of plane_box), kind 1 stores interior tiles of tx x ty.
+ripple_status encode_plane_map(void* buffer, const FieldGeom& g, ripple_layout layout, ripple_dtype dtype, int kind,
+                               int r, int tx, int ty, CUtensorMap* out);
 const CUtensorMap* field_map(ripple_field f, int buffer, int kind, int r, int tx, int ty, ripple_status* st);
 ripple_status take_device_error(ripple_field f);
 size_t elem_size(ripple_dtype d);

@@ -145,6 +145,15 @@ __device__ __forceinline__ void bulk_wait()
     asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// Acquire a tensor map that lives in global memory (not a kernel parameter)
+// and may have been rewritten by a host copy since the tensormap proxy last
+// read that address: orders the generic-proxy contents before TMA use.
+__device__ __forceinline__ void tensormap_acquire(const CUtensorMap* map)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.sys [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
+
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map)
 {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
