@@ -547,6 +547,15 @@ ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t 
         for (int c = 0; c < kNumSweepVariants && v < 0; ++c)
             if (sweep_smem(U->dtype, U->ndim, layout, scheme, c) > 0) v = c;
         if (v < 0) return fail(RIPPLE_ERR_INTERNAL, "no sweep kernel fits this configuration");
+        // a 2D grid with fewer tiles than SMs: the shorter tile spreads it over more SMs
+        // (the one-cell-per-item 32x4 variant; FP64 arithmetic is the bound there)
+        auto tiles = [&](int c) {
+            return ((g.n[0] + kSweepVariants[c].tx - 1) / kSweepVariants[c].tx) *
+                   ((g.n[1] + kSweepVariants[c].ty - 1) / kSweepVariants[c].ty);
+        };
+        if (U->ndim == 2 && U->dtype == RIPPLE_F64 && tiles(v) < ctx->sm_count &&
+            sweep_smem(U->dtype, U->ndim, layout, scheme, 1) > 0 && tiles(1) > tiles(v))
+            v = 1;
     }
     const int tx = kSweepVariants[v].tx, ty = kSweepVariants[v].ty;
     const double inv_dx[3] = {1.0 / p->dx[0], 1.0 / p->dx[1], U->ndim == 3 ? 1.0 / p->dx[2] : 0.0};
