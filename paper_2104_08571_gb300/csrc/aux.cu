@@ -25,6 +25,13 @@ cudaError_t launch_prep(int dtype, int dim, void* buf, FieldCtl* ctl, const Fiel
     return cudaGetLastError();
 }
 
+cudaError_t launch_pad_nan(int dtype, void* buf, const FieldGeom& g, int grid, cudaStream_t s)
+{
+    if (dtype == RIPPLE_F32) pad_fill_nan_kernel<float><<<grid, 256, 0, s>>>(static_cast<float*>(buf), g);
+    else pad_fill_nan_kernel<double><<<grid, 256, 0, s>>>(static_cast<double*>(buf), g);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_totals(int dtype, int ncomp, const void* buf, const FieldGeom& g, double* partials, int nblocks,
                           FieldCtl* ctl, cudaStream_t s)
 {

@@ -66,6 +66,26 @@ __global__ void __launch_bounds__(256) euler_prep_kernel(T* __restrict__ buf, Fi
     }
 }
 
+// Quiet NaN in every padded cell outside the interior (all components).  The
+// sweep rewrites the face ghosts each step; edge and corner ghosts and the
+// alignment padding stay NaN, so a stencil item that reaches beyond the
+// ghost layers carries NaN, which the admissibility minimum ignores.
+template <typename T>
+__global__ void __launch_bounds__(256) pad_fill_nan_kernel(T* __restrict__ buf, const FieldGeom g)
+{
+    const long long cells = g.px * g.py * g.pz;
+    const T qnan = (T)__int_as_float(0x7fc00000);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
+         c += (long long)gridDim.x * blockDim.x) {
+        const long long x = c % g.px, r = c / g.px;
+        const long long y = r % g.py, z = r / g.py;
+        const bool inside = x >= g.lead + g.h && x < g.lead + g.h + g.n[0] && y >= g.h && y < g.h + g.n[1] &&
+                            (g.ndim < 3 || (z >= g.h && z < g.h + g.n[2]));
+        if (inside) continue;
+        for (int m = 0; m < g.ncomp; ++m) buf[c * g.cell_stride + (long long)m * g.comp_stride] = qnan;
+    }
+}
+
 // Neumaier (improved Kahan-Babuska) compensated accumulation in FP64.
 struct Neumaier {
     double s, c;

@@ -236,9 +236,7 @@ __global__ void __launch_bounds__(256, 2)
                         qc[m] = f2{A.y, B.x};
                         qp[m] = B;
                     }
-                    const bool vr = y0 + cy < g.n[1];
-                    muscl<f2, DIM, 0>(qm, qc, qp, gm1, half_dtdx[0], L, Rr, chk, vr && x0 + c0 <= g.n[0],
-                                      vr && x0 + c0 + 1 <= g.n[0]);
+                    muscl<f2, DIM, 0>(qm, qc, qp, gm1, half_dtdx[0], L, Rr, chk);
                     const int pi = cy * PC::XR + c0 + 1;
 #pragma unroll
                     for (int m = 0; m < NC; ++m) {
@@ -255,9 +253,7 @@ __global__ void __launch_bounds__(256, 2)
                     load_pair(S, o - SY, qm);
                     load_pair(S, o, qc);
                     load_pair(S, o + SY, qp);
-                    muscl<f2, DIM, 1>(qm, qc, qp, gm1, half_dtdx[1], L, Rr, chk,
-                                      (x0 + cx < g.n[0]) && (y0 + cy <= g.n[1]),
-                                      (x0 + cx + 1 < g.n[0]) && (y0 + cy <= g.n[1]));
+                    muscl<f2, DIM, 1>(qm, qc, qp, gm1, half_dtdx[1], L, Rr, chk);
                     const int pi = PC::NPX + (cy + 1) * TX + cx;
 #pragma unroll
                     for (int m = 0; m < NC; ++m) {
@@ -280,16 +276,16 @@ __global__ void __launch_bounds__(256, 2)
                     f2 q0[NC], q1[NC];
                     load_pair(plane_ptr(seq_base + 0), my_off, q0);
                     load_pair(plane_ptr(seq_base + 1), my_off, q1);
-                    rus<f2, DIM, 2 % DIM>(q0, q1, gamma, gm1, Fzm, chk, vx0, vx1);
+                    rus<f2, DIM, 2 % DIM>(q0, q1, gamma, gm1, Fzm, chk);
                 } else {
                     f2 q0[NC], q1[NC], q2[NC], q3[NC], L1[NC], R1[NC], L2[NC];
                     load_pair(plane_ptr(seq_base + 0), my_off, q0);
                     load_pair(plane_ptr(seq_base + 1), my_off, q1);
                     load_pair(plane_ptr(seq_base + 2), my_off, q2);
                     load_pair(plane_ptr(seq_base + 3), my_off, q3);
-                    muscl<f2, DIM, 2 % DIM>(q0, q1, q2, gm1, half_dtdx[2], L1, R1, chk, vx0, vx1);
-                    muscl<f2, DIM, 2 % DIM>(q1, q2, q3, gm1, half_dtdx[2], L2, zR, chk, vx0, vx1);
-                    rus<f2, DIM, 2 % DIM>(R1, L2, gamma, gm1, Fzm, chk, vx0, vx1);
+                    muscl<f2, DIM, 2 % DIM>(q0, q1, q2, gm1, half_dtdx[2], L1, R1, chk);
+                    muscl<f2, DIM, 2 % DIM>(q1, q2, q3, gm1, half_dtdx[2], L2, zR, chk);
+                    rus<f2, DIM, 2 % DIM>(R1, L2, gamma, gm1, Fzm, chk);
                 }
             }
         } else {
@@ -311,15 +307,15 @@ __global__ void __launch_bounds__(256, 2)
                     f2 q0[NC], q1[NC];
                     load_pair(S, my_off, q0);
                     load_pair(plane_ptr(seq_base + jc + 1), my_off, q1);
-                    rus<f2, DIM, 2 % DIM>(q0, q1, gamma, gm1, Fzp, chk, vx0, vx1);
+                    rus<f2, DIM, 2 % DIM>(q0, q1, gamma, gm1, Fzp, chk);
                 } else {
                     // predicted states of plane z + 1 and the face z + 1/2
                     f2 q0[NC], q1[NC], q2[NC], L[NC], Rn[NC];
                     load_pair(S, my_off, q0);
                     load_pair(plane_ptr(seq_base + jc + 1), my_off, q1);
                     load_pair(plane_ptr(seq_base + jc + 2), my_off, q2);
-                    muscl<f2, DIM, 2 % DIM>(q0, q1, q2, gm1, half_dtdx[2], L, Rn, chk, vx0, vx1);
-                    rus<f2, DIM, 2 % DIM>(zR, L, gamma, gm1, Fzp, chk, vx0, vx1);
+                    muscl<f2, DIM, 2 % DIM>(q0, q1, q2, gm1, half_dtdx[2], L, Rn, chk);
+                    rus<f2, DIM, 2 % DIM>(zR, L, gamma, gm1, Fzp, chk);
 #pragma unroll
                     for (int m = 0; m < NC; ++m) zR[m] = Rn[m];
                 }
@@ -357,9 +353,7 @@ __global__ void __launch_bounds__(256, 2)
                             b[m] = B;
                         }
                     }
-                    const bool vr = y0 + cy < g.n[1];
-                    rus<f2, DIM, 0>(a, b, gamma, gm1, F, chk, vr && (x0 + f <= g.n[0]),
-                                    vr && (f + 1 <= TX) && (x0 + f + 1 <= g.n[0]));
+                    rus<f2, DIM, 0>(a, b, gamma, gm1, F, chk);
                     const int fi = cy * PC::FXR + f;
 #pragma unroll
                     for (int m = 0; m < NC; ++m) st2(FX + m * PC::NFX + fi, F[m]);
@@ -380,8 +374,7 @@ __global__ void __launch_bounds__(256, 2)
                         load_pair(S, o, a);
                         load_pair(S, o + SY, b);
                     }
-                    rus<f2, DIM, 1>(a, b, gamma, gm1, F, chk, (x0 + cx < g.n[0]) && (y0 + fy <= g.n[1]),
-                                    (x0 + cx + 1 < g.n[0]) && (y0 + fy <= g.n[1]));
+                    rus<f2, DIM, 1>(a, b, gamma, gm1, F, chk);
 #pragma unroll
                     for (int m = 0; m < NC; ++m) st2(FY + m * PC::NFY + fy * TX + cx, F[m]);
                 }

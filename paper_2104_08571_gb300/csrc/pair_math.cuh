@@ -99,16 +99,19 @@ __device__ __forceinline__ float min3f(float a, float b, float c)
     return r;
 }
 
-// Smallest of four quantities per lane into chk, for the lanes that lie in the domain.
-__device__ __forceinline__ void track4(float& chk, float a, float b, float c, float d, bool v0, bool)
+// Smallest density/pressure of four states into chk (both lanes).  Items that
+// reach beyond a field's ghost layers read NaN (padding and out-of-tensor
+// cells are NaN), which the minimum ignores, so no per-lane domain predicate
+// is needed.  A NaN produced from in-domain data is skipped here too but
+// reaches the updated cells, whose own check catches it.
+__device__ __forceinline__ void track4(float& chk, float a, float b, float c, float d)
 {
-    if (v0) chk = min3f(chk, min3f(a, b, c), d);
+    chk = min3f(chk, min3f(a, b, c), d);
 }
-__device__ __forceinline__ void track4(float& chk, f2 a, f2 b, f2 c, f2 d, bool v0, bool v1)
+__device__ __forceinline__ void track4(float& chk, f2 a, f2 b, f2 c, f2 d)
 {
     const float m0 = min3f(a.x, b.x, c.x), m1 = min3f(a.y, b.y, c.y);
-    if (v0) chk = min3f(chk, m0, d.x);
-    if (v1) chk = min3f(chk, m1, d.y);
+    chk = min3f(chk, min3f(m0, m1, d.x), d.y);
 }
 
 // Physical flux along axis D; also returns 1/rho, the normal velocity, the pressure.
@@ -128,15 +131,15 @@ __device__ __forceinline__ void pflux(const V (&q)[DIM + 2], V gm1, V (&F)[DIM +
 }
 
 // Rusanov face flux along D between left states a and right states b;
-// the smallest density/pressure of the in-domain lanes (v0, v1) goes to chk.
+// the smallest density/pressure of both goes to chk.
 template <typename V, int DIM, int D>
 __device__ __forceinline__ void rus(const V (&a)[DIM + 2], const V (&b)[DIM + 2], V gamma, V gm1, V (&F)[DIM + 2],
-                                    float& chk, bool v0, bool v1)
+                                    float& chk)
 {
     V Fa[DIM + 2], Fb[DIM + 2], ia, ua, pa, ib, ub, pb;
     pflux<V, DIM, D>(a, gm1, Fa, ia, ua, pa);
     pflux<V, DIM, D>(b, gm1, Fb, ib, ub, pb);
-    track4(chk, a[0], pa, b[0], pb, v0, v1);
+    track4(chk, a[0], pa, b[0], pb);
     const V ca = sqrt_v(gamma * pa * ia);
     const V cb = sqrt_v(gamma * pb * ib);
     const V s = max_v(abs_v(ua) + ca, abs_v(ub) + cb);
@@ -148,7 +151,7 @@ __device__ __forceinline__ void rus(const V (&a)[DIM + 2], const V (&b)[DIM + 2]
 // MUSCL-Hancock face states of cells along D from (left, centre, right).
 template <typename V, int DIM, int D>
 __device__ __forceinline__ void muscl(const V (&qm)[DIM + 2], const V (&q)[DIM + 2], const V (&qp)[DIM + 2], V gm1,
-                                      V half_dtdx, V (&L)[DIM + 2], V (&R)[DIM + 2], float& chk, bool v0, bool v1)
+                                      V half_dtdx, V (&L)[DIM + 2], V (&R)[DIM + 2], float& chk)
 {
     const V half = splat<V>(0.5f), mhalf = splat<V>(-0.5f);
 #pragma unroll
@@ -160,7 +163,7 @@ __device__ __forceinline__ void muscl(const V (&qm)[DIM + 2], const V (&q)[DIM +
     V FL[DIM + 2], FR[DIM + 2], il, ir, u, pl, pr;
     pflux<V, DIM, D>(L, gm1, FL, il, u, pl);
     pflux<V, DIM, D>(R, gm1, FR, ir, u, pr);
-    track4(chk, L[0], pl, R[0], pr, v0, v1);
+    track4(chk, L[0], pl, R[0], pr);
 #pragma unroll
     for (int m = 0; m < DIM + 2; ++m) {
         const V inc = half_dtdx * (FL[m] - FR[m]);

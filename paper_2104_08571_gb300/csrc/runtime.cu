@@ -192,7 +192,10 @@ ripple_status encode_plane_map(void* buffer, const FieldGeom& g, ripple_layout l
     }
     CUresult cr = enc(out, dtype == RIPPLE_F64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
                       rank, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      // staging loads read NaN beyond the tensor (as the padded cells of an Euler
+                      // field); stores are clipped and fill nothing
+                      kind == 0 ? CU_TENSOR_MAP_FLOAT_OOB_FILL_NAN_REQUEST_ZERO_FMA : CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (cr != CUDA_SUCCESS)
         return fail(RIPPLE_ERR_CUDA, "cuTensorMapEncodeTiled failed (code " + std::to_string((int)cr) + ")");
     return RIPPLE_OK;
@@ -537,6 +540,15 @@ ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t 
     ripple_ctx ctx = U->ctx;
     ripple_status st = ensure_second_buffer(U);
     if (st != RIPPLE_OK) return st;
+    if (!U->pad_nan) {
+        // stencil items beyond the ghost layers then read NaN (ignored by the
+        // admissibility minimum); prep below refills the current face ghosts
+        const long long cells = g.px * g.py * g.pz;
+        for (int b = 0; b < 2; ++b)
+            RIPPLE_CUDA(launch_pad_nan(U->dtype, U->buf[b], g, grid_for(ctx, cells, 256), ctx->stream));
+        U->pad_nan = true;
+        U->prepared = false;
+    }
 
     const int layout = U->layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
     const int scheme = p->scheme == RIPPLE_MUSCL_HANCOCK_MINMOD ? SCHEME_MUSCL : SCHEME_RUSANOV1;

@@ -70,6 +70,8 @@ int sweep_occ_f64_3d(int layout, int scheme, int v);
 // Aux kernels (f32/f64 x 2D/3D), defined in aux.cu.
 cudaError_t launch_prep(int dtype, int dim, void* buf, FieldCtl* ctl, const FieldGeom& g, int bc, double gamma,
                         const double inv_dx[3], int slot, int grid, cudaStream_t s);
+// Quiet NaN in every non-interior cell of a padded buffer (pad_fill_nan_kernel).
+cudaError_t launch_pad_nan(int dtype, void* buf, const FieldGeom& g, int grid, cudaStream_t s);
 cudaError_t launch_totals(int dtype, int ncomp, const void* buf, const FieldGeom& g, double* partials, int nblocks,
                           FieldCtl* ctl, cudaStream_t s);
 cudaError_t launch_interior_copy(int dtype, void* buf, const FieldGeom& g, void* dense, int dense_layout, int dir,
@@ -121,6 +123,7 @@ struct ripple_field_s {
     std::deque<ripple::MapEntry> maps;  // deque: push_back keeps earlier entries in place
     // Euler bookkeeping
     long long steps_total = 0;  // selects the smax ring slot
+    bool pad_nan = false;       // non-interior cells of both buffers set to NaN (before the first step)
     bool prepared = false;      // ghosts + smax of the current buffer valid for:
     double prep_gamma = 0, prep_dx[3] = {0, 0, 0};
     int prep_bc = -1;
