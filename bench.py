@@ -43,7 +43,7 @@ BYTES_PER_CELL_UPDATE = 40  # FP32, 5 components: 20 B read + 20 B written per c
 # DRAM bytes per cell update of the sweep kernel as measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum of one 256x256x128 launch, divided by its cells);
 # traffic scales with the cells of a launch.  Re-measure whenever the kernel changes.
-DRAM_BYTES_PER_CELL_UPDATE = 355.013888e6 / (256 * 256 * 128)
+DRAM_BYTES_PER_CELL_UPDATE = (214383616 + 140687872) / (256 * 256 * 128)
 METRIC = "cell-updates/s"
 ACTIVE_CELLS = 4 << 20  # serving: per-step cell budget of stepped Euler problems
 
@@ -197,6 +197,15 @@ def bench_gpu(args, rank, world, local):
     st = R.ripple_fv_step(f, prm, 0)  # synchronous error check + totals of the final state
     result["soa_ms_per_step"] = ms / args.steps
     result["soa_totals_mass"] = st["totals"][0]
+    # parity data (checked against the oracle in the CPU leg): the state after the
+    # timed steps and one more GPU step of it at seeded sampled cells
+    par = {}
+    if rank == 0 and not args.skip_cpu_baseline and not args.sweep_only:
+        Un = R.ripple_field_download(f)
+        st1 = R.ripple_fv_step(f, prm, 1)
+        cells = np.random.default_rng(7).choice(ncell, 4096, replace=False)
+        par["headline"] = dict(Un=Un, cells=cells, gpu=R.ripple_field_download(f).reshape(5, -1)[:, cells].T,
+                               dt=st1["dt_last"], dx=[1.0 / N3] * 3)
     R.ripple_field_destroy(f)
     hbm_peak, peak_kind = load_peaks()
     achieved = BYTES_PER_CELL_UPDATE * ncell / (ms / args.steps / 1e3) / 1e9
@@ -251,6 +260,10 @@ def bench_gpu(args, rank, world, local):
     torch.cuda.synchronize()
     ms2 = e0.elapsed_time(e1)
     R.ripple_fv_step(f2, prm2, 0)
+    if "headline" in par:  # 100 steps from the initial state, for the oracle comparison
+        R.ripple_field_upload(f2, U2)
+        R.ripple_fv_step(f2, prm2, 100)
+        par["euler2d_fp64_128"] = dict(U0=U2, gpu=R.ripple_field_download(f2))
     R.ripple_field_destroy(f2)
 
     # ---- secondary: eikonal FIM solves ----
@@ -273,20 +286,22 @@ def bench_gpu(args, rank, world, local):
             eik[name] = {"solve_ms": dt * 1e3, "solved_cells_per_s": ncells / dt,
                          "godunov_updates_per_s": est["cell_updates"] / dt, "iterations": est["iterations"],
                          "tile_visits": est["tile_visits"], "sources": len(src)}
+            if "headline" in par:
+                par["eikonal_" + name] = dict(s=s, src=src, h=1.0 / edims[0], gpu=R.ripple_field_download(ft))
             R.ripple_field_destroy(fs)
             R.ripple_field_destroy(ft)
 
     R.ripple_ctx_destroy(ctx)
-    batched = None if args.skip_batched else bench_batched(R, torch, local)
+    batched = None if args.skip_batched else bench_batched(R, torch, local, keep=par if "headline" in par else None)
     serve = None if args.skip_serve else bench_serving(R, torch, local)
     value = world * args.steps * ncell / (ms_max / 1e3)
     return dict(value=value, ms_per_step=ms_max / args.steps, clocks=clocks, ms_aos=ms_aos / args.steps,
                 e2e_value=e2e_value, e2e_s=e2e_s, e2e_solves=e2e_solves, ms2=ms2, eik=eik,
                 achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result, batched=batched,
-                serve=serve)
+                serve=serve, parity_data=par)
 
 
-def bench_batched(R, torch, local, nsteps=100, count=512):
+def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
     """512 independent 2D Euler problems (sides log-uniform in [32, 512], FP32,
     sine density with per-instance amplitude, periodic Rusanov, 100 steps):
     one batched launch per global step (autotuned layout and tile shape, CUDA
@@ -314,6 +329,10 @@ def bench_batched(R, torch, local, nsteps=100, count=512):
         st0 = R.ripple_batch_get_stats(ctx)
         reqs, infos, t_batch = run_batch()
         st1 = R.ripple_batch_get_stats(ctx)
+        if keep is not None:  # four instances (the smallest, two middle, the largest) for the oracle
+            order = np.argsort(sides)
+            pick = [int(order[0]), int(order[count // 3]), int(order[2 * count // 3]), int(order[-1])]
+            keep["batched"] = [dict(U0=states[i], gpu=reqs[i]["output"], side=sides[i]) for i in pick]
         span = max(i["finish_s"] for i in infos) - min(i["start_s"] for i in infos)
         # per-instance launch loop over device-resident fields (no transfers timed)
         fields = []
@@ -349,6 +368,9 @@ def bench_batched(R, torch, local, nsteps=100, count=512):
         "batched_compute_span_s": span,
         "batched_value_compute_span": cells * nsteps / span,
         "launches": st1["launches"] - st0["launches"], "graph_replays": st1["graph_replays"] - st0["graph_replays"],
+        "roofline": {"bound": "hbm", "achieved": 32.0 * cells * nsteps / span / 1e9, "peak": load_peaks()[0],
+                     "unit": "GB/s", "frac": 32.0 * cells * nsteps / span / 1e9 / load_peaks()[0],
+                     "algorithmic_bytes_per_cell_update": 32, "timing": "compute span of the 100 global steps"},
         "per_instance_loop_value": cells * nsteps / t_loop, "per_instance_loop_seconds": t_loop,
         "per_instance_loop_launches": count * nsteps,
         "speedup_vs_loop": t_loop / t_batch,
@@ -471,6 +493,62 @@ def cpu_baseline_sample():
             "sample": f"one MUSCL-Hancock step of the 256^3 blast in FP64 ({dt:.1f} s)"}
 
 
+def rel_l1(a, b):
+    """Per-component relative L1 of a against b (component axis first), max over components."""
+    a = np.asarray(a, dtype=np.float64).reshape(np.shape(b)[0] if np.ndim(b) > 1 else 1, -1)
+    b = np.asarray(b, dtype=np.float64).reshape(a.shape)
+    return float((np.abs(a - b).sum(1) / np.abs(b).sum(1).clip(1e-300)).max())
+
+
+def oracle_legs(par):
+    """The FP64 oracle beside each GPU result of this run: its time on the host
+    cores (a reported baseline) and the GPU result's error against it."""
+    import oracle
+    oracle.build()
+    out = {}
+    if "headline" in par:
+        p = par["headline"]
+        t0 = time.perf_counter()
+        vals, dt = oracle.euler_step_cells(p["Un"].astype(np.float64), p["cells"], scheme=oracle.MUSCL_HANCOCK,
+                                           bc=oracle.TRANSMISSIVE, dx=p["dx"])
+        t = time.perf_counter() - t0
+        err = float((np.abs(p["gpu"] - vals).sum(0) / np.abs(vals).sum(0)).max())
+        out["euler3d_256"] = {"rel_l1_vs_oracle": err, "tolerance": 2e-5,
+                              "check": "one step from the GPU state after the timed steps, 4096 seeded cells",
+                              "dt_rel_diff": abs(dt - p["dt"]) / dt, "oracle_seconds": t}
+    if "euler2d_fp64_128" in par:
+        p = par["euler2d_fp64_128"]
+        t0 = time.perf_counter()
+        ref, _ = oracle.euler_run(p["U0"], 100)
+        t = time.perf_counter() - t0
+        out["euler2d_fp64_128"] = {"rel_l1_vs_oracle": rel_l1(p["gpu"], ref), "tolerance": 1e-12,
+                                   "check": "100 steps from the initial state",
+                                   "oracle_cell_updates_per_s": 128 * 128 * 100 / t, "oracle_seconds": t}
+    for name in ("2d_2048", "3d_192"):
+        key = "eikonal_" + name
+        if key in par:
+            p = par[key]
+            t0 = time.perf_counter()
+            T = oracle.eikonal_fmm(p["s"].astype(np.float64), p["h"], p["src"])
+            t = time.perf_counter() - t0
+            out[key] = {"rel_l1_vs_oracle": rel_l1(np.asarray(p["gpu"]).reshape(T.shape)[None], T[None]),
+                        "tolerance": 1e-4, "check": "whole grid against Fast Marching",
+                        "oracle_solved_cells_per_s": T.size / t, "oracle_seconds": t}
+    if "batched" in par:
+        errs, cells, t = [], 0, 0.0
+        for p in par["batched"]:
+            side = p["side"]
+            t0 = time.perf_counter()
+            ref, _ = oracle.euler_run(p["U0"].astype(np.float64), 100, dx=[1.0 / side] * 2)
+            t += time.perf_counter() - t0
+            errs.append(rel_l1(p["gpu"], ref))
+            cells += side * side
+        out["batched"] = {"rel_l1_vs_oracle": max(errs), "tolerance": 2e-5,
+                          "check": f"4 of the 512 problems (sides {[p['side'] for p in par['batched']]}), 100 steps",
+                          "oracle_cell_updates_per_s": cells * 100 / t, "oracle_seconds": t}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -547,8 +625,12 @@ def main():
             "clocks": r["clocks"]}))
         return
     cpu = None
+    parity = None
     if not args.skip_cpu_baseline and world == 1:
         cpu = cpu_baseline_sample()
+        legs = oracle_legs(r["parity_data"])
+        cpu["workloads"] = {k: {kk: v for kk, v in d.items() if kk.startswith("oracle")} for k, d in legs.items()}
+        parity = {k: {kk: v for kk, v in d.items() if not kk.startswith("oracle")} for k, d in legs.items()}
     state_bytes = ncell * 5 * 4
     line = {
         "metric": METRIC, "value": r["value"], "unit": METRIC, "n_gpus": world, "steps": args.steps,
@@ -566,6 +648,7 @@ def main():
                 "step": f"one {NSTEPS_SOLVE}-step solve: pinned host -> device, {NSTEPS_SOLVE} sweeps, device -> pinned host",
                 "solves": r["e2e_solves"], "seconds": r["e2e_s"]},
         "cpu_baseline": cpu,
+        "parity": parity,
         "aos": {"value": ncell / (r["ms_aos"] / 1e3), "ms_per_step": r["ms_aos"]},
         "euler2d_fp64_128": {"ms_per_100_steps": r["ms2"], "us_per_step": r["ms2"] * 10.0,
                              "cell_updates_per_s": 100 * 128 * 128 / (r["ms2"] / 1e3)},
