@@ -294,11 +294,12 @@ def bench_gpu(args, rank, world, local):
     R.ripple_ctx_destroy(ctx)
     batched = None if args.skip_batched else bench_batched(R, torch, local, keep=par if "headline" in par else None)
     serve = None if args.skip_serve else bench_serving(R, torch, local)
+    layout = None if args.skip_layout else bench_layout(R, torch, local)
     value = world * args.steps * ncell / (ms_max / 1e3)
     return dict(value=value, ms_per_step=ms_max / args.steps, clocks=clocks, ms_aos=ms_aos / args.steps,
                 e2e_value=e2e_value, e2e_s=e2e_s, e2e_solves=e2e_solves, ms2=ms2, eik=eik,
                 achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result, batched=batched,
-                serve=serve, parity_data=par)
+                serve=serve, layout=layout, parity_data=par)
 
 
 def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
@@ -380,6 +381,55 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
                      "ms_per_global_step": {f"{'SoA' if k[0] == R.RIPPLE_SOA else 'AoS'}/{['32x8', '8x32', '16x16'][k[1]]}": v
                                             for k, v in timings.items()}},
     }
+
+
+def bench_layout(R, torch, local, n_saxpy=1 << 30, n_particles=80_000_000, reps=10):
+    """Section 7.1 SAXPY (1 G elements) and Section 7.2 particle update (80 M
+    particles) in both layouts, read directly or staged through shared memory
+    by bulk copies; CUDA-event times on the library's stream, inputs far larger
+    than L2.  The paper's V100 times of the same sizes are quoted as context."""
+    ctx = R.ripple_ctx_create(local)
+    stream = torch.cuda.Stream(device=local)
+    R.ripple_set_stream(ctx, stream)
+    peak = load_peaks()[0]
+    out = {}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        st = R.ripple_ctx_sync(ctx)
+        return e0.elapsed_time(e1) / reps
+
+    try:
+        x = torch.rand(n_saxpy, device=f"cuda:{local}")
+        y = torch.rand(n_saxpy, device=f"cuda:{local}")
+        torch.cuda.synchronize()
+        ms = timed(lambda: R.ripple_saxpy(ctx, 1.0001, x, y))
+        gbs = 12.0 * n_saxpy / (ms / 1e3) / 1e9
+        out["saxpy"] = {"elements": n_saxpy, "ms": ms, "GB_s": gbs, "hbm_frac": gbs / peak,
+                        "bytes_per_element": 12, "paper_v100_ms_1e9": {"ripple": 15.048, "cublas": 14.556}}
+        del x, y
+        p = torch.rand(6 * n_particles, device=f"cuda:{local}")
+        torch.cuda.synchronize()
+        out["particle_update"] = {"particles": n_particles, "bytes_per_particle": 36,
+                                  "note": "AoS stores whole 24-byte records back (48 B moved per particle)",
+                                  "paper_v100_ms_80M": {"s": 6.7914, "c": 11.452, "ss": 9.3259, "cs": 16.3081}}
+        for name, layout, staged in (("soa", R.RIPPLE_SOA, False), ("aos", R.RIPPLE_AOS, False),
+                                     ("soa_staged", R.RIPPLE_SOA, True), ("aos_staged", R.RIPPLE_AOS, True)):
+            ms = timed(lambda: R.ripple_particle_update(ctx, p, 1e-3, layout=layout, staged=staged))
+            gbs = 36.0 * n_particles / (ms / 1e3) / 1e9
+            out["particle_update"][name] = {"ms": ms, "GB_s": gbs, "hbm_frac": gbs / peak}
+        del p
+    finally:
+        R.ripple_ctx_destroy(ctx)
+    return out
 
 
 def _serve_requests(R, reqs_spec):
@@ -560,6 +610,7 @@ def main():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-batched", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--skip-layout", action="store_true")
     ap.add_argument("--sweep-only", action="store_true",
                     help="time only the SoA sweep (a small case for profiling; not the headline line)")
     ap.add_argument("--sweep-dims", type=int, nargs=3, default=[N3, N3, N3], metavar=("NX", "NY", "NZ"))
@@ -655,6 +706,7 @@ def main():
         "eikonal": r["eik"],
         "batched": r["batched"],
         "serve": r["serve"],
+        "layout_microbench": r["layout"],
     }
     print(json.dumps(line))
 

@@ -308,6 +308,40 @@ RIPPLE_API ripple_status ripple_batch_autotune(ripple_ctx ctx, const int64_t* si
 /* ------------------------------------------------------------------------ */
 /* Conserved totals for callers that cannot allocate device memory.          */
 /* ------------------------------------------------------------------------ */
+/* Layout microbenchmarks (Section 7.1 SAXPY, Table saxpy; Section 7.2      */
+/* particle update, Table particle_update).  Streaming kernels that          */
+/* calibrate the HBM roofline and the cost of the two layouts of Section 4.2 */
+/* ("strided" = RIPPLE_SOA, "contiguous" = RIPPLE_AOS).                       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * y <- a * x + y over n FP32 elements (Section 7.1).  x and y are DEVICE
+ * pointers owned by the caller (4-byte aligned; when they share an alignment
+ * modulo 16 bytes the body runs on 16-byte vectors).  Each element is one
+ * fused multiply-add rounded once.  Asynchronous on the context's stream.
+ * RIPPLE_ERR_INVALID: NULL ctx, n < 0, NULL or misaligned pointers.
+ */
+RIPPLE_API ripple_status ripple_saxpy(ripple_ctx ctx, int64_t n, float a, const float* x, float* y);
+
+/*
+ * One explicit update of n particles (Section 7.2): for d = 0, 1, 2
+ *   x_d <- x_d + v_d * dt   (one fused multiply-add, rounded once).
+ * `particles` is a DEVICE array of 6n floats owned by the caller, in `layout`:
+ *   RIPPLE_AOS ("contiguous"): record r = (x0 x1 x2 v0 v1 v2) at [6r, 6r+6);
+ *   RIPPLE_SOA ("strided"):    component d at [d*n, d*n + n), d = x0, x1, x2,
+ *                              v0, v1, v2.
+ * staged = 0 reads and writes global memory directly; staged = 1 passes
+ * 2048-particle chunks through shared memory by asynchronous bulk copies (the
+ * paper's shared-memory variants), when the array is 16-byte aligned and n is
+ * a multiple of 4 (SoA) or 2 (AoS); otherwise the direct kernel runs.  Both
+ * give identical bits.  Asynchronous on the context's stream; a bounded wait
+ * that runs out is reported by the next ripple_ctx_sync as RIPPLE_ERR_TIMEOUT.
+ * RIPPLE_ERR_INVALID: NULL ctx, n < 0, NULL or misaligned pointer, bad layout.
+ */
+RIPPLE_API ripple_status ripple_particle_update(ripple_ctx ctx, int64_t n, float dt, float* particles,
+                                                ripple_layout layout, int staged);
+
+/* ------------------------------------------------------------------------ */
 
 /*
  * The paper has no counterpart to this entry point.

@@ -26,6 +26,9 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
       and the 4-neighbour graph-Dijkstra upper bound.
   godunov -- pinned through the same tests plus its 1-term/2-term/3-term
       closed forms.
+  saxpy / particle_update (numpy, FP64) -- pinned: exact results on
+      integer-valued inputs, the identities a = 0 and dt = 0, and the two
+      layouts of one particle set giving the same positions.
 """
 from __future__ import annotations
 
@@ -205,3 +208,30 @@ def threads_used() -> int:
 
 if __name__ == "__main__":  # pragma: no cover
     print(build(force="--force" in sys.argv))
+
+
+def saxpy(a, x, y):
+    """Section 7.1 (SAXPY): y + a x, in FP64.  FP32 operands make the product
+    exact, so rounding the result once to FP32 gives the fused multiply-add of
+    the same operands except when the FP64 sum itself rounded onto an FP32
+    rounding midpoint (at most one unit in the last FP32 place)."""
+    return np.asarray(y, dtype=np.float64) + np.float64(a) * np.asarray(x, dtype=np.float64)
+
+
+def particle_update(p, dt, layout):
+    """Section 7.2 (particle update in three dimensions): x_d + v_d dt for
+    d = 0, 1, 2 of n particles held as 6n numbers, in FP64.
+    layout "aos" ("contiguous"): record r = (x0 x1 x2 v0 v1 v2) at [6r, 6r+6);
+    layout "soa" ("strided"): component d at [d n, d n + n).
+    Returns the updated 6n array (velocities unchanged)."""
+    q = np.array(p, dtype=np.float64).reshape(-1)
+    n = q.size // 6
+    if layout == "aos":
+        r = q.reshape(n, 6)
+        for d in range(3):
+            r[:, d] = r[:, d] + r[:, 3 + d] * np.float64(dt)
+    else:
+        r = q.reshape(6, n)
+        for d in range(3):
+            r[d] = r[d] + r[3 + d] * np.float64(dt)
+    return q

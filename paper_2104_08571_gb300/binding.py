@@ -122,6 +122,8 @@ _SIGNATURES = {
     "ripple_eikonal_solve": [_VP, _VP, _I64P, ctypes.c_int, ctypes.POINTER(ripple_eik_params),
                              ctypes.POINTER(ripple_eik_stats)],
     "ripple_totals_noalloc": [_VP, ctypes.c_int, _I64P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _VP],
+    "ripple_saxpy": [_VP, ctypes.c_int64, ctypes.c_float, _VP, _VP],
+    "ripple_particle_update": [_VP, ctypes.c_int64, ctypes.c_float, _VP, ctypes.c_int, ctypes.c_int],
     "ripple_batch_configure": [_VP, ctypes.POINTER(ripple_batch_config)],
     "ripple_batch_submit": [_VP, ctypes.POINTER(ripple_request), ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)],
     "ripple_poll": [_VP, ctypes.c_uint64, ctypes.POINTER(ripple_ticket_info)],
@@ -347,6 +349,22 @@ def ripple_totals_noalloc(state, dims, ncomp, layout, dtype, totals_out, stream=
         handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     _check(load().ripple_totals_noalloc(_VP(state.data_ptr()), len(dims), d, int(ncomp), int(layout), int(dtype),
                                         _VP(totals_out.data_ptr()), handle), "ripple_totals_noalloc")
+
+
+def ripple_saxpy(ctx, a, x, y):
+    """y <- a x + y on CUDA float32 tensors x, y (same number of elements), on the context's stream."""
+    n = x.numel()
+    if y.numel() != n:
+        raise RippleError(RIPPLE_ERR_INVALID, "x and y differ in length")
+    _check(load().ripple_saxpy(ctx, n, float(a), _VP(x.data_ptr()), _VP(y.data_ptr())), "ripple_saxpy")
+
+
+def ripple_particle_update(ctx, particles, dt, layout=RIPPLE_SOA, staged=False):
+    """x_d <- x_d + v_d dt on a CUDA float32 tensor of 6n floats (AoS records or SoA runs)."""
+    if particles.numel() % 6:
+        raise RippleError(RIPPLE_ERR_INVALID, "particles must hold 6 floats per particle")
+    _check(load().ripple_particle_update(ctx, particles.numel() // 6, float(dt), _VP(particles.data_ptr()),
+                                         int(layout), int(bool(staged))), "ripple_particle_update")
 
 
 # ---------------------------------------------------------------------------

@@ -358,6 +358,8 @@ ripple_status ripple_ctx_sync(ripple_ctx ctx)
         ripple_status st = take_device_error(f);
         if (first == RIPPLE_OK) first = st;
     }
+    if (layout_bench_take_error(ctx->stream) && first == RIPPLE_OK)
+        first = fail(RIPPLE_ERR_TIMEOUT, "a bounded wait of a staged particle update ran out");
     return first;
 }
 

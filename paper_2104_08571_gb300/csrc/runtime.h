@@ -70,6 +70,8 @@ int sweep_occ_f64_3d(int layout, int scheme, int v);
 // Aux kernels (f32/f64 x 2D/3D), defined in aux.cu.
 cudaError_t launch_prep(int dtype, int dim, void* buf, FieldCtl* ctl, const FieldGeom& g, int bc, double gamma,
                         const double inv_dx[3], int slot, int grid, cudaStream_t s);
+// Read and clear the timeout flag of the staged layout microbenchmark kernels.
+unsigned layout_bench_take_error(cudaStream_t s);
 // Quiet NaN in every non-interior cell of a padded buffer (pad_fill_nan_kernel).
 cudaError_t launch_pad_nan(int dtype, void* buf, const FieldGeom& g, int grid, cudaStream_t s);
 cudaError_t launch_totals(int dtype, int ncomp, const void* buf, const FieldGeom& g, double* partials, int nblocks,

@@ -232,3 +232,33 @@ def test_blast_conserves_before_waves_reach_boundary(oracle_lib):
     assert np.all(np.abs(t1 - t0) / scale <= 1e-13)
     # 6 steps of dt <= 0.4 / (3 * c_max / dx) keep the fastest wave inside r < 0.45
     assert info["t"] * 2.0 < 0.25
+
+
+# ---------------------------------------------------------------------------
+# Layout microbenchmark oracles (Section 7.1 SAXPY, Section 7.2 particle update)
+# ---------------------------------------------------------------------------
+def test_saxpy_oracle_exact_on_integers_and_identities(oracle_lib):
+    oracle = oracle_lib
+    x = np.arange(-50, 50, dtype=np.float32)
+    y = np.arange(100, dtype=np.float32) * 3
+    assert np.array_equal(oracle.saxpy(2.0, x, y), 2.0 * np.arange(-50, 50) + 3.0 * np.arange(100))
+    assert np.array_equal(oracle.saxpy(0.0, x, y), y.astype(np.float64))
+    assert np.array_equal(oracle.saxpy(1.5, np.zeros(7), np.ones(7)), np.ones(7))
+
+
+def test_particle_oracle_closed_forms_and_layouts(oracle_lib):
+    oracle = oracle_lib
+    rng = np.random.default_rng(3)
+    n = 37
+    pos = rng.integers(-100, 100, size=(n, 3)).astype(np.float64)
+    vel = rng.integers(-8, 8, size=(n, 3)).astype(np.float64)
+    aos = np.concatenate([pos, vel], axis=1).reshape(-1)
+    soa = np.concatenate([pos.T, vel.T], axis=0).reshape(-1)
+    out_a = oracle.particle_update(aos, 0.25, "aos").reshape(n, 6)
+    out_s = oracle.particle_update(soa, 0.25, "soa").reshape(6, n)
+    # exact: integers plus quarter-integers
+    assert np.array_equal(out_a[:, :3], pos + 0.25 * vel)
+    assert np.array_equal(out_a[:, 3:], vel)
+    # the two layouts of one particle set give the same positions
+    assert np.array_equal(out_s[:3].T, out_a[:, :3])
+    assert np.array_equal(oracle.particle_update(aos, 0.0, "aos"), aos)
