@@ -46,6 +46,7 @@ _LIB_PATH = os.path.join(_BUILD, "libripple_oracle.so")
 
 RUSANOV1 = 0
 MUSCL_HANCOCK = 1
+FORCE_SPLIT = 2  # dimensionally split step with the FORCE flux (Listing euler_graph, Section 7.3)
 PERIODIC = 0
 TRANSMISSIVE = 1
 

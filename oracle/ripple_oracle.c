@@ -22,6 +22,9 @@
  *        start of the step;
  *      * second order: MUSCL-Hancock in conserved variables, component-wise
  *        minmod slopes, per-direction half-step predictor;
+ *      * the paper's own solver (Listing euler_graph) is also provided: a
+ *        dimensionally split step (x, then y, then z sweeps, padding refilled
+ *        before each) with the FORCE face flux of Section 7.3;
  *      * padding fills (Section 4.1 names "constant extrapolation"):
  *        periodic, or transmissive = every ghost layer copies the edge cell;
  *      * a non-positive (or NaN) density or pressure anywhere (cell,
@@ -47,6 +50,7 @@
 
 #define SCHEME_RUSANOV1 0
 #define SCHEME_MUSCL_HANCOCK 1
+#define SCHEME_FORCE_SPLIT 2
 #define BC_PERIODIC 0
 #define BC_TRANSMISSIVE 1
 
@@ -199,6 +203,37 @@ static int rusanov(int ndim, int d, const double* qL, const double* qR, double g
     physical_flux(ndim, d, qL, gamma, FL);
     physical_flux(ndim, d, qR, gamma, FR);
     for (int m = 0; m < ncomp; m++) F[m] = 0.5 * (FL[m] + FR[m]) - 0.5 * s * (qR[m] - qL[m]);
+    return 1;
+}
+
+/*
+ * FORCE face flux (Toro's first-order centred scheme, the face flux the paper
+ * uses in Section 7.3) for a time step dt over cells of width dx along axis d,
+ * with dtdx = dt/dx: the mean of the Lax-Friedrichs flux
+ *   F_LF = (F(qL) + F(qR))/2 - (qR - qL)/(2 dtdx)
+ * and the Richtmyer flux F_RI = F(q_RI) of the intermediate state
+ *   q_RI = (qL + qR)/2 - dtdx (F(qR) - F(qL))/2.
+ * Returns 0 if qL or qR is not admissible (q_RI is an intermediate of the
+ * formula and is not required to be).
+ */
+static int force_flux(int ndim, int d, const double* qL, const double* qR, double gamma, double dtdx,
+                      double* F)
+{
+    int ncomp = ndim + 2;
+    double rho, u[3], p;
+    primitives(ndim, qL, gamma, &rho, u, &p);
+    if (!admissible(rho, p)) return 0;
+    primitives(ndim, qR, gamma, &rho, u, &p);
+    if (!admissible(rho, p)) return 0;
+    double FL[MAXC], FR[MAXC], qRI[MAXC], FRI[MAXC];
+    physical_flux(ndim, d, qL, gamma, FL);
+    physical_flux(ndim, d, qR, gamma, FR);
+    for (int m = 0; m < ncomp; m++) qRI[m] = 0.5 * (qL[m] + qR[m]) - 0.5 * dtdx * (FR[m] - FL[m]);
+    physical_flux(ndim, d, qRI, gamma, FRI);
+    for (int m = 0; m < ncomp; m++) {
+        double flf = 0.5 * (FL[m] + FR[m]) - 0.5 * (qR[m] - qL[m]) / dtdx;
+        F[m] = 0.5 * (flf + FRI[m]);
+    }
     return 1;
 }
 
@@ -386,10 +421,79 @@ static int euler_step(const grid_t* g, double* U, double* Unew, int ncomp, doubl
     return status;
 }
 
+/*
+ * One dimensionally split step, the paper's Euler solver (Listing euler_graph:
+ * set_wavespeeds -> MaxReducer -> set_dt -> set_boundary -> update_state_x ->
+ * set_boundary -> update_state_y [-> set_boundary -> update_state_z] ->
+ * swap_in_out) with the FORCE face flux.  dt comes from the state at the start
+ * of the step (the same rule as the unsplit step); each sweep fills the
+ * padding of its input and applies the flux difference along its own axis:
+ *   U^(d+1)_i = U^(d)_i - (dt/dx_d) (F_{i+1/2} - F_{i-1/2}).
+ * Every updated cell must be admissible.  The result is written to Unew.
+ */
+static int euler_split_step(const grid_t* g, double* U, double* Unew, int ncomp, double gamma, double cfl,
+                            const double* dx, int bc, double* dt_out)
+{
+    double smax;
+    if (!max_wavespeed(g, U, ncomp, gamma, dx, &smax)) return ORACLE_NUMERIC;
+    double dt = cfl / smax;
+    if (dt_out) *dt_out = dt;
+    int64_t nmax = g->n[0];
+    if (g->n[1] > nmax) nmax = g->n[1];
+    if (g->n[2] > nmax) nmax = g->n[2];
+    double* line = (double*)malloc(sizeof(double) * (size_t)((nmax + 1) * ncomp));
+    if (!line) return ORACLE_OOM;
+    double* src = U;
+    double* dst = Unew;
+    int status = ORACLE_OK;
+    for (int d = 0; d < g->ndim && status == ORACLE_OK; d++) {
+        fill_padding(g, src, ncomp, bc);
+        memcpy(dst, src, sizeof(double) * (size_t)(g->ncell * ncomp));
+        int64_t c[3] = {0, 0, 0};
+        int64_t ext[3] = {g->n[0], g->n[1], g->n[2]};
+        ext[d] = 1;
+        for (int64_t b2 = 0; b2 < ext[2] && status == ORACLE_OK; b2++)
+            for (int64_t b1 = 0; b1 < ext[1] && status == ORACLE_OK; b1++)
+                for (int64_t b0 = 0; b0 < ext[0] && status == ORACLE_OK; b0++) {
+                    c[0] = b0;
+                    c[1] = b1;
+                    c[2] = b2;
+                    /* faces between cells f-1 and f for f = 0..n_d; slot f */
+                    for (int64_t f = 0; f <= g->n[d] && status == ORACLE_OK; f++) {
+                        double qL[MAXC], qR[MAXC];
+                        c[d] = f - 1;
+                        load_cell(g, src, ncomp, c, qL);
+                        c[d] = f;
+                        load_cell(g, src, ncomp, c, qR);
+                        if (!force_flux(ncomp - 2, d, qL, qR, gamma, dt / dx[d], line + f * ncomp))
+                            status = ORACLE_NUMERIC;
+                    }
+                    for (int64_t i = 0; i < g->n[d] && status == ORACLE_OK; i++) {
+                        c[d] = i;
+                        int64_t id = pidx(g, c);
+                        double q[MAXC], rho, u[3], p;
+                        for (int m = 0; m < ncomp; m++) {
+                            q[m] = src[m * g->ncell + id] -
+                                   dt / dx[d] * (line[(i + 1) * ncomp + m] - line[i * ncomp + m]);
+                            dst[m * g->ncell + id] = q[m];
+                        }
+                        primitives(ncomp - 2, q, gamma, &rho, u, &p);
+                        if (!admissible(rho, p)) status = ORACLE_NUMERIC;
+                    }
+                }
+        double* tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    if (status == ORACLE_OK && src != Unew) memcpy(Unew, src, sizeof(double) * (size_t)(g->ncell * ncomp));
+    free(line);
+    return status;
+}
+
 static int check_euler_args(int ndim, int ncomp, int scheme, int bc)
 {
     if (ndim < 2 || ndim > 3 || ncomp != ndim + 2) return 0;
-    if (scheme != SCHEME_RUSANOV1 && scheme != SCHEME_MUSCL_HANCOCK) return 0;
+    if (scheme != SCHEME_RUSANOV1 && scheme != SCHEME_MUSCL_HANCOCK && scheme != SCHEME_FORCE_SPLIT) return 0;
     if (bc != BC_PERIODIC && bc != BC_TRANSMISSIVE) return 0;
     return 1;
 }
@@ -406,7 +510,7 @@ int oracle_euler_run(int ndim, const int64_t* n, double* U, double gamma, double
     int ncomp = ndim + 2;
     if (!check_euler_args(ndim, ncomp, scheme, bc) || nsteps < 0) return ORACLE_INVALID;
     grid_t g;
-    int h = scheme == SCHEME_RUSANOV1 ? 1 : 2;
+    int h = scheme == SCHEME_MUSCL_HANCOCK ? 2 : 1;
     if (grid_init(&g, ndim, n, h) != ORACLE_OK) return ORACLE_INVALID;
     if (bc == BC_PERIODIC)
         for (int d = 0; d < ndim; d++)
@@ -424,7 +528,8 @@ int oracle_euler_run(int ndim, const int64_t* n, double* U, double gamma, double
     int status = ORACLE_OK;
     int64_t s = 0;
     for (; s < nsteps; s++) {
-        status = euler_step(&g, A, B, ncomp, gamma, cfl, dx, scheme, bc, &dt);
+        status = scheme == SCHEME_FORCE_SPLIT ? euler_split_step(&g, A, B, ncomp, gamma, cfl, dx, bc, &dt)
+                                              : euler_step(&g, A, B, ncomp, gamma, cfl, dx, scheme, bc, &dt);
         if (status != ORACLE_OK) break;
         t += dt;
         double* tmp = A; /* swap_in_out */
@@ -463,7 +568,8 @@ int oracle_euler_step_cells(int ndim, const int64_t* n, const double* U, double 
                             const int64_t* cells, double* out, double* dt_out)
 {
     int ncomp = ndim + 2;
-    if (!check_euler_args(ndim, ncomp, scheme, bc)) return ORACLE_INVALID;
+    /* a split step's value at a cell needs the whole first sweep: full runs only */
+    if (!check_euler_args(ndim, ncomp, scheme, bc) || scheme == SCHEME_FORCE_SPLIT) return ORACLE_INVALID;
     grid_t g;
     int h = scheme == SCHEME_RUSANOV1 ? 1 : 2;
     if (grid_init(&g, ndim, n, h) != ORACLE_OK) return ORACLE_INVALID;

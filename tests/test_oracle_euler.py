@@ -262,3 +262,97 @@ def test_particle_oracle_closed_forms_and_layouts(oracle_lib):
     # the two layouts of one particle set give the same positions
     assert np.array_equal(out_s[:3].T, out_a[:, :3])
     assert np.array_equal(oracle.particle_update(aos, 0.0, "aos"), aos)
+
+
+# ---------------------------------------------------------------------------
+# The paper's own solver: dimensionally split step with the FORCE flux
+# (Listing euler_graph, Section 7.3).  Scheme id 2.
+# ---------------------------------------------------------------------------
+FORCE = 2
+
+
+@pytest.mark.parametrize("ndim,dims", [(2, (12, 10)), (3, (8, 6, 5))])
+@pytest.mark.parametrize("bc", [0, 1])
+def test_force_split_uniform_state_bit_exact(oracle_lib, ndim, dims, bc):
+    vel = [0.7, -0.4, 0.25][:ndim]
+    U0 = inputs.uniform_state(dims, 1.3, vel, 0.9)
+    U, info = oracle_lib.euler_run(U0, 25, scheme=FORCE, bc=bc)
+    assert info["steps_done"] == 25
+    assert np.array_equal(U, U0)
+
+
+def test_force_split_periodic_conservation(oracle_lib):
+    U0 = inputs.euler2d_sine(64)
+    U, _ = oracle_lib.euler_run(U0, 100, scheme=FORCE, bc=0)
+    t0, t1 = _totals(U0), _totals(U)
+    scale = np.maximum(np.abs(t0), np.abs(U0).sum(axis=(1, 2)))
+    assert np.all(np.abs(t1 - t0) / scale <= 1e-13)
+    r = inputs.uniform(9, 5 * 10 * 9 * 8).reshape(5, 8, 9, 10)
+    U0 = inputs.conserved(1.0 + 0.3 * r[0], [0.3 * (r[1 + d] - 0.5) for d in range(3)], 1.0 + 0.3 * r[4])
+    U, _ = oracle_lib.euler_run(U0, 20, scheme=FORCE, bc=0)
+    t0, t1 = _totals(U0), _totals(U)
+    assert np.all(np.abs(t1 - t0) / np.abs(U0).sum(axis=(1, 2, 3)) <= 1e-13)
+
+
+def test_force_split_advection_invariants_and_order(oracle_lib):
+    """FORCE keeps u, v, p uniform on the advected sine density and converges at first order."""
+    U, _ = oracle_lib.euler_run(inputs.euler2d_sine(64), 60, scheme=FORCE, bc=0)
+    rho, (u, v), p = prim(U, 2)
+    assert np.max(np.abs(u - 1.0)) <= 1e-12 and np.max(np.abs(v - 0.5)) <= 1e-12
+    assert np.max(np.abs(p - 1.0)) <= 1e-12
+    errs = [_advection_error(oracle_lib, n, FORCE) for n in (32, 64, 128, 256)]
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(3)]
+    assert all(e1 < e0 for e0, e1 in zip(errs, errs[1:])), errs
+    assert 0.8 <= orders[-1] <= 1.2, orders
+
+
+def test_force_reduces_to_the_linear_lf_lw_average(oracle_lib):
+    """On a contact (uniform u and p) FORCE is linear in rho: its mass update is
+    the mean of the Lax-Friedrichs and Lax-Wendroff schemes at Courant number
+    nu, rho_i - nu/2 (rho_{i+1} - rho_{i-1}) + (1 + nu^2)/4 (rho_{i+1} - 2 rho_i + rho_{i-1})."""
+    n = 48
+    x = inputs.cell_centres(n)
+    rho1 = 1.0 + 0.3 * np.sin(2 * math.pi * x) + 0.1 * inputs.uniform(5, n)
+    rho = np.tile(rho1[None, :], (3, 1))                 # (ny=3, nx)
+    U0 = inputs.conserved(rho, [np.full_like(rho, 0.8), np.zeros_like(rho)], np.ones_like(rho))
+    dx = [1.0 / n, 2.0 ** 100]
+    U, info = oracle_lib.euler_run(U0, 1, scheme=FORCE, bc=0, dx=dx)
+    nu = 0.8 * info["dt_last"] * n
+    rp, rm = np.roll(rho1, -1), np.roll(rho1, 1)
+    expect = rho1 - 0.5 * nu * (rp - rm) + 0.25 * (1.0 + nu * nu) * (rp - 2.0 * rho1 + rm)
+    assert np.max(np.abs(U[0, 1] - expect)) <= 1e-13
+    assert 0.1 < nu < 1.0
+
+
+def test_force_split_sod_converges(oracle_lib):
+    res = [_sod_errors(oracle_lib, n, FORCE) for n in (100, 200, 400)]
+    for comp in range(3):
+        errs = [r[comp] for r in res]
+        assert errs[0] > errs[1] > errs[2], errs
+    o = [math.log2(res[1][c] / res[2][c]) for c in range(3)]
+    assert o[0] >= 0.45 and o[1] >= 0.6 and o[2] >= 0.6, o
+
+
+def test_force_split_axis_permutation_bit_exact(oracle_lib):
+    """A 1-D Sod problem along x, y (2D) and x, y, z (3D) gives the same bits:
+    the sweeps across a uniform direction change nothing, exactly."""
+    n, nt, steps = 64, 3, 30
+    profiles = []
+    for ndim in (2, 3):
+        for axis in range(ndim):
+            U0 = inputs.sod(ndim, n, axis=axis, ntrans=nt)
+            dx = [2.0 ** 100] * ndim
+            dx[axis] = 1.0 / n
+            U, _ = oracle_lib.euler_run(U0, steps, scheme=FORCE, bc=1, dx=dx)
+            sl = [1] * ndim
+            sl[ndim - 1 - axis] = slice(None)
+            profiles.append(np.stack([U[0][tuple(sl)], U[1 + axis][tuple(sl)], U[ndim + 1][tuple(sl)]]))
+    for prof in profiles[1:]:
+        assert np.array_equal(prof, profiles[0])
+
+
+def test_force_split_negative_pressure_is_reported(oracle_lib):
+    U0 = inputs.uniform_state((8, 8), 1.0, [0.0, 0.0], 1.0)
+    U0[3, 4, 4] = -1.0
+    _, info = oracle_lib.euler_run(U0, 3, scheme=FORCE, allow_numeric=True)
+    assert info["status"] == oracle_lib.NUMERIC and info["steps_done"] == 0
