@@ -295,11 +295,12 @@ def bench_gpu(args, rank, world, local):
     batched = None if args.skip_batched else bench_batched(R, torch, local, keep=par if "headline" in par else None)
     serve = None if args.skip_serve else bench_serving(R, torch, local)
     layout = None if args.skip_layout else bench_layout(R, torch, local)
+    force = bench_force_split(R, torch, local, par=par if "headline" in par else None)
     value = world * args.steps * ncell / (ms_max / 1e3)
     return dict(value=value, ms_per_step=ms_max / args.steps, clocks=clocks, ms_aos=ms_aos / args.steps,
                 e2e_value=e2e_value, e2e_s=e2e_s, e2e_solves=e2e_solves, ms2=ms2, eik=eik,
                 achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result, batched=batched,
-                serve=serve, layout=layout, parity_data=par)
+                serve=serve, layout=layout, force=force, parity_data=par)
 
 
 def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
@@ -381,6 +382,48 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
                      "ms_per_global_step": {f"{'SoA' if k[0] == R.RIPPLE_SOA else 'AoS'}/{['32x8', '8x32', '16x16'][k[1]]}": v
                                             for k, v in timings.items()}},
     }
+
+
+def bench_force_split(R, torch, local, par=None):
+    """The paper's own Euler solver (dimensionally split x then y sweeps, FORCE
+    face flux): 2D FP32 8192^2 periodic sine density (a Table flux size), and
+    the 2D FP64 128^2 workload.  One step = one sweep per axis."""
+    ctx = R.ripple_ctx_create(local)
+    R.use_torch_allocator(ctx, local)
+    stream = torch.cuda.Stream(device=local)
+    R.ripple_set_stream(ctx, stream)
+    out = {}
+    try:
+        for name, n, dtype, steps in (("fp32_8192", 8192, R.RIPPLE_F32, 20), ("fp64_128", 128, R.RIPPLE_F64, 100)):
+            npdt = np.float32 if dtype == R.RIPPLE_F32 else np.float64
+            U0 = inputs.euler2d_sine(n).astype(npdt)
+            f = R.ripple_field_create(ctx, (n, n), 4, R.RIPPLE_SOA, 1, dtype)
+            prm = R.make_fv_params([1.0 / n] * 2, scheme=R.RIPPLE_FORCE_SPLIT)
+            R.ripple_field_upload(f, U0)
+            R.ripple_fv_step(f, prm, 3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            R.ripple_fv_step(f, prm, steps, stats=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            R.ripple_fv_step(f, prm, 0)
+            es = 16 if dtype == R.RIPPLE_F32 else 32
+            gbs = 2 * 2 * es * n * n / (ms / 1e3) / 1e9  # two sweeps, each reads and writes the state
+            out[name] = {"cells": n * n, "ms_per_step": ms, "cell_updates_per_s": n * n / (ms / 1e3),
+                         "launches_per_step": 2, "GB_s_algorithmic": gbs, "hbm_frac": gbs / load_peaks()[0]}
+            if name == "fp32_8192":
+                out[name]["paper_v100_flux_difference_ms_8k"] = {"ripple_s": 3.5533, "ripple_c": 5.5284,
+                                                                   "kokkos": 12.919}
+            if name == "fp64_128" and par is not None:
+                R.ripple_field_upload(f, U0)
+                R.ripple_fv_step(f, prm, 100)
+                par["force_split_fp64_128"] = dict(U0=U0, gpu=R.ripple_field_download(f))
+            R.ripple_field_destroy(f)
+    finally:
+        R.ripple_ctx_destroy(ctx)
+    return out
 
 
 def bench_layout(R, torch, local, n_saxpy=1 << 30, n_particles=80_000_000, reps=10):
@@ -566,6 +609,14 @@ def oracle_legs(par):
         out["euler3d_256"] = {"rel_l1_vs_oracle": err, "tolerance": 2e-5,
                               "check": "one step from the GPU state after the timed steps, 4096 seeded cells",
                               "dt_rel_diff": abs(dt - p["dt"]) / dt, "oracle_seconds": t}
+    if "force_split_fp64_128" in par:
+        p = par["force_split_fp64_128"]
+        t0 = time.perf_counter()
+        ref, _ = oracle.euler_run(p["U0"], 100, scheme=oracle.FORCE_SPLIT)
+        t = time.perf_counter() - t0
+        out["force_split_fp64_128"] = {"rel_l1_vs_oracle": rel_l1(p["gpu"], ref), "tolerance": 1e-12,
+                                       "check": "100 split FORCE steps from the initial state",
+                                       "oracle_cell_updates_per_s": 128 * 128 * 100 / t, "oracle_seconds": t}
     if "euler2d_fp64_128" in par:
         p = par["euler2d_fp64_128"]
         t0 = time.perf_counter()
@@ -707,6 +758,7 @@ def main():
         "batched": r["batched"],
         "serve": r["serve"],
         "layout_microbench": r["layout"],
+        "force_split": r["force"],
     }
     print(json.dumps(line))
 

@@ -63,7 +63,7 @@ typedef enum {
 
 typedef enum { RIPPLE_AOS = 0, RIPPLE_SOA = 1 } ripple_layout;
 typedef enum { RIPPLE_F32 = 0, RIPPLE_F64 = 1 } ripple_dtype;
-typedef enum { RIPPLE_RUSANOV1 = 0, RIPPLE_MUSCL_HANCOCK_MINMOD = 1 } ripple_scheme;
+typedef enum { RIPPLE_RUSANOV1 = 0, RIPPLE_MUSCL_HANCOCK_MINMOD = 1, RIPPLE_FORCE_SPLIT = 2 } ripple_scheme;
 typedef enum { RIPPLE_BC_PERIODIC = 0, RIPPLE_BC_TRANSMISSIVE = 1 } ripple_bc;
 
 typedef struct ripple_ctx_s* ripple_ctx;
@@ -177,9 +177,14 @@ typedef struct {
  * Advance the Euler field U by `nsteps` explicit steps (Section 8, Listing
  * "euler_graph": wave speeds -> max reduction -> dt -> padding fill -> flux
  * difference update -> swap; the flux difference is that of Section 7.3).
- * The update is unsplit (all axes in one pass) with a Rusanov face flux,
- * first order or MUSCL-Hancock with minmod slopes.  U must have ncomp =
- * ndim + 2 and halo >= 1 (Rusanov) or >= 2 (MUSCL-Hancock).  For RIPPLE_F32
+ * RIPPLE_RUSANOV1 and RIPPLE_MUSCL_HANCOCK_MINMOD: the update is unsplit (all
+ * axes in one pass) with a Rusanov face flux, first order or MUSCL-Hancock
+ * with minmod slopes.  RIPPLE_FORCE_SPLIT is the paper's own solver: a
+ * dimensionally split step (update_state_x, then y, then z, each a sweep
+ * along one axis with the padding refilled in between) with the FORCE face
+ * flux of Section 7.3 (the mean of the Lax-Friedrichs and Richtmyer fluxes),
+ * dt from the state at the start of the step by the same rule.  U must have
+ * ncomp = ndim + 2 and halo >= 1 (Rusanov, FORCE) or >= 2 (MUSCL-Hancock).  For RIPPLE_F32
  * fields the stencil runs in FP32 while dt and the totals are reduced in
  * FP64; RIPPLE_F64 fields run fully in FP64.
  * With stats != NULL the call synchronises, fills *stats (totals of the final

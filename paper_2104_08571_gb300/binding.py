@@ -35,6 +35,7 @@ RIPPLE_F32 = 0
 RIPPLE_F64 = 1
 RIPPLE_RUSANOV1 = 0
 RIPPLE_MUSCL_HANCOCK_MINMOD = 1
+RIPPLE_FORCE_SPLIT = 2
 RIPPLE_BC_PERIODIC = 0
 RIPPLE_BC_TRANSMISSIVE = 1
 

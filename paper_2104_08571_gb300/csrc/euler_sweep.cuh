@@ -46,7 +46,7 @@
 
 namespace ripple {
 
-enum { SCHEME_RUSANOV1 = 0, SCHEME_MUSCL = 1 };
+enum { SCHEME_RUSANOV1 = 0, SCHEME_MUSCL = 1, SCHEME_FORCE = 2 };
 
 struct SweepGeom {
     FieldGeom f;
@@ -60,6 +60,8 @@ struct SweepParams {
     int bc;       // 0 periodic, 1 transmissive
     int slot_in;  // ring slot holding smax of the input state
     int first;    // first step of a call: t = dt instead of t += dt
+    int axis;     // -1: all axes (the unsplit step); 0/1/2: one sweep of a split step along that axis
+    int last;     // this launch completes the step: advance t, reduce the new wave speeds
 };
 
 // ---------------------------------------------------------------------------
@@ -140,6 +142,36 @@ __device__ __forceinline__ void rusanov(const T (&a)[DIM + 2], const T (&b)[DIM 
     for (int m = 0; m < DIM + 2; ++m) F[m] = T(0.5) * (Fa[m] + Fb[m]) - T(0.5) * s * (b[m] - a[m]);
 }
 
+// FORCE face flux along D (Toro's first-order centred scheme, the flux of
+// Section 7.3): the mean of the Lax-Friedrichs flux and the Richtmyer flux of
+// the intermediate state q = (a + b)/2 - (dt/dx)(F(b) - F(a))/2, for
+// dtdx = dt/dx_D and inv_dtdx = dx_D/dt.  The admissibility of a and b goes to
+// chk; q is an intermediate of the formula and is not checked.
+template <typename T, int DIM, int D>
+__device__ __forceinline__ void force_flux(const T (&a)[DIM + 2], const T (&b)[DIM + 2], T gm1, T dtdx, T inv_dtdx,
+                                           T (&F)[DIM + 2], T& chk, bool valid)
+{
+    T Fa[DIM + 2], Fb[DIM + 2], q[DIM + 2], Fq[DIM + 2], ia, ua, pa, ib, ub, pb, iq, uq, pq;
+    phys_flux<T, DIM, D>(a, gm1, Fa, ia, ua, pa);
+    phys_flux<T, DIM, D>(b, gm1, Fb, ib, ub, pb);
+    track_min(chk, valid, a[0], pa, b[0], pb);
+#pragma unroll
+    for (int m = 0; m < DIM + 2; ++m) q[m] = T(0.5) * (a[m] + b[m]) - T(0.5) * dtdx * (Fb[m] - Fa[m]);
+    phys_flux<T, DIM, D>(q, gm1, Fq, iq, uq, pq);
+#pragma unroll
+    for (int m = 0; m < DIM + 2; ++m)
+        F[m] = T(0.5) * (T(0.5) * (Fa[m] + Fb[m]) - T(0.5) * inv_dtdx * (b[m] - a[m]) + Fq[m]);
+}
+
+// First-order face flux of a scheme: Rusanov, or FORCE for the split step.
+template <int SCHEME, typename T, int DIM, int D>
+__device__ __forceinline__ void face_flux1(const T (&a)[DIM + 2], const T (&b)[DIM + 2], T gamma, T gm1, T dtdx,
+                                           T inv_dtdx, T (&F)[DIM + 2], T& chk, bool valid)
+{
+    if constexpr (SCHEME == SCHEME_FORCE) force_flux<T, DIM, D>(a, b, gm1, dtdx, inv_dtdx, F, chk, valid);
+    else rusanov<T, DIM, D>(a, b, gamma, gm1, F, chk, valid);
+}
+
 // MUSCL-Hancock face states of a cell along D from (left, centre, right):
 // slopes by minmod, boundary extrapolation, half-step predictor with the
 // direction-D flux difference (admissibility of the extrapolated states goes to chk).
@@ -166,6 +198,14 @@ __device__ __forceinline__ void muscl_states(const T (&qm)[DIM + 2], const T (&q
     }
 }
 
+// Separately rounded product and sum (never contracted into a fused
+// multiply-add): the wave-speed sum then does not depend on the order of the
+// axes, so a problem and its axis-permuted twin get the same dt.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
 // Wave-speed sum and admissibility of a conserved state.
 template <typename T, int DIM>
 __device__ __forceinline__ T wave_sum(const T (&q)[DIM + 2], T gamma, T gm1, const T (&inv_dx)[3], bool& ok)
@@ -179,7 +219,7 @@ __device__ __forceinline__ T wave_sum(const T (&q)[DIM + 2], T gamma, T gm1, con
     const T c = sqrt_t(gamma * p * inv_rho);
     T s = T(0);
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) s += (fabs(q[1 + d] * inv_rho) + c) * inv_dx[d];
+    for (int d = 0; d < DIM; ++d) s = add_rn(s, mul_rn(fabs(q[1 + d] * inv_rho) + c, inv_dx[d]));
     return s;
 }
 
@@ -292,7 +332,7 @@ struct SweepCfg {
     static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);  // faces
     static constexpr int P_BYTES = SCHEME == SCHEME_MUSCL ? ((2 * NC * (NPX + NPY) * ES + 127) / 128) * 128 : 0;
     static constexpr int F_BYTES = ((NC * (NFX + NFY) * ES + 127) / 128) * 128;
-    static constexpr int HDR_BYTES = 256;  // mbarriers + reduction scratch
+    static constexpr int HDR_BYTES = 384;  // mbarriers, reduction scratch, abort flag, step scalars
     static constexpr int SMEM = HDR_BYTES + NS * SLOT_BYTES + 2 * OUT_BYTES + P_BYTES + F_BYTES;
     static_assert(TX % A == 0, "tile width must keep TMA x coordinates 16-byte aligned");
     static_assert(BX * (LAYOUT == LAYOUT_AOS ? NC : 1) <= 256 && BY <= 256, "TMA box too large");
@@ -362,27 +402,28 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
     T* FX = Fs;           // [NC][NFX]
     T* FY = Fs + NC * C::NFX;  // [NC][NFY]
 
+    double* sdt = reinterpret_cast<double*>(smem + 256);  // step scalars formed by thread 0
+
     const int tid = threadIdx.x;
     const int lx = tid % TX, ly = tid / TX;
     const FieldGeom& g = sg.f;
 
-    // dt from the max wave-speed sum of the input state (FP64)
-    const double smax_in = __longlong_as_double((long long)ctl->smax[prm.slot_in]);
-    const double dt = prm.cfl / smax_in;
-    const T gamma = (T)prm.gamma, gm1 = (T)(prm.gamma - 1.0);
-    const T dtT = (T)dt;
-    T inv_dx[3], half_dtdx[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        inv_dx[d] = (T)prm.inv_dx[d];
-        half_dtdx[d] = (T)(0.5 * dt * prm.inv_dx[d]);
-    }
-    if (blockIdx.x == 0 && tid == 0) {
-        ctl->t = prm.first ? dt : ctl->t + dt;
-        ctl->dt_last = dt;
-        ctl->smax[(prm.slot_in + 2) % 3] = 0ull;  // slot the next step reduces into after this one
-    }
     if (tid == 0) {
+        // dt from the max wave-speed sum of the input state, in FP64 once per
+        // CTA (FP64 throughput is small on this part); every sweep of a split
+        // step reads the same ring slot and so uses the same dt
+        const double dt = prm.cfl / __longlong_as_double((long long)ctl->smax[prm.slot_in]);
+        sdt[0] = dt;
+        for (int d = 0; d < 3; ++d) {
+            sdt[1 + d] = 0.5 * dt * prm.inv_dx[d];
+            sdt[4 + d] = dt * prm.inv_dx[d];
+            sdt[7 + d] = prm.inv_dx[d] > 0.0 ? 1.0 / (dt * prm.inv_dx[d]) : 0.0;
+        }
+        if (blockIdx.x == 0 && prm.last) {
+            ctl->t = prm.first ? dt : ctl->t + dt;
+            ctl->dt_last = dt;
+            ctl->smax[(prm.slot_in + 2) % 3] = 0ull;  // slot the next step reduces into after this one
+        }
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
         flags[0] = 0;
         fence_mbar_init();
@@ -390,6 +431,20 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
         prefetch_tensormap(&map_out);
     }
     __syncthreads();
+    const T gamma = (T)prm.gamma, gm1 = (T)(prm.gamma - 1.0);
+    const T dtT = (T)sdt[0];
+    T inv_dx[3], half_dtdx[3], dtdx[3], inv_dtdx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        inv_dx[d] = (T)prm.inv_dx[d];
+        half_dtdx[d] = (T)sdt[1 + d];
+        dtdx[d] = (T)sdt[4 + d];
+        inv_dtdx[d] = (T)sdt[7 + d];
+    }
+    // axes whose faces this launch evaluates (all of them for the unsplit step)
+    const bool ax0 = prm.axis < 0 || prm.axis == 0;
+    const bool ax1 = prm.axis < 0 || prm.axis == 1;
+    const bool ax2 = DIM == 3 && (prm.axis < 0 || prm.axis == 2);
 
     // ---- plane sequence of this CTA: items strided over CTAs ----
     auto item_planes = [&](int item) -> int {
@@ -597,7 +652,9 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
             if (!MUSCL) {
                 load_q(plane_ptr(seq_base + 0), my_off, qa);  // z0 - 1
                 load_q(plane_ptr(seq_base + 1), my_off, qb);  // z0
-                rusanov<T, DIM, 2 % DIM>(qa, qb, gamma, gm1, Fzm, chk, col_valid);
+                if (ax2)
+                    face_flux1<SCHEME, T, DIM, 2 % DIM>(qa, qb, gamma, gm1, dtdx[2], inv_dtdx[2], Fzm, chk,
+                                                        col_valid);
 #pragma unroll
                 for (int m = 0; m < NC; ++m) qa[m] = qb[m];  // qa = column value of z0
             } else {
@@ -628,14 +685,16 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
             if (DIM == 3 && !MUSCL) {
                 T qc[NC];
                 load_q(plane_ptr(seq_base + jc + 1), my_off, qc);
-                rusanov<T, DIM, 2 % DIM>(qa, qc, gamma, gm1, Fzp, chk, col_valid);
+                if (ax2)
+                    face_flux1<SCHEME, T, DIM, 2 % DIM>(qa, qc, gamma, gm1, dtdx[2], inv_dtdx[2], Fzp, chk,
+                                                        col_valid);
 #pragma unroll
                 for (int m = 0; m < NC; ++m) qb[m] = qc[m];
             }
 #pragma unroll
             for (int k = 0; k < KF; ++k) {
                 const unsigned kind = (f_bits >> (2 * k)) & 3u;
-                if (kind == 0u) continue;
+                if (kind == 0u || (kind == 1u && !ax0) || (kind == 2u && !ax1)) continue;
                 const int it = tid + k * NT;
                 T a[NC], b[NC], F[NC];
                 if (MUSCL) {
@@ -650,8 +709,14 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
                     load_q(S, f_off[k] + (kind == 1u ? SX : SY), b);
                 }
                 const bool v = (f_bits >> (16 + k)) & 1u;
-                if (kind == 1u) rusanov<T, DIM, 0>(a, b, gamma, gm1, F, chk, v);
-                else rusanov<T, DIM, 1>(a, b, gamma, gm1, F, chk, v);
+                if (MUSCL) {
+                    if (kind == 1u) rusanov<T, DIM, 0>(a, b, gamma, gm1, F, chk, v);
+                    else rusanov<T, DIM, 1>(a, b, gamma, gm1, F, chk, v);
+                } else if (kind == 1u) {
+                    face_flux1<SCHEME, T, DIM, 0>(a, b, gamma, gm1, dtdx[0], inv_dtdx[0], F, chk, v);
+                } else {
+                    face_flux1<SCHEME, T, DIM, 1>(a, b, gamma, gm1, dtdx[1], inv_dtdx[1], F, chk, v);
+                }
                 if (kind == 1u) {
 #pragma unroll
                     for (int m = 0; m < NC; ++m) FX[m * C::NFX + it] = F[m];
@@ -679,9 +744,9 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
                     const T fxm = FX[m * C::NFX + ly * (TX + 1) + lx];
                     const T fyp = FY[m * C::NFY + (ly + 1) * TX + lx];
                     const T fym = FY[m * C::NFY + ly * TX + lx];
-                    T acc = (fxp - fxm) * inv_dx[0];
-                    acc += (fyp - fym) * inv_dx[1];
-                    if (DIM == 3) acc += (Fzp[m] - Fzm[m]) * inv_dx[2];
+                    T acc = ax0 ? (fxp - fxm) * inv_dx[0] : T(0);
+                    if (ax1) acc += (fyp - fym) * inv_dx[1];
+                    if (ax2) acc += (Fzp[m] - Fzm[m]) * inv_dx[2];
                     qn[m] = qc[m] - dtT * acc;
                     if (tma_store_ok) {
                         if (LAYOUT == LAYOUT_SOA) st[(m * TY + ly) * TX + lx] = qn[m];
@@ -758,7 +823,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
     if (tid == 0) {
         double m = 0.0;
         for (int w = 0; w < NT / 32; ++w) m = fmax(m, red[w]);
-        atomic_max_pos_double(&ctl->smax[(prm.slot_in + 1) % 3], m);
+        if (prm.last) atomic_max_pos_double(&ctl->smax[(prm.slot_in + 1) % 3], m);
         if (any_bad) atomicOr(&ctl->err, DEV_ERR_NUMERIC);
     }
 }

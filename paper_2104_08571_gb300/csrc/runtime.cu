@@ -527,7 +527,7 @@ ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t 
     if (!U || !p) return fail(RIPPLE_ERR_INVALID, "NULL argument");
     if (nsteps < 0) return fail(RIPPLE_ERR_INVALID, "nsteps < 0");
     if (U->ncomp != U->ndim + 2) return fail(RIPPLE_ERR_INVALID, "Euler fields need ncomp = ndim + 2");
-    if (p->scheme != RIPPLE_RUSANOV1 && p->scheme != RIPPLE_MUSCL_HANCOCK_MINMOD)
+    if (p->scheme != RIPPLE_RUSANOV1 && p->scheme != RIPPLE_MUSCL_HANCOCK_MINMOD && p->scheme != RIPPLE_FORCE_SPLIT)
         return fail(RIPPLE_ERR_INVALID, "bad scheme");
     if (p->bc != RIPPLE_BC_PERIODIC && p->bc != RIPPLE_BC_TRANSMISSIVE) return fail(RIPPLE_ERR_INVALID, "bad bc");
     const int R = p->scheme == RIPPLE_MUSCL_HANCOCK_MINMOD ? 2 : 1;
@@ -553,7 +553,10 @@ ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t 
     }
 
     const int layout = U->layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
-    const int scheme = p->scheme == RIPPLE_MUSCL_HANCOCK_MINMOD ? SCHEME_MUSCL : SCHEME_RUSANOV1;
+    const int scheme = p->scheme == RIPPLE_MUSCL_HANCOCK_MINMOD ? SCHEME_MUSCL
+                       : p->scheme == RIPPLE_FORCE_SPLIT    ? SCHEME_FORCE
+                                                            : SCHEME_RUSANOV1;
+    const bool split = scheme == SCHEME_FORCE;
     int v = U->variant;
     if (v < 0 || sweep_smem(U->dtype, U->ndim, layout, scheme, v) == 0) {
         // default: the packed pair kernel where it exists (FP32), else the first that fits
@@ -612,17 +615,24 @@ ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t 
     for (int d = 0; d < 3; ++d) L.prm.inv_dx[d] = inv_dx[d];
     L.prm.bc = (int)p->bc;
 
+    // one launch per step (unsplit), or one sweep per axis (split: x, then y, then z;
+    // each sweep writes the ghost images its successor reads; all read the same dt)
+    const int sweeps = split ? U->ndim : 1;
     for (int64_t n = 0; n < nsteps; ++n) {
-        const int in = U->cur, outb = 1 - U->cur;
-        L.map_in = field_map(U, in, 0, R, tx, ty, &st);
-        if (!L.map_in) return st;
-        L.map_out = field_map(U, outb, 1, R, tx, ty, &st);
-        if (!L.map_out) return st;
-        L.out = U->buf[outb];
-        L.prm.slot_in = (int)(U->steps_total % 3);
-        L.prm.first = n == 0;
-        RIPPLE_CUDA(sweep_launch(U->dtype, U->ndim, layout, scheme, v, L));
-        U->cur = outb;
+        for (int a = 0; a < sweeps; ++a) {
+            const int in = U->cur, outb = 1 - U->cur;
+            L.map_in = field_map(U, in, 0, R, tx, ty, &st);
+            if (!L.map_in) return st;
+            L.map_out = field_map(U, outb, 1, R, tx, ty, &st);
+            if (!L.map_out) return st;
+            L.out = U->buf[outb];
+            L.prm.slot_in = (int)(U->steps_total % 3);
+            L.prm.first = n == 0;
+            L.prm.axis = split ? a : -1;
+            L.prm.last = a == sweeps - 1;
+            RIPPLE_CUDA(sweep_launch(U->dtype, U->ndim, layout, scheme, v, L));
+            U->cur = outb;
+        }
         U->steps_total++;
     }
 

@@ -17,7 +17,8 @@ struct SweepKernel {
     static constexpr bool pair = V == kPairVariant;
     static constexpr int TX = kSweepVariants[V].tx;
     static constexpr int TY = kSweepVariants[V].ty;
-    static constexpr bool exists = !pair || std::is_same<T, float>::value;
+    // the pair kernel covers the unsplit FP32 schemes; FORCE (split step) runs one cell per item
+    static constexpr bool exists = !pair || (std::is_same<T, float>::value && SCHEME != SCHEME_FORCE);
     static constexpr int smem()
     {
         if constexpr (pair) return PairCfg<DIM, LAYOUT, SCHEME>::SMEM;
@@ -116,27 +117,33 @@ struct SweepDim {
     {
         if (layout == LAYOUT_SOA) {
             if (scheme == SCHEME_MUSCL) return SweepRow<T, DIM, LAYOUT_SOA, SCHEME_MUSCL>::template launch_v<0>(v, L);
+            if (scheme == SCHEME_FORCE) return SweepRow<T, DIM, LAYOUT_SOA, SCHEME_FORCE>::template launch_v<0>(v, L);
             return SweepRow<T, DIM, LAYOUT_SOA, SCHEME_RUSANOV1>::template launch_v<0>(v, L);
         }
         if (scheme == SCHEME_MUSCL) return SweepRow<T, DIM, LAYOUT_AOS, SCHEME_MUSCL>::template launch_v<0>(v, L);
+        if (scheme == SCHEME_FORCE) return SweepRow<T, DIM, LAYOUT_AOS, SCHEME_FORCE>::template launch_v<0>(v, L);
         return SweepRow<T, DIM, LAYOUT_AOS, SCHEME_RUSANOV1>::template launch_v<0>(v, L);
     }
     static int smem(int layout, int scheme, int v)
     {
         if (layout == LAYOUT_SOA) {
             if (scheme == SCHEME_MUSCL) return SweepRow<T, DIM, LAYOUT_SOA, SCHEME_MUSCL>::template smem_v<0>(v);
+            if (scheme == SCHEME_FORCE) return SweepRow<T, DIM, LAYOUT_SOA, SCHEME_FORCE>::template smem_v<0>(v);
             return SweepRow<T, DIM, LAYOUT_SOA, SCHEME_RUSANOV1>::template smem_v<0>(v);
         }
         if (scheme == SCHEME_MUSCL) return SweepRow<T, DIM, LAYOUT_AOS, SCHEME_MUSCL>::template smem_v<0>(v);
+        if (scheme == SCHEME_FORCE) return SweepRow<T, DIM, LAYOUT_AOS, SCHEME_FORCE>::template smem_v<0>(v);
         return SweepRow<T, DIM, LAYOUT_AOS, SCHEME_RUSANOV1>::template smem_v<0>(v);
     }
     static int occ(int layout, int scheme, int v)
     {
         if (layout == LAYOUT_SOA) {
             if (scheme == SCHEME_MUSCL) return SweepRow<T, DIM, LAYOUT_SOA, SCHEME_MUSCL>::template occ_v<0>(v);
+            if (scheme == SCHEME_FORCE) return SweepRow<T, DIM, LAYOUT_SOA, SCHEME_FORCE>::template occ_v<0>(v);
             return SweepRow<T, DIM, LAYOUT_SOA, SCHEME_RUSANOV1>::template occ_v<0>(v);
         }
         if (scheme == SCHEME_MUSCL) return SweepRow<T, DIM, LAYOUT_AOS, SCHEME_MUSCL>::template occ_v<0>(v);
+        if (scheme == SCHEME_FORCE) return SweepRow<T, DIM, LAYOUT_AOS, SCHEME_FORCE>::template occ_v<0>(v);
         return SweepRow<T, DIM, LAYOUT_AOS, SCHEME_RUSANOV1>::template occ_v<0>(v);
     }
 };
