@@ -316,7 +316,7 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
     try:
         cfg, timings = R.ripple_batch_autotune(ctx, sides)
         R.ripple_batch_configure(ctx, layout=cfg["layout"], tile_variant=cfg["tile_variant"],
-                                 steps_per_sync=nsteps, use_graphs=True)
+                                 steps_per_sync=nsteps, use_graphs=True, staging=cfg["staging"])
 
         def run_batch():
             reqs = [R.euler_request(U, nsteps, [1.0 / U.shape[2], 1.0 / U.shape[1]]) for U in states]
@@ -379,8 +379,10 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
         "max_rel_l1_vs_loop": worst,
         "autotune": {"layout": "SoA" if cfg["layout"] == R.RIPPLE_SOA else "AoS",
                      "tile": ["32x8", "8x32", "16x16"][cfg["tile_variant"]],
-                     "ms_per_global_step": {f"{'SoA' if k[0] == R.RIPPLE_SOA else 'AoS'}/{['32x8', '8x32', '16x16'][k[1]]}": v
-                                            for k, v in timings.items()}},
+                     "staging": ["tma", "direct"][cfg["staging"]],
+                     "ms_per_global_step": {
+                         f"{['tma', 'direct'][k[2]]}/{'SoA' if k[0] == R.RIPPLE_SOA else 'AoS'}/"
+                         f"{['32x8', '8x32', '16x16'][k[1]]}": v for k, v in timings.items()}},
     }
 
 

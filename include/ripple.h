@@ -270,6 +270,8 @@ typedef struct {
     int fim_iters_per_step;   /* eikonal FIM iterations run per Euler global step (1..64) */
     int64_t active_cells;     /* per-step cell budget of stepped Euler problems, chosen by least
                                  remaining work (0 = step every resident problem) */
+    int staging;              /* halo staging of the Euler step: 0 = TMA tile loads by a producer warp
+                                 into a shared-memory ring; 1 = direct loads by every thread */
 } ripple_batch_config;
 
 typedef struct {
@@ -280,8 +282,8 @@ typedef struct {
 } ripple_batch_stats;
 
 /* Set the batch configuration (defaults: SoA, 32x8, 16 steps per sync, graphs
- * on, F32, 4 FIM iterations per step, no cell budget).  Only while no request
- * is in flight. */
+ * on, F32, 4 FIM iterations per step, no cell budget, TMA staging).  Only
+ * while no request is in flight. */
 RIPPLE_API ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* cfg);
 
 /* Queue n requests; tickets_out[i] identifies request i.  Validates every
@@ -301,11 +303,13 @@ RIPPLE_API ripple_status ripple_wait(ripple_ctx ctx, uint64_t ticket, int64_t ti
 RIPPLE_API ripple_status ripple_batch_get_stats(ripple_ctx ctx, ripple_batch_stats* out);
 
 /*
- * Autotuner: time the batched step for each layout (SoA, AoS) and tile shape
- * on n sample Euler problems of the given square sides (dtype `dtype`), and
- * return the fastest in *chosen (other fields of *chosen are kept).
- * ms_per_step (nullable) receives 2 x 3 timings, SoA first.  Does not change
- * the context's configuration (pass *chosen to ripple_batch_configure).
+ * Autotuner: time the batched step for each halo staging (TMA, direct), layout
+ * (SoA, AoS) and tile shape on n sample Euler problems of the given square
+ * sides (dtype `dtype`), and return the fastest in *chosen (other fields of
+ * *chosen are kept).  ms_per_step (nullable) receives 2 x 2 x 3 timings,
+ * index (staging * 2 + layout_index) * 3 + tile_variant, SoA = layout index 0.
+ * Does not change the context's configuration (pass *chosen to
+ * ripple_batch_configure).
  */
 RIPPLE_API ripple_status ripple_batch_autotune(ripple_ctx ctx, const int64_t* sides, int n, ripple_dtype dtype,
                                                ripple_batch_config* chosen, double* ms_per_step);

@@ -95,7 +95,7 @@ class ripple_ticket_info(ctypes.Structure):
 class ripple_batch_config(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int), ("tile_variant", ctypes.c_int), ("steps_per_sync", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("dtype", ctypes.c_int), ("fim_iters_per_step", ctypes.c_int),
-                ("active_cells", ctypes.c_int64)]
+                ("active_cells", ctypes.c_int64), ("staging", ctypes.c_int)]
 
 
 class ripple_batch_stats(ctypes.Structure):
@@ -381,9 +381,9 @@ def _info_dict(info):
 
 
 def ripple_batch_configure(ctx, layout=RIPPLE_SOA, tile_variant=0, steps_per_sync=16, use_graphs=True,
-                           dtype=RIPPLE_F32, fim_iters_per_step=4, active_cells=0):
+                           dtype=RIPPLE_F32, fim_iters_per_step=4, active_cells=0, staging=0):
     cfg = ripple_batch_config(int(layout), int(tile_variant), int(steps_per_sync), int(bool(use_graphs)), int(dtype),
-                              int(fim_iters_per_step), int(active_cells))
+                              int(fim_iters_per_step), int(active_cells), int(staging))
     _check(load().ripple_batch_configure(ctx, ctypes.byref(cfg)), "ripple_batch_configure")
 
 
@@ -463,14 +463,15 @@ def ripple_batch_get_stats(ctx):
 def ripple_batch_autotune(ctx, sides, dtype=RIPPLE_F32):
     """Returns (chosen config dict, {(layout, variant): ms per global step})."""
     arr = (ctypes.c_int64 * len(sides))(*[int(x) for x in sides])
-    cfg = ripple_batch_config(RIPPLE_SOA, 0, 16, 1, int(dtype), 4, 0)
-    ms = (ctypes.c_double * 6)()
+    cfg = ripple_batch_config(RIPPLE_SOA, 0, 16, 1, int(dtype), 4, 0, 0)
+    ms = (ctypes.c_double * 12)()
     _check(load().ripple_batch_autotune(ctx, arr, len(sides), int(dtype), ctypes.byref(cfg), ms),
            "ripple_batch_autotune")
     timings = {}
-    for li, lay in enumerate((RIPPLE_SOA, RIPPLE_AOS)):
-        for v in range(3):
-            timings[(lay, v)] = ms[li * 3 + v]
+    for sg in range(2):
+        for li, lay in enumerate((RIPPLE_SOA, RIPPLE_AOS)):
+            for v in range(3):
+                timings[(lay, v, sg)] = ms[(sg * 2 + li) * 3 + v]
     return dict(layout=cfg.layout, tile_variant=cfg.tile_variant, steps_per_sync=cfg.steps_per_sync,
                 use_graphs=cfg.use_graphs, dtype=cfg.dtype, fim_iters_per_step=cfg.fim_iters_per_step,
-                active_cells=cfg.active_cells), timings
+                active_cells=cfg.active_cells, staging=cfg.staging), timings

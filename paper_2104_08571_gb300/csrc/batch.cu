@@ -36,54 +36,67 @@ struct BatchTileShape {
 constexpr int kNumBatchVariants = 3;
 constexpr BatchTileShape kBatchVariants[kNumBatchVariants] = {{32, 8}, {8, 32}, {16, 16}};
 
+// Halo staging of the batched Euler step (an autotuner dimension).
+constexpr int kBatchStagingTma = 0;     // producer warp + TMA ring (batch_euler_kernel)
+constexpr int kBatchStagingDirect = 1;  // every thread loads from global memory (batch_euler_direct_kernel)
+
 template <typename T, int LAYOUT, int V>
-static cudaError_t step_v(int grid, cudaStream_t s, const BatchEuler* e, const void* f, const int* table,
-                          BatchCtl* c, int kind)
+static cudaError_t step_v(int staging, int grid, cudaStream_t s, const BatchEuler* e, const void* f,
+                          const int* table, BatchCtl* c, int kind)
 {
     constexpr int TX = kBatchVariants[V].tx, TY = kBatchVariants[V].ty;
     using BC = BatchEulerCfg<T, LAYOUT, TX, TY>;
-    if (kind == 0)
-        batch_euler_kernel<T, LAYOUT, TX, TY><<<grid, BC::NTHREADS, BC::SMEM, s>>>(e, table, c);
-    else
+    if (kind != 0)
         batch_fim_kernel<T><<<grid, 256, 0, s>>>(static_cast<const BatchFim<T>*>(f), table, c);
+    else if (staging == kBatchStagingDirect)
+        batch_euler_direct_kernel<T, LAYOUT, TX, TY><<<grid, 256, 0, s>>>(e, table, c);
+    else
+        batch_euler_kernel<T, LAYOUT, TX, TY><<<grid, BC::NTHREADS, BC::SMEM, s>>>(e, table, c);
     return cudaGetLastError();
 }
-// CTAs per SM of the Euler step kernel (which also sets its dynamic shared
-// memory limit: called before any launch of the variant).
+// CTAs per SM of the Euler step kernel of a staging (which also sets the TMA
+// kernel's dynamic shared memory limit: called before any launch of it).
 template <typename T, int LAYOUT, int V>
-static int occ_v()
+static int occ_v(int staging)
 {
     constexpr int TX = kBatchVariants[V].tx, TY = kBatchVariants[V].ty;
+    int n = 0;
+    if (staging == kBatchStagingDirect) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_euler_direct_kernel<T, LAYOUT, TX, TY>, 256, 0);
+        return n;
+    }
     using BC = BatchEulerCfg<T, LAYOUT, TX, TY>;
     auto k = batch_euler_kernel<T, LAYOUT, TX, TY>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, BC::SMEM) != cudaSuccess) return 0;
-    int n = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, BC::NTHREADS, BC::SMEM);
     return n;
 }
 template <typename T, int LAYOUT>
-static cudaError_t step_l(int v, int grid, cudaStream_t s, const BatchEuler* e, const void* f, const int* t,
-                          BatchCtl* c, int kind)
+static cudaError_t step_l(int v, int staging, int grid, cudaStream_t s, const BatchEuler* e, const void* f,
+                          const int* t, BatchCtl* c, int kind)
 {
-    if (v == 1) return step_v<T, LAYOUT, 1>(grid, s, e, f, t, c, kind);
-    if (v == 2) return step_v<T, LAYOUT, 2>(grid, s, e, f, t, c, kind);
-    return step_v<T, LAYOUT, 0>(grid, s, e, f, t, c, kind);
+    if (v == 1) return step_v<T, LAYOUT, 1>(staging, grid, s, e, f, t, c, kind);
+    if (v == 2) return step_v<T, LAYOUT, 2>(staging, grid, s, e, f, t, c, kind);
+    return step_v<T, LAYOUT, 0>(staging, grid, s, e, f, t, c, kind);
 }
-static cudaError_t launch_batch_step(ripple_dtype dt, int layout, int v, int grid, cudaStream_t s,
+static cudaError_t launch_batch_step(ripple_dtype dt, int layout, int v, int staging, int grid, cudaStream_t s,
                                      const BatchEuler* e, const void* f, const int* t, BatchCtl* c, int kind)
 {
     if (dt == RIPPLE_F32)
-        return layout == LAYOUT_SOA ? step_l<float, LAYOUT_SOA>(v, grid, s, e, f, t, c, kind)
-                                    : step_l<float, LAYOUT_AOS>(v, grid, s, e, f, t, c, kind);
-    return layout == LAYOUT_SOA ? step_l<double, LAYOUT_SOA>(v, grid, s, e, f, t, c, kind)
-                                : step_l<double, LAYOUT_AOS>(v, grid, s, e, f, t, c, kind);
+        return layout == LAYOUT_SOA ? step_l<float, LAYOUT_SOA>(v, staging, grid, s, e, f, t, c, kind)
+                                    : step_l<float, LAYOUT_AOS>(v, staging, grid, s, e, f, t, c, kind);
+    return layout == LAYOUT_SOA ? step_l<double, LAYOUT_SOA>(v, staging, grid, s, e, f, t, c, kind)
+                                : step_l<double, LAYOUT_AOS>(v, staging, grid, s, e, f, t, c, kind);
 }
-static int batch_occupancy(ripple_dtype dt, int layout, int v)
+static int batch_occupancy(ripple_dtype dt, int layout, int v, int staging)
 {
     auto pick = [&](auto tag) -> int {
         using T = decltype(tag);
-        if (layout == LAYOUT_SOA) return v == 1 ? occ_v<T, LAYOUT_SOA, 1>() : v == 2 ? occ_v<T, LAYOUT_SOA, 2>() : occ_v<T, LAYOUT_SOA, 0>();
-        return v == 1 ? occ_v<T, LAYOUT_AOS, 1>() : v == 2 ? occ_v<T, LAYOUT_AOS, 2>() : occ_v<T, LAYOUT_AOS, 0>();
+        if (layout == LAYOUT_SOA)
+            return v == 1 ? occ_v<T, LAYOUT_SOA, 1>(staging) : v == 2 ? occ_v<T, LAYOUT_SOA, 2>(staging)
+                                                                     : occ_v<T, LAYOUT_SOA, 0>(staging);
+        return v == 1 ? occ_v<T, LAYOUT_AOS, 1>(staging) : v == 2 ? occ_v<T, LAYOUT_AOS, 2>(staging)
+                                                                 : occ_v<T, LAYOUT_AOS, 0>(staging);
     };
     return dt == RIPPLE_F32 ? pick(0.0f) : pick(0.0);
 }
@@ -153,7 +166,7 @@ struct BatchRuntime {
     std::deque<Inst*> pending;                      // guarded by mu
     std::unordered_map<uint64_t, Ticket> tickets;   // guarded by mu
     uint64_t next_ticket = 1;                       // guarded by mu
-    ripple_batch_config cfg{RIPPLE_SOA, 0, 16, 1, RIPPLE_F32, 4, 0};
+    ripple_batch_config cfg{RIPPLE_SOA, 0, 16, 1, RIPPLE_F32, 4, 0, 0};
     ripple_batch_stats stats{};                     // guarded by mu
     Clock::time_point epoch = Clock::now();
     // scheduler-thread state
@@ -185,7 +198,7 @@ struct BatchRuntime {
     long long gstep_f = 0;  // FIM iterations issued
     int grid = 0;
     std::map<int, cudaGraphExec_t> graphs;  // key: (steps << 2) | has_euler << 1 | has_fim
-    int graph_variant = -1, graph_layout = -1, graph_fim = -1;
+    int graph_variant = -1, graph_layout = -1, graph_fim = -1, graph_staging = -1;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - epoch).count(); }
 };
@@ -507,10 +520,12 @@ static ripple_status launch_steps(BatchRuntime* rt, int K)
     auto unit = [&]() -> cudaError_t {
         cudaError_t e = cudaSuccess;
         if (rt->has_e)
-            e = launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->grid, rt->compute, rt->d_euler,
+            e = launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->cfg.staging, rt->grid,
+                                  rt->compute, rt->d_euler,
                                   rt->d_fim, rt->d_table, rt->d_bctl, 0);
         for (int f = 0; f < F && rt->has_f && e == cudaSuccess; ++f)
-            e = launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->grid, rt->compute, rt->d_euler,
+            e = launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->cfg.staging, rt->grid,
+                                  rt->compute, rt->d_euler,
                                   rt->d_fim, rt->d_table, rt->d_bctl, 1);
         return e;
     };
@@ -521,11 +536,13 @@ static ripple_status launch_steps(BatchRuntime* rt, int K)
         rt->stats.launches += (int64_t)K * per_unit;
         return RIPPLE_OK;
     }
-    if (rt->graph_variant != rt->cfg.tile_variant || rt->graph_layout != layout || rt->graph_fim != F) {
+    if (rt->graph_variant != rt->cfg.tile_variant || rt->graph_layout != layout || rt->graph_fim != F ||
+        rt->graph_staging != rt->cfg.staging) {
         for (auto& g : rt->graphs) cudaGraphExecDestroy(g.second);
         rt->graphs.clear();
         rt->graph_variant = rt->cfg.tile_variant;
         rt->graph_layout = layout;
+        rt->graph_staging = rt->cfg.staging;
         rt->graph_fim = F;
     }
     // K as a sum of powers of two, each replayed from a captured graph
@@ -757,7 +774,7 @@ static ripple_status rt_start(BatchRuntime* rt)
     rt->free_slots.clear();
     for (int i = kSlots - 1; i >= 0; --i) rt->free_slots.push_back(i);
     const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
-    const int occ = std::max(1, batch_occupancy(rt->cfg.dtype, layout, rt->cfg.tile_variant));
+    const int occ = std::max(1, batch_occupancy(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->cfg.staging));
     rt->grid = occ * rt->ctx->sm_count;
     rt->gstep_e = 0;
     rt->gstep_f = 0;
@@ -778,8 +795,8 @@ static BatchRuntime* runtime_of(ripple_ctx ctx, bool create)
 }
 
 // ---------------------------------------------------------------------------
-// Autotuner: time each (layout, tile shape) candidate of the batched step on
-// sample Euler problems of the given sides and keep the fastest.
+// Autotuner: time each (halo staging, layout, tile shape) candidate of the
+// batched step on sample Euler problems of the given sides and keep the fastest.
 // ---------------------------------------------------------------------------
 static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, ripple_dtype dt, ripple_batch_config* best,
                               double* ms)
@@ -789,6 +806,7 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
     RIPPLE_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     double best_ms = 1e300;
     ripple_status status = RIPPLE_OK;
+    for (int sg = 0; sg < 2 && status == RIPPLE_OK; ++sg)
     for (int li = 0; li < 2 && status == RIPPLE_OK; ++li) {
         const ripple_layout lay = li == 0 ? RIPPLE_SOA : RIPPLE_AOS;
         for (int v = 0; v < kNumBatchVariants && status == RIPPLE_OK; ++v) {
@@ -861,17 +879,17 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
             cudaMemcpyAsync(d_t, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(d_c, &hb, sizeof(BatchCtl), cudaMemcpyHostToDevice, s);
             const int lay_i = lay == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
-            const int grid = std::max(1, batch_occupancy(dt, lay_i, v)) * ctx->sm_count;
+            const int grid = std::max(1, batch_occupancy(dt, lay_i, v, sg)) * ctx->sm_count;
             cudaEvent_t e0, e1;
             cudaEventCreate(&e0);
             cudaEventCreate(&e1);
             cudaError_t ce = cudaSuccess;
             for (int k = 0; k < 3 && ce == cudaSuccess; ++k)
-                ce = launch_batch_step(dt, lay_i, v, grid, s, d_e, nullptr, d_t, d_c, 0);
+                ce = launch_batch_step(dt, lay_i, v, sg, grid, s, d_e, nullptr, d_t, d_c, 0);
             cudaEventRecord(e0, s);
             const int reps = 6;
             for (int k = 0; k < reps && ce == cudaSuccess; ++k)
-                ce = launch_batch_step(dt, lay_i, v, grid, s, d_e, nullptr, d_t, d_c, 0);
+                ce = launch_batch_step(dt, lay_i, v, sg, grid, s, d_e, nullptr, d_t, d_c, 0);
             cudaEventRecord(e1, s);
             cudaStreamSynchronize(s);
             float el = 0.f;
@@ -881,11 +899,12 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
             cleanup();
             if (ce != cudaSuccess) return cuda_fail(ce, "autotune launch");
             const double t = el / reps;
-            if (ms) ms[li * kNumBatchVariants + v] = t;
+            if (ms) ms[(sg * 2 + li) * kNumBatchVariants + v] = t;
             if (t < best_ms) {
                 best_ms = t;
                 best->layout = lay;
                 best->tile_variant = v;
+                best->staging = sg;
             }
         }
     }
@@ -942,6 +961,8 @@ ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* 
     if (!ctx || !cfg) return fail(RIPPLE_ERR_INVALID, "NULL argument");
     if (cfg->layout != RIPPLE_AOS && cfg->layout != RIPPLE_SOA) return fail(RIPPLE_ERR_INVALID, "bad layout");
     if (cfg->tile_variant < 0 || cfg->tile_variant >= kNumBatchVariants) return fail(RIPPLE_ERR_INVALID, "bad tile variant");
+    if (cfg->staging != kBatchStagingTma && cfg->staging != kBatchStagingDirect)
+        return fail(RIPPLE_ERR_INVALID, "bad halo staging");
     if (cfg->steps_per_sync < 1) return fail(RIPPLE_ERR_INVALID, "steps_per_sync must be >= 1");
     if (cfg->fim_iters_per_step < 1 || cfg->fim_iters_per_step > 64)
         return fail(RIPPLE_ERR_INVALID, "fim_iters_per_step must be 1..64");
@@ -951,10 +972,11 @@ ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* 
     if (rt->started) {
         const bool idle = rt->stats.submitted == rt->stats.completed + rt->stats.failed;
         if (!idle) return fail(RIPPLE_ERR_INVALID, "configure only while no request is in flight");
-        if (cfg->dtype != rt->cfg.dtype || cfg->layout != rt->cfg.layout || cfg->tile_variant != rt->cfg.tile_variant) {
+        if (cfg->dtype != rt->cfg.dtype || cfg->layout != rt->cfg.layout || cfg->tile_variant != rt->cfg.tile_variant ||
+            cfg->staging != rt->cfg.staging) {
             // the kernel grid depends on the variant; the scheduler re-reads it
             const int layout = cfg->layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
-            rt->grid = std::max(1, batch_occupancy(cfg->dtype, layout, cfg->tile_variant)) * ctx->sm_count;
+            rt->grid = std::max(1, batch_occupancy(cfg->dtype, layout, cfg->tile_variant, cfg->staging)) * ctx->sm_count;
             if (cfg->dtype != rt->cfg.dtype) {
                 // descriptor arrays hold the element type: reallocate on next use
                 cudaFree(rt->d_fim);

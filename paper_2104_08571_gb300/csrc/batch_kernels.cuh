@@ -377,6 +377,146 @@ __device__ __forceinline__ void batch_fim_tile(FimSmem<T, 2>& sm, const BatchFim
     }
 }
 
+// The same batched Euler step with the other halo staging: every thread loads
+// its share of the tile plus one ghost layer straight from global memory
+// (coalesced along x, all loads of a thread issued before its shared-memory
+// stores), one tile at a time per CTA.  The autotuner picks between this and
+// the TMA pipeline above.
+template <typename T, int LAYOUT, int TX, int TY>
+__global__ void __launch_bounds__(256) batch_euler_direct_kernel(const BatchEuler* __restrict__ euler,
+                                                                 const int* __restrict__ table,
+                                                                 BatchCtl* __restrict__ bctl)
+{
+    constexpr int NC = 4, NT = TX * TY;
+    constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1);
+    constexpr int CELLS = (TX + 2) * (TY + 2);
+    constexpr int KL = (NC * CELLS + NT - 1) / NT;  // staged elements per thread
+    constexpr int NFXr = ((NFX + 31) / 32) * 32, NFYr = ((NFY + 31) / 32) * 32;
+    constexpr int KF = (NFXr + NFYr + NT - 1) / NT;
+    static_assert(NT == 256, "the batched step runs 256 threads");
+    __shared__ T S[NC][TY + 2][TX + 2];
+    __shared__ T FX[NC][NFX];
+    __shared__ T FY[NC][NFY];
+    __shared__ T sp[5];  // tile parameters: gamma, gm1, 1/dx, 1/dy, dt
+    const int tid = threadIdx.x;
+    const int lx = tid % TX, ly = tid / TX;
+    const unsigned long long gstep = __ldcg(&bctl->gstep[0]);
+    const int end = __ldcg(&bctl->ntiles_e);
+    for (int t = blockIdx.x; t < end; t += gridDim.x) {
+        const BatchEuler& d = euler[__ldg(&table[t]) >> 1];
+        const long long local = (long long)gstep - d.start_step;
+        if (local < 0 || local >= d.nsteps) continue;  // the same for every thread of the CTA
+        const FieldGeom g = d.g;
+        const int lt = t - d.tile_begin;
+        const int x0 = (lt % d.tiles_x) * TX, y0 = (lt / d.tiles_x) * TY;
+        const int rs = (int)(local % 3);
+        FieldCtl* ctl = d.ctl;
+        const T* __restrict__ in = static_cast<const T*>(d.buf[local & 1]);
+        T* __restrict__ out = static_cast<T*>(d.buf[(local & 1) ^ 1]);
+        T v[KL];
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+            const int e = tid + k * NT;
+            v[k] = T(0);
+            if (e < NC * CELLS) {
+                const int m = LAYOUT == LAYOUT_SOA ? e / CELLS : e % NC;
+                const int r = LAYOUT == LAYOUT_SOA ? e % CELLS : e / NC;
+                const int gx = x0 + r % (TX + 2) - 1, gy = y0 + r / (TX + 2) - 1;
+                if (gx <= g.n[0] && gy <= g.n[1]) v[k] = in[geom_elem(g, gx, gy, 0, m)];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KL; ++k) {
+            const int e = tid + k * NT;
+            if (e < NC * CELLS) {
+                const int m = LAYOUT == LAYOUT_SOA ? e / CELLS : e % NC;
+                const int r = LAYOUT == LAYOUT_SOA ? e % CELLS : e / NC;
+                S[m][r / (TX + 2)][r % (TX + 2)] = v[k];
+            }
+        }
+        if (tid == 0) {
+            const double dt = d.cfl / __longlong_as_double((long long)__ldcg(&ctl->smax[rs]));
+            sp[0] = (T)d.gamma;
+            sp[1] = (T)d.gm1;
+            sp[2] = (T)d.inv_dx0;
+            sp[3] = (T)d.inv_dx1;
+            sp[4] = (T)dt;
+            if (lt == 0) {
+                ctl->t = local == 0 ? dt : ctl->t + dt;
+                ctl->dt_last = dt;
+                ctl->smax[(rs + 2) % 3] = 0ull;
+            }
+        }
+        __syncthreads();
+        const T gamma = sp[0], gm1 = sp[1], dtT = sp[4];
+        const T inv_dx[3] = {sp[2], sp[3], T(0)};
+        T chk = T(1);
+#pragma unroll 1
+        for (int k = 0; k < KF; ++k) {
+            const int it = tid + k * NT;
+            T a[NC], b[NC], F[NC];
+            if (it < NFXr) {
+                if (it >= NFX) continue;
+                const int fx = it % (TX + 1), cy = it / (TX + 1);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    a[m] = S[m][cy + 1][fx];
+                    b[m] = S[m][cy + 1][fx + 1];
+                }
+                rusanov<T, 2, 0>(a, b, gamma, gm1, F, chk, (x0 + fx <= g.n[0]) && (y0 + cy < g.n[1]));
+#pragma unroll
+                for (int m = 0; m < NC; ++m) FX[m][it] = F[m];
+            } else {
+                const int kk = it - NFXr;
+                if (kk >= NFY) continue;
+                const int cx = kk % TX, fy = kk / TX;
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    a[m] = S[m][fy][cx + 1];
+                    b[m] = S[m][fy + 1][cx + 1];
+                }
+                rusanov<T, 2, 1>(a, b, gamma, gm1, F, chk, (x0 + cx < g.n[0]) && (y0 + fy <= g.n[1]));
+#pragma unroll
+                for (int m = 0; m < NC; ++m) FY[m][kk] = F[m];
+            }
+        }
+        __syncthreads();
+        const int gx = x0 + lx, gy = y0 + ly;
+        T smax = T(0);
+        bool bad = !(chk > T(0));
+        if ((gx < g.n[0]) & (gy < g.n[1])) {
+            T qn[NC];
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                T acc = (FX[m][ly * (TX + 1) + lx + 1] - FX[m][ly * (TX + 1) + lx]) * inv_dx[0];
+                acc += (FY[m][(ly + 1) * TX + lx] - FY[m][ly * TX + lx]) * inv_dx[1];
+                qn[m] = S[m][ly + 1][lx + 1] - dtT * acc;
+            }
+            const long long base = geom_cell(g, gx, gy, 0) * g.cell_stride;
+#pragma unroll
+            for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = qn[m];
+            bool ok;
+            smax = wave_sum<T, 2>(qn, gamma, gm1, inv_dx, ok);
+            bad |= !ok;
+            if (gx < g.h || gx >= g.n[0] - g.h || gy < g.h || gy >= g.n[1] - g.h)
+                write_ghost_images<T, 2>(out, g, d.bc, gx, gy, 0, qn);
+        }
+        T w = smax;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+        const bool wbad = __any_sync(0xffffffffu, bad);
+        if ((tid & 31) == 0) {
+            atomic_max_pos_double(&ctl->smax[(rs + 1) % 3], (double)w);
+            if (wbad) {
+                record_bad(ctl, BAD_STATE, x0, y0, 0);
+                atomicOr(&ctl->err, DEV_ERR_NUMERIC);
+            }
+        }
+        __syncthreads();  // the next tile overwrites S, FX, FY and sp
+    }
+    batch_finish_launch(bctl, 0);
+}
+
 // One FIM iteration of every resident eikonal problem.
 template <typename T>
 __global__ void __launch_bounds__(256) batch_fim_kernel(const BatchFim<T>* __restrict__ fim,

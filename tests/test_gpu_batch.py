@@ -111,15 +111,17 @@ def test_graphs_and_sync_interval_do_not_change_results(ctx):
     assert np.array_equal(reqs1[1]["output"], reqs2[1]["output"])
 
 
-def test_aos_layout_and_tile_variants(ctx):
+def test_aos_layout_tile_variants_and_staging(ctx):
     base = _euler(77, 61, 0.2, 21)
     _run(ctx, [base])
-    for layout in (R.RIPPLE_SOA, R.RIPPLE_AOS):
-        for v in range(3):
-            R.ripple_batch_configure(ctx, layout=layout, tile_variant=v)
-            r = R.euler_request(base["input"], 21, base["dx"])
-            _run(ctx, [r])
-            assert rel_l1(r["output"], base["output"]) <= 1e-6
+    for staging in (0, 1):
+        for layout in (R.RIPPLE_SOA, R.RIPPLE_AOS):
+            for v in range(3):
+                R.ripple_batch_configure(ctx, layout=layout, tile_variant=v, staging=staging)
+                r = R.euler_request(base["input"], 21, base["dx"])
+                _run(ctx, [r])
+                assert rel_l1(r["output"], base["output"]) <= 1e-6
+    R.ripple_batch_configure(ctx)
 
 
 def test_budget_admission_waits_for_memory():
@@ -194,5 +196,6 @@ def test_autotune_picks_a_candidate(ctx):
     sides = [s for s, _ in inputs.batch_problems(32, seed=2)]
     cfg, timings = R.ripple_batch_autotune(ctx, sides)
     assert cfg["layout"] in (R.RIPPLE_SOA, R.RIPPLE_AOS) and 0 <= cfg["tile_variant"] < 3
-    assert all(v > 0 for v in timings.values())
-    assert timings[(cfg["layout"], cfg["tile_variant"])] == min(timings.values())
+    assert cfg["staging"] in (0, 1)
+    assert len(timings) == 12 and all(v > 0 for v in timings.values())
+    assert timings[(cfg["layout"], cfg["tile_variant"], cfg["staging"])] == min(timings.values())
