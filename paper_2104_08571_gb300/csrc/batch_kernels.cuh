@@ -75,7 +75,7 @@ struct BatchEulerCfg {
     static constexpr int NCT = TX * TY;          // consumer threads: one cell each
     static constexpr int NTHREADS = NCT + 32;    // plus one producer warp
     static constexpr int HDRS = 16 * NS;         // after the 2 * NS mbarriers
-    static constexpr int SLOT_HDR = 64;          // per-slot tile parameters
+    static constexpr int SLOT_HDR = 192;         // per-slot tile parameters (BatchTileHdr)
     static constexpr int RING = ((HDRS + NS * SLOT_HDR + 127) / 128) * 128;
     static constexpr int FACES = RING + NS * C::SLOT_BYTES;
     static constexpr int SMEM = FACES + 2 * C::F_BYTES;
@@ -83,15 +83,18 @@ struct BatchEulerCfg {
     static_assert(RING % 128 == 0 && C::SLOT_BYTES % 128 == 0 && C::F_BYTES % 128 == 0, "TMA destinations");
 };
 
-// Parameters of a staged tile, written by the producer before the slot's
-// full barrier completes.  tile < 0 marks the end of the CTA's work.
+// Everything the consumers need about a staged tile, written by the producer
+// before the slot's full barrier completes (the consumers then read no
+// descriptor from global memory).  tile < 0 marks the end of the CTA's work.
 template <typename T>
 struct BatchTileHdr {
+    FieldGeom g;
+    T* out;          // output buffer of this step
+    FieldCtl* ctl;   // the instance's control block
     T gamma, gm1, inv_dx0, inv_dx1, dt;
-    int tile, x0, y0;
-    long long local;
+    int tile, x0, y0, bc, rs;  // rs: the instance's ring slot of this step's input
 };
-static_assert(sizeof(BatchTileHdr<double>) <= 64, "tile header fits the slot header");
+static_assert(sizeof(BatchTileHdr<double>) <= 192, "tile header fits the slot header");
 
 // The last CTA of a launch to finish advances the launch counter of its kind.
 __device__ __forceinline__ void batch_finish_launch(BatchCtl* bctl, int kind)
@@ -206,6 +209,9 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
                 const int rs = (int)(local % 3);
                 FieldCtl* ctl = d->ctl;
                 const double dt = d->cfl / __longlong_as_double((long long)__ldcg(&ctl->smax[rs]));
+                h->g = d->g;
+                h->out = static_cast<T*>(d->buf[(local & 1) ^ 1]);
+                h->ctl = ctl;
                 h->gamma = (T)d->gamma;
                 h->gm1 = (T)d->gm1;
                 h->inv_dx0 = (T)d->inv_dx0;
@@ -214,7 +220,8 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
                 h->tile = t;
                 h->x0 = x0;
                 h->y0 = y0;
-                h->local = local;
+                h->bc = d->bc;
+                h->rs = rs;
                 if (lt == 0) {
                     ctl->t = local == 0 ? dt : ctl->t + dt;
                     ctl->dt_last = dt;
@@ -244,12 +251,10 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
     for (unsigned seq = 0;; ++seq) {
         const unsigned s = seq % NS;
         const bool got = mbar_wait_bounded(&full[s], (seq / NS) & 1u);
-        Hdr h{};
-        if (got) h = *slot_hdr(s);
+        const Hdr& h = *slot_hdr(s);  // shared memory, valid until this warp releases the slot
         const bool stop = !got || h.tile < 0;  // taken by all consumers together at the barrier below
         timed_out |= !got;
-        const BatchEuler& d = euler[stop ? 0 : (__ldg(&table[h.tile]) >> 1)];  // entry 0 always exists
-        const FieldGeom g = d.g;
+        const FieldGeom& g = h.g;
         const int x0 = h.x0, y0 = h.y0;
         const T gamma = h.gamma, gm1 = h.gm1, dtT = h.dt;
         const T inv_dx[3] = {h.inv_dx0, h.inv_dx1, T(0)};
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
         T smax = T(0);
         bool bad = !(chk > T(0));
         if (valid) {
-            T* __restrict__ out = static_cast<T*>(d.buf[(h.local & 1) ^ 1]);
+            T* __restrict__ out = h.out;
             const int o = PV::idx(lx, ly, 0);
             T qn[NC];
 #pragma unroll
@@ -313,25 +318,24 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
             smax = wave_sum<T, 2>(qn, gamma, gm1, inv_dx, ok);
             bad |= !ok;
             if (gx < g.h || gx >= g.n[0] - g.h || gy < g.h || gy >= g.n[1] - g.h)
-                write_ghost_images<T, 2>(out, g, d.bc, gx, gy, 0, qn);
+                write_ghost_images<T, 2>(out, g, h.bc, gx, gy, 0, qn);
         }
-        // this thread's reads of the slot are done: the warp releases it
-        __syncwarp();
-        if ((tid & 31) == 0) mbar_arrive(&empty[s]);
         // warp max of the new wave-speed sums -> the instance's next ring slot
         T v = smax;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
         const bool wbad = __any_sync(0xffffffffu, bad);
         if ((tid & 31) == 0) {
-            FieldCtl* ctl = d.ctl;
-            const int rs = (int)(h.local % 3);
-            atomic_max_pos_double(&ctl->smax[(rs + 1) % 3], (double)v);
+            FieldCtl* ctl = h.ctl;
+            atomic_max_pos_double(&ctl->smax[(h.rs + 1) % 3], (double)v);
             if (wbad) {
                 record_bad(ctl, BAD_STATE, x0, y0, 0);
                 atomicOr(&ctl->err, DEV_ERR_NUMERIC);
             }
         }
+        // this warp's reads of the slot (tile and header) are done: release it
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[s]);
     }
     if (timed_out) atomicOr(&bctl->err, DEV_ERR_TIMEOUT);  // the runtime fails the resident set
     __syncwarp();
