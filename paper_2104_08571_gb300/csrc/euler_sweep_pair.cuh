@@ -84,25 +84,17 @@ __global__ void __launch_bounds__(256, 2)
     const int fth = tid - PC::NPT;          // phase-F item index base of non-pair threads
     const FieldGeom& g = sg.f;
 
-    const double smax_in = __longlong_as_double((long long)ctl->smax[prm.slot_in]);
-    const double dt = prm.cfl / smax_in;
-    const f2 gamma = splat<f2>((float)prm.gamma), gm1 = splat<f2>((float)(prm.gamma - 1.0));
-    const f2 dtv = splat<f2>((float)dt);
-    f2 inv_dx[3], half_dtdx[3];
-    float inv_dx_s[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        inv_dx_s[d] = (float)prm.inv_dx[d];
-        inv_dx[d] = splat<f2>(inv_dx_s[d]);
-        half_dtdx[d] = splat<f2>((float)(0.5 * dt * prm.inv_dx[d]));
-    }
-    const float gamma_s = (float)prm.gamma, gm1_s = (float)(prm.gamma - 1.0);
-    if (blockIdx.x == 0 && tid == 0) {
-        ctl->t = prm.first ? dt : ctl->t + dt;
-        ctl->dt_last = dt;
-        ctl->smax[(prm.slot_in + 2) % 3] = 0ull;
-    }
+    double* sdt = reinterpret_cast<double*>(smem + 256);  // step scalars formed by thread 0
     if (tid == 0) {
+        // dt from the max wave-speed sum of the input state, in FP64 once per CTA
+        const double dt = prm.cfl / __longlong_as_double((long long)ctl->smax[prm.slot_in]);
+        sdt[0] = dt;
+        for (int d = 0; d < 3; ++d) sdt[1 + d] = 0.5 * dt * prm.inv_dx[d];
+        if (blockIdx.x == 0) {
+            ctl->t = prm.first ? dt : ctl->t + dt;
+            ctl->dt_last = dt;
+            ctl->smax[(prm.slot_in + 2) % 3] = 0ull;
+        }
         for (int s = 0; s < NS; ++s) mbar_init(&bars[s], 1);
         flags[0] = 0;
         fence_mbar_init();
@@ -110,6 +102,14 @@ __global__ void __launch_bounds__(256, 2)
         prefetch_tensormap(&map_out);
     }
     __syncthreads();
+    const f2 gamma = splat<f2>((float)prm.gamma), gm1 = splat<f2>((float)(prm.gamma - 1.0));
+    const f2 dtv = splat<f2>((float)sdt[0]);
+    f2 inv_dx[3], half_dtdx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        inv_dx[d] = splat<f2>((float)prm.inv_dx[d]);
+        half_dtdx[d] = splat<f2>((float)sdt[1 + d]);
+    }
 
     auto item_planes = [&](int item) -> int {
         if (DIM == 2) return 1;
@@ -411,7 +411,9 @@ __global__ void __launch_bounds__(256, 2)
                     for (int m = 0; m < NC; ++m) Fzm[m] = Fzp[m];
                 }
                 fence_proxy_async_smem();
-                // epilogue per cell of the pair
+                // epilogue: wave-speed sums of both cells at once, then per cell
+                bool ok_l[2];
+                const f2 sw = wave_sum2<DIM>(qn, gamma, gm1, inv_dx, ok_l[0], ok_l[1]);
 #pragma unroll
                 for (int lane = 0; lane < 2; ++lane) {
                     const bool v = lane == 0 ? vx0 : vx1;
@@ -424,13 +426,11 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
                         for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = q1[m];
                     }
-                    bool ok;
-                    const float s = wave_sum<float, DIM>(q1, gamma_s, gm1_s, inv_dx_s, ok);
-                    if (!ok) {
+                    if (!ok_l[lane]) {
                         bad = true;
                         record_bad(ctl, BAD_CELL, gx + lane, gy, z);
                     }
-                    smax_local = fmaxf(smax_local, s);
+                    smax_local = fmaxf(smax_local, lane == 0 ? sw.x : sw.y);
                     if (near_xy || (DIM == 3 && (z < g.h || z >= g.n[2] - g.h)))
                         write_ghost_images<float, DIM>(out, g, prm.bc, gx + lane, gy, z, q1);
                 }

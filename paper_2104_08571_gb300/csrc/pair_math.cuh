@@ -130,6 +130,28 @@ __device__ __forceinline__ void pflux(const V (&q)[DIM + 2], V gm1, V (&F)[DIM +
     F[DIM + 1] = (q[DIM + 1] + p) * un;
 }
 
+// Wave-speed sums sum_d (|u_d| + c)/dx_d of a pair of conserved states and
+// their admissibility (density and pressure > 0) per lane.  Products and sums
+// are separate roundings (packed mul/add are never contracted), so the sum
+// does not depend on the order of the axes.
+template <int DIM>
+__device__ __forceinline__ f2 wave_sum2(const f2 (&q)[DIM + 2], f2 gamma, f2 gm1, const f2 (&inv_dx)[3], bool& ok0,
+                                        bool& ok1)
+{
+    const f2 inv_rho = rcp_v(q[0]);
+    f2 mm = q[1] * q[1];
+#pragma unroll
+    for (int e = 1; e < DIM; ++e) mm = fma_v(q[1 + e], q[1 + e], mm);
+    const f2 p = gm1 * fma_v(splat<f2>(-0.5f), mm * inv_rho, q[DIM + 1]);
+    ok0 = (q[0].x > 0.f) & (p.x > 0.f);
+    ok1 = (q[0].y > 0.f) & (p.y > 0.f);
+    const f2 c = sqrt_v(gamma * p * inv_rho);
+    f2 s = (abs_v(q[1] * inv_rho) + c) * inv_dx[0];
+#pragma unroll
+    for (int d = 1; d < DIM; ++d) s = s + (abs_v(q[1 + d] * inv_rho) + c) * inv_dx[d];
+    return s;
+}
+
 // Rusanov face flux along D between left states a and right states b;
 // the smallest density/pressure of both goes to chk.
 template <typename V, int DIM, int D>
