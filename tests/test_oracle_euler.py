@@ -110,13 +110,25 @@ def test_uniform_dt_closed_form(oracle_lib):
     assert dt == pytest.approx(0.4 / ((0.3 + c) * 16 + (0.6 + c) * 8), rel=1e-15)
 
 
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = {}
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            rows[line[0]] = [float(v) for v in line[1:]]
+    return rows
+
+
 def test_riemann_solver_textbook_star_state():
-    # Sod (1978) tube; textbook star state p* = 0.30313, u* = 0.92745
-    p, u = riemann_exact.star_state((1.0, 0.0, 1.0), (0.125, 0.0, 0.1))
-    assert abs(p - 0.30313) < 1e-5 and abs(u - 0.92745) < 1e-5
-    # Toro's 123 problem (two rarefactions): p* = 0.00189, u* = 0
+    # Sod (1978) tube and Toro's 123 problem: star states printed in the
+    # textbook (fixture tests/golden/riemann_star_states.txt, with its citation)
+    for name, (rl, ul, pl, rr, ur, pr, p_star, u_star) in _golden("riemann_star_states.txt").items():
+        p, u = riemann_exact.star_state((rl, ul, pl), (rr, ur, pr))
+        assert abs(p - p_star) < 1e-5 and abs(u - u_star) < 1e-5, name
     p, u = riemann_exact.star_state((1.0, -2.0, 0.4), (1.0, 2.0, 0.4))
-    assert abs(p - 0.00189) < 1e-5 and abs(u) < 1e-12
+    assert abs(u) < 1e-12  # symmetric data: u* = 0 exactly
 
 
 def _run_to_time(oracle_lib, U, t_target, **kw):
