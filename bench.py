@@ -283,9 +283,12 @@ def bench_gpu(args, rank, world, local):
                 est = R.ripple_eikonal_solve(fs, ft, src, 1.0 / edims[0], 1e-6)
             dt = (time.perf_counter() - t0) / reps
             ncells = int(np.prod(edims))
+            hbm = 8.0 * ncells / dt / 1e9  # algorithmic: read s, write T once per solve
             eik[name] = {"solve_ms": dt * 1e3, "solved_cells_per_s": ncells / dt,
                          "godunov_updates_per_s": est["cell_updates"] / dt, "iterations": est["iterations"],
-                         "tile_visits": est["tile_visits"], "sources": len(src)}
+                         "tile_visits": est["tile_visits"], "sources": len(src),
+                         "hbm_GB_s_algorithmic": hbm, "hbm_frac": hbm / load_peaks()[0],
+                         "bound": "latency of the active-list iterations (the front crosses the grid)"}
             if "headline" in par:
                 par["eikonal_" + name] = dict(s=s, src=src, h=1.0 / edims[0], gpu=R.ripple_field_download(ft))
             R.ripple_field_destroy(fs)

@@ -207,6 +207,8 @@ static size_t fim_elem_size(ripple_dtype d) { return d == RIPPLE_F64 ? sizeof(Ba
 
 static ripple_status rt_alloc(BatchRuntime* rt, size_t bytes, void** p)
 {
+    *p = nullptr;
+    if (fault_injected("alloc")) return fail(RIPPLE_ERR_OOM, "device allocation failed (injected: RIPPLE_FAULT=alloc)");
     bytes = (bytes + 255) / 256 * 256;
     if (!budget_reserve(rt->ctx, bytes)) return RIPPLE_ERR_BUDGET;
     cudaError_t e = cudaMallocAsync(p, bytes, rt->copy);
@@ -324,6 +326,7 @@ static ripple_status admit(BatchRuntime* rt, Inst* in)
                           (in->scratch_bytes + 255) / 256 * 256;
     }
     if (dense > in->buf_bytes) return fail(RIPPLE_ERR_INTERNAL, "staging buffer too small");
+    if (fault_injected("admit")) return fail(RIPPLE_ERR_OOM, "admission failed (injected: RIPPLE_FAULT=admit)");
     if (rt->free_slots.empty()) return RIPPLE_ERR_BUDGET;
     if (rt->ctx->budget && in->total_bytes > rt->ctx->budget)
         return fail(RIPPLE_ERR_BUDGET, "request larger than the whole memory budget");
@@ -343,6 +346,7 @@ static ripple_status admit(BatchRuntime* rt, Inst* in)
     }
     in->slot = rt->free_slots.back();
     rt->free_slots.pop_back();
+    if (fault_injected("upload")) return fail(RIPPLE_ERR_CUDA, "input upload failed (injected: RIPPLE_FAULT=upload)");
     cudaStream_t s = rt->copy;
     const long long total = dims[0] * dims[1];
     const int grid = (int)std::min<long long>((total + 255) / 256, 4LL * rt->ctx->sm_count);

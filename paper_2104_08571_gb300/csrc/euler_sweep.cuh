@@ -40,6 +40,7 @@
 #pragma once
 #include <cuda.h>
 #include <cstdint>
+#include <type_traits>
 
 #include "field.cuh"
 #include "tma.cuh"
@@ -93,6 +94,23 @@ __device__ __forceinline__ T minmod_t(T a, T b)
     return fabs(a) < fabs(b) ? a : b;
 }
 
+// Physical flux along axis D from the state and its 1/rho; also returns the
+// normal velocity and the pressure.
+template <typename T, int DIM, int D>
+__device__ __forceinline__ void phys_flux_ir(const T (&q)[DIM + 2], T inv_rho, T gm1, T (&F)[DIM + 2], T& un, T& p)
+{
+    T mm = q[1] * q[1];
+#pragma unroll
+    for (int e = 1; e < DIM; ++e) mm = fma(q[1 + e], q[1 + e], mm);
+    p = gm1 * (q[DIM + 1] - T(0.5) * mm * inv_rho);
+    un = q[1 + D] * inv_rho;
+    F[0] = q[1 + D];
+#pragma unroll
+    for (int e = 0; e < DIM; ++e) F[1 + e] = q[1 + e] * un;
+    F[1 + D] += p;
+    F[DIM + 1] = (q[DIM + 1] + p) * un;
+}
+
 // Physical flux along axis D; also returns 1/rho, the normal velocity and the pressure.
 template <typename T, int DIM, int D>
 __device__ __forceinline__ void phys_flux(const T (&q)[DIM + 2], T gm1, T (&F)[DIM + 2], T& inv_rho, T& un, T& p)
@@ -137,6 +155,22 @@ __device__ __forceinline__ void rusanov(const T (&a)[DIM + 2], const T (&b)[DIM 
     track_min(chk, valid, a[0], pa, b[0], pb);
     const T ca = sqrt_t(gamma * pa * ia);
     const T cb = sqrt_t(gamma * pb * ib);
+    const T s = fmax(fabs(ua) + ca, fabs(ub) + cb);
+#pragma unroll
+    for (int m = 0; m < DIM + 2; ++m) F[m] = T(0.5) * (Fa[m] + Fb[m]) - T(0.5) * s * (b[m] - a[m]);
+}
+
+// Rusanov face flux from states whose 1/rho and sound speed were formed once
+// per cell beforehand (the FP64 path, where division and square root are
+// the costly operations): the same flux as rusanov().
+template <typename T, int DIM, int D>
+__device__ __forceinline__ void rusanov_pre(const T (&a)[DIM + 2], const T (&b)[DIM + 2], T ia, T ib, T ca, T cb,
+                                            T gm1, T (&F)[DIM + 2], T& chk, bool valid)
+{
+    T Fa[DIM + 2], Fb[DIM + 2], ua, pa, ub, pb;
+    phys_flux_ir<T, DIM, D>(a, ia, gm1, Fa, ua, pa);
+    phys_flux_ir<T, DIM, D>(b, ib, gm1, Fb, ub, pb);
+    track_min(chk, valid, a[0], pa, b[0], pb);
     const T s = fmax(fabs(ua) + ca, fabs(ub) + cb);
 #pragma unroll
     for (int m = 0; m < DIM + 2; ++m) F[m] = T(0.5) * (Fa[m] + Fb[m]) - T(0.5) * s * (b[m] - a[m]);
@@ -333,7 +367,11 @@ struct SweepCfg {
     static constexpr int P_BYTES = SCHEME == SCHEME_MUSCL ? ((2 * NC * (NPX + NPY) * ES + 127) / 128) * 128 : 0;
     static constexpr int F_BYTES = ((NC * (NFX + NFY) * ES + 127) / 128) * 128;
     static constexpr int HDR_BYTES = 384;  // mbarriers, reduction scratch, abort flag, step scalars
-    static constexpr int SMEM = HDR_BYTES + NS * SLOT_BYTES + 2 * OUT_BYTES + P_BYTES + F_BYTES;
+    // FP64 first-order 2D: 1/rho and the sound speed of every staged cell are
+    // formed once per tile (division and square root are costly in FP64)
+    static constexpr bool PRIM = std::is_same<T, double>::value && SCHEME == SCHEME_RUSANOV1 && DIM == 2;
+    static constexpr int Q_BYTES = PRIM ? ((2 * BX * BY * ES + 127) / 128) * 128 : 0;
+    static constexpr int SMEM = HDR_BYTES + NS * SLOT_BYTES + 2 * OUT_BYTES + P_BYTES + F_BYTES + Q_BYTES;
     static_assert(TX % A == 0, "tile width must keep TMA x coordinates 16-byte aligned");
     static_assert(BX * (LAYOUT == LAYOUT_AOS ? NC : 1) <= 256 && BY <= 256, "TMA box too large");
     static_assert(TX * (LAYOUT == LAYOUT_AOS ? NC : 1) <= 256, "TMA store box too large");
@@ -401,6 +439,9 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
     T* PR = P + NC * NP;  // [NC][NPX + NPY]
     T* FX = Fs;           // [NC][NFX]
     T* FY = Fs + NC * C::NFX;  // [NC][NFY]
+    T* QI = reinterpret_cast<T*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * C::OUT_BYTES + C::P_BYTES +
+                                 C::F_BYTES);  // [BX * BY] 1/rho of each staged cell (PRIM only)
+    T* QC = QI + C::BX * C::BY;                // [BX * BY] sound speed of each staged cell (PRIM only)
 
     double* sdt = reinterpret_cast<double*>(smem + 256);  // step scalars formed by thread 0
 
@@ -680,6 +721,23 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
             if (flags[0]) { aborted = true; break; }
             producer_step(seq_base + jc);
             const T* S = plane_ptr(seq_base + jc);
+            if constexpr (C::PRIM) {
+                // 1/rho and c of every staged cell (padding and beyond-domain cells
+                // give values no face in the domain reads)
+                for (int c = tid; c < C::BX * C::BY; c += NT) {
+                    T q[NC];
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) q[m] = S[(LAYOUT == LAYOUT_SOA ? c : c * NC) + m * SM];
+                    const T ir = rcp_t(q[0]);
+                    T mm = q[1] * q[1];
+#pragma unroll
+                    for (int e = 1; e < DIM; ++e) mm = fma(q[1 + e], q[1 + e], mm);
+                    const T p = gm1 * (q[DIM + 1] - T(0.5) * mm * ir);
+                    QI[c] = ir;
+                    QC[c] = sqrt_t(gamma * p * ir);
+                }
+                __syncthreads();
+            }
 
             // ---------------- phase F: face fluxes ----------------
             if (DIM == 3 && !MUSCL) {
@@ -709,7 +767,12 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 ? 2 : 4))
                     load_q(S, f_off[k] + (kind == 1u ? SX : SY), b);
                 }
                 const bool v = (f_bits >> (16 + k)) & 1u;
-                if (MUSCL) {
+                if constexpr (C::PRIM) {
+                    const int ca = LAYOUT == LAYOUT_SOA ? f_off[k] : f_off[k] / NC;
+                    const int cb = ca + (kind == 1u ? 1 : C::BX);
+                    if (kind == 1u) rusanov_pre<T, DIM, 0>(a, b, QI[ca], QI[cb], QC[ca], QC[cb], gm1, F, chk, v);
+                    else rusanov_pre<T, DIM, 1>(a, b, QI[ca], QI[cb], QC[ca], QC[cb], gm1, F, chk, v);
+                } else if (MUSCL) {
                     if (kind == 1u) rusanov<T, DIM, 0>(a, b, gamma, gm1, F, chk, v);
                     else rusanov<T, DIM, 1>(a, b, gamma, gm1, F, chk, v);
                 } else if (kind == 1u) {

@@ -4,6 +4,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -66,9 +67,25 @@ FieldGeom make_field_geom(int ndim, const int64_t* dims, int ncomp, ripple_layou
     return g;
 }
 
+bool fault_injected(const char* step)
+{
+    const char* env = std::getenv("RIPPLE_FAULT");
+    if (!env || !*env) return false;
+    const size_t n = std::strlen(step);
+    for (const char* p = env; *p;) {
+        const char* e = std::strchr(p, ',');
+        const size_t len = e ? (size_t)(e - p) : std::strlen(p);
+        if (len == n && std::strncmp(p, step, n) == 0) return true;
+        if (!e) break;
+        p = e + 1;
+    }
+    return false;
+}
+
 ripple_status ctx_alloc(ripple_ctx ctx, size_t bytes, void** out)
 {
     *out = nullptr;
+    if (fault_injected("alloc")) return fail(RIPPLE_ERR_OOM, "device allocation failed (injected: RIPPLE_FAULT=alloc)");
     bytes = round_up(std::max<size_t>(bytes, 256), 256);
     if (!budget_reserve(ctx, bytes))
         return fail(RIPPLE_ERR_BUDGET, "allocation of " + std::to_string(bytes) + " bytes exceeds the memory budget");

@@ -70,6 +70,11 @@ int sweep_occ_f64_3d(int layout, int scheme, int v);
 // Aux kernels (f32/f64 x 2D/3D), defined in aux.cu.
 cudaError_t launch_prep(int dtype, int dim, void* buf, FieldCtl* ctl, const FieldGeom& g, int bc, double gamma,
                         const double inv_dx[3], int slot, int grid, cudaStream_t s);
+// Host-side fault injection for tests: RIPPLE_FAULT holds a comma-separated
+// list of host steps (alloc, admit, upload) that then fail as if the CUDA call
+// behind them had failed.  Nothing reaches the GPU: the failure is made on
+// the host, before the call it stands for.
+bool fault_injected(const char* step);
 // Read and clear the timeout flag of the staged layout microbenchmark kernels.
 unsigned layout_bench_take_error(cudaStream_t s);
 // Quiet NaN in every non-interior cell of a padded buffer (pad_fill_nan_kernel).
