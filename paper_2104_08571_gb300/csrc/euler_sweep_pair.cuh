@@ -78,11 +78,56 @@ __global__ void __launch_bounds__(256, 2)
     float* FY = Fs + NC * PC::NFX;
 
     const int tid = threadIdx.x;
-    const bool pthr = tid < PC::NPT;        // pair thread: owns columns (lx, lx+1) of row ly
+    const int lane = tid & 31;
+    // warp index broadcast from lane 0, so the compiler treats it (and every
+    // role or item-kind decision derived from it) as warp-uniform
+    const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
+    const bool pthr = warp < PC::NPT / 32;  // pair warps: each thread owns columns (lx, lx+1) of row ly
     const int lx = 2 * (tid % (TX / 2)), ly = (tid / (TX / 2)) % TY;
-    const int rot = (tid + 128) % NT;       // phase-P item rotation: second-pass items land on non-pair threads
-    const int fth = tid - PC::NPT;          // phase-F item index base of non-pair threads
     const FieldGeom& g = sg.f;
+
+    // Work items of this thread, the same for every plane and tile: only the
+    // staged plane (a ring slot) changes, so their shared-memory offsets are
+    // formed once.  Item bases are warp-uniform; the lanes of a partly filled
+    // warp past the last item repeat the last item (same operands, same
+    // results, same addresses), so no lane-dependent branch is needed.
+    // Phase P (predicted states, all warps; the rotation puts the second pass
+    // on the non-pair warps): plane offset of the leftmost stencil cell, then
+    // the index into the predicted-state arrays.
+    int p_src[PC::KP > 0 ? PC::KP : 1], p_dst[PC::KP > 0 ? PC::KP : 1];
+#pragma unroll
+    for (int k = 0; k < PC::KP; ++k) {
+        const int base = (warp * 32 + PC::NPT) % NT + k * NT;
+        if (base < PC::NXPr) {
+            const int it = min(base + lane, PC::NXP - 1);
+            const int cy = it / PC::XP, c0 = 2 * (it % PC::XP) - 1;
+            p_src[k] = PV::idx(c0 - 1, cy, 0);
+            p_dst[k] = cy * PC::XR + c0 + 1;
+        } else {
+            const int jj = min(base - PC::NXPr + lane, PC::NYP - 1);
+            const int cy = jj / (TX / 2) - 1, cx = 2 * (jj % (TX / 2));
+            p_src[k] = PV::idx(cx, cy, 0);
+            p_dst[k] = PC::NPX + (cy + 1) * TX + cx;
+        }
+    }
+    // Phase F (x/y face pairs, non-pair warps): source offset (predicted-state
+    // index, or plane offset for first order) and face-array index.
+    int f_src[PC::KF], f_dst[PC::KF];
+#pragma unroll
+    for (int k = 0; k < PC::KF; ++k) {
+        const int base = (warp - PC::NPT / 32) * 32 + k * (NT - PC::NPT);
+        if (base < PC::NXFr) {
+            const int it = min(max(base + lane, 0), PC::NXF - 1);
+            const int cy = it / PC::XP, f = 2 * (it % PC::XP);
+            f_src[k] = MUSCL ? cy * PC::XR + f : PV::idx(f - 2, cy, 0);
+            f_dst[k] = cy * PC::FXR + f;
+        } else {
+            const int jj = min(base - PC::NXFr + lane, PC::NYF - 1);
+            const int fy = jj / (TX / 2), cx = 2 * (jj % (TX / 2));
+            f_src[k] = MUSCL ? PC::NPX + fy * TX + cx : PV::idx(cx, fy - 1, 0);
+            f_dst[k] = fy * TX + cx;
+        }
+    }
 
     double* sdt = reinterpret_cast<double*>(smem + 256);  // step scalars formed by thread 0
     if (tid == 0) {
@@ -214,14 +259,11 @@ __global__ void __launch_bounds__(256, 2)
             const float* S = plane_ptr(seq_base + j);
 #pragma unroll
             for (int k = 0; k < PC::KP; ++k) {
-                const int it = rot + k * NT;
-                if (it < PC::NXPr) {
-                    if (it >= PC::NXP) continue;
-                    // x pair: cells (2q - 1, 2q) of row cy
-                    const int cy = it / PC::XP, q = it % PC::XP;
-                    const int c0 = 2 * q - 1;
+                const int base = (warp * 32 + PC::NPT) % NT + k * NT;  // warp-uniform
+                if (base < PC::NXPr) {
+                    // x pair: cells (2q - 1, 2q) of row cy, read from cell 2q - 2 (even x)
                     f2 qm[NC], qc[NC], qp[NC], L[NC], Rr[NC];
-                    const int o = PV::idx(c0 - 1, cy, 0);  // cell 2q - 2: even x
+                    const int o = p_src[k];
 #pragma unroll
                     for (int m = 0; m < NC; ++m) {
                         f2 A, B;
@@ -237,24 +279,21 @@ __global__ void __launch_bounds__(256, 2)
                         qp[m] = B;
                     }
                     muscl<f2, DIM, 0>(qm, qc, qp, gm1, half_dtdx[0], L, Rr, chk);
-                    const int pi = cy * PC::XR + c0 + 1;
+                    const int pi = p_dst[k];
 #pragma unroll
                     for (int m = 0; m < NC; ++m) {
                         st2(PL + m * NP + pi, L[m]);
                         st2(PR + m * NP + pi, Rr[m]);
                     }
-                } else {
-                    const int jj = it - PC::NXPr;
-                    if (jj >= PC::NYP) continue;
+                } else if (base < PC::NXPr + PC::NYPr) {
                     // y pair: cells (cx, cy), (cx + 1, cy)
-                    const int cy = jj / (TX / 2) - 1, cx = 2 * (jj % (TX / 2));
                     f2 qm[NC], qc[NC], qp[NC], L[NC], Rr[NC];
-                    const int o = PV::idx(cx, cy, 0);
+                    const int o = p_src[k];
                     load_pair(S, o - SY, qm);
                     load_pair(S, o, qc);
                     load_pair(S, o + SY, qp);
                     muscl<f2, DIM, 1>(qm, qc, qp, gm1, half_dtdx[1], L, Rr, chk);
-                    const int pi = PC::NPX + (cy + 1) * TX + cx;
+                    const int pi = p_dst[k];
 #pragma unroll
                     for (int m = 0; m < NC; ++m) {
                         st2(PL + m * NP + pi, L[m]);
@@ -323,14 +362,12 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
             for (int k = 0; k < PC::KF; ++k) {
                 if (pthr) break;
-                const int it = fth + k * (NT - PC::NPT);
-                if (it < PC::NXFr) {
-                    if (it >= PC::NXF) continue;
+                const int base = (warp - PC::NPT / 32) * 32 + k * (NT - PC::NPT);  // warp-uniform
+                if (base < PC::NXFr) {
                     // x faces (f, f + 1), f = 2q, between cells f - 1 | f and f | f + 1
-                    const int cy = it / PC::XP, f = 2 * (it % PC::XP);
                     f2 a[NC], b[NC], F[NC];
                     if (MUSCL) {
-                        const int i0 = cy * PC::XR + f;  // x-predicted index of cell f - 1
+                        const int i0 = f_src[k];  // x-predicted index of cell f - 1
 #pragma unroll
                         for (int m = 0; m < NC; ++m) {
                             a[m] = ld2(PR + m * NP + i0);
@@ -338,7 +375,7 @@ __global__ void __launch_bounds__(256, 2)
                             b[m] = f2{u.y, w.x};
                         }
                     } else {
-                        const int o = PV::idx(f - 2, cy, 0);  // cell f - 2: even x
+                        const int o = f_src[k];  // cell f - 2: even x
 #pragma unroll
                         for (int m = 0; m < NC; ++m) {
                             f2 A, B;
@@ -354,29 +391,27 @@ __global__ void __launch_bounds__(256, 2)
                         }
                     }
                     rus<f2, DIM, 0>(a, b, gamma, gm1, F, chk);
-                    const int fi = cy * PC::FXR + f;
+                    const int fi = f_dst[k];
 #pragma unroll
                     for (int m = 0; m < NC; ++m) st2(FX + m * PC::NFX + fi, F[m]);
-                } else {
-                    const int jj = it - PC::NXFr;
-                    if (jj >= PC::NYF) continue;
-                    const int fy = jj / (TX / 2), cx = 2 * (jj % (TX / 2));
+                } else if (base < PC::NXFr + PC::NYFr) {
                     f2 a[NC], b[NC], F[NC];
                     if (MUSCL) {
-                        const int il = PC::NPX + fy * TX + cx, ir = il + TX;
+                        const int il = f_src[k], ir = il + TX;
 #pragma unroll
                         for (int m = 0; m < NC; ++m) {
                             a[m] = ld2(PR + m * NP + il);
                             b[m] = ld2(PL + m * NP + ir);
                         }
                     } else {
-                        const int o = PV::idx(cx, fy - 1, 0);
+                        const int o = f_src[k];
                         load_pair(S, o, a);
                         load_pair(S, o + SY, b);
                     }
                     rus<f2, DIM, 1>(a, b, gamma, gm1, F, chk);
+                    const int fi = f_dst[k];
 #pragma unroll
-                    for (int m = 0; m < NC; ++m) st2(FY + m * PC::NFY + fy * TX + cx, F[m]);
+                    for (int m = 0; m < NC; ++m) st2(FY + m * PC::NFY + fi, F[m]);
                 }
             }
             __syncthreads();  // B3
@@ -411,28 +446,32 @@ __global__ void __launch_bounds__(256, 2)
                     for (int m = 0; m < NC; ++m) Fzm[m] = Fzp[m];
                 }
                 fence_proxy_async_smem();
-                // epilogue: wave-speed sums of both cells at once, then per cell
-                bool ok_l[2];
-                const f2 sw = wave_sum2<DIM>(qn, gamma, gm1, inv_dx, ok_l[0], ok_l[1]);
+                // epilogue: wave-speed sums and checks of both cells at once;
+                // cells outside the domain (ragged tiles) take no part in either
+                bool ok0, ok1;
+                const f2 sw = wave_sum2<DIM>(qn, gamma, gm1, inv_dx, ok0, ok1);
+                smax_local = fmaxf(smax_local, fmaxf(vx0 ? sw.x : 0.f, vx1 ? sw.y : 0.f));
+                const bool bad0 = vx0 && !ok0, bad1 = vx1 && !ok1;
+                if (bad0 || bad1) {
+                    bad = true;
+                    record_bad(ctl, BAD_CELL, bad0 ? gx : gx + 1, gy, z);
+                }
+                // tile-uniform: ragged tiles store directly; edge tiles write ghost images
+                if (!tma_store_ok || near_xy || (DIM == 3 && (z < g.h || z >= g.n[2] - g.h))) {
 #pragma unroll
-                for (int lane = 0; lane < 2; ++lane) {
-                    const bool v = lane == 0 ? vx0 : vx1;
-                    if (!v) continue;
-                    float q1[NC];
+                    for (int h = 0; h < 2; ++h) {
+                        if (!(h == 0 ? vx0 : vx1)) continue;
+                        float q1[NC];
 #pragma unroll
-                    for (int m = 0; m < NC; ++m) q1[m] = lane == 0 ? qn[m].x : qn[m].y;
-                    if (!tma_store_ok) {
-                        const long long base = geom_cell(g, gx + lane, gy, z) * g.cell_stride;
+                        for (int m = 0; m < NC; ++m) q1[m] = h == 0 ? qn[m].x : qn[m].y;
+                        if (!tma_store_ok) {
+                            const long long base = geom_cell(g, gx + h, gy, z) * g.cell_stride;
 #pragma unroll
-                        for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = q1[m];
+                            for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = q1[m];
+                        }
+                        if (near_xy || (DIM == 3 && (z < g.h || z >= g.n[2] - g.h)))
+                            write_ghost_images<float, DIM>(out, g, prm.bc, gx + h, gy, z, q1);
                     }
-                    if (!ok_l[lane]) {
-                        bad = true;
-                        record_bad(ctl, BAD_CELL, gx + lane, gy, z);
-                    }
-                    smax_local = fmaxf(smax_local, lane == 0 ? sw.x : sw.y);
-                    if (near_xy || (DIM == 3 && (z < g.h || z >= g.n[2] - g.h)))
-                        write_ghost_images<float, DIM>(out, g, prm.bc, gx + lane, gy, z, q1);
                 }
             }
             if (tma_store_ok) {

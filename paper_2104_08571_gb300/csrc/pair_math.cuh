@@ -84,9 +84,10 @@ __device__ __forceinline__ float max_lanes(f2 a) { return fmaxf(a.x, a.y); }
 
 __device__ __forceinline__ float minmod_s(float a, float b)
 {
-    // 0 if the one-sided differences disagree in sign, else the smaller one
-    if (a * b <= 0.f) return 0.f;
-    return fabsf(a) < fabsf(b) ? a : b;
+    // minmod(a, b) (0 if the one-sided differences disagree in sign, else the
+    // one of smaller magnitude) is the median of a, b and 0: three min/max
+    // operations and no compare-and-select
+    return fmaxf(fminf(a, b), fminf(fmaxf(a, b), 0.f));
 }
 __device__ __forceinline__ float minmod_v(float a, float b) { return minmod_s(a, b); }
 __device__ __forceinline__ f2 minmod_v(f2 a, f2 b) { return f2{minmod_s(a.x, b.x), minmod_s(a.y, b.y)}; }
