@@ -363,6 +363,39 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
             b = np.abs(loop_out.astype(np.float64)).reshape(4, -1).sum(1)
             worst = max(worst, float((a / b).max()))
             R.ripple_field_destroy(f)
+        # dependency-driven rounds: the same batch in ONE persistent launch
+        R.ripple_batch_configure(ctx, layout=cfg["layout"], tile_variant=cfg["tile_variant"],
+                                 steps_per_sync=nsteps, use_graphs=True, staging=cfg["staging"], async_queue=True)
+        run_batch()
+        sa0 = R.ripple_batch_get_stats(ctx)
+        reqs_a, infos_a, t_async = run_batch()
+        sa1 = R.ripple_batch_get_stats(ctx)
+        span_a = max(i["finish_s"] for i in infos_a) - min(i["start_s"] for i in infos_a)
+        same = all(np.array_equal(x["output"], y["output"]) for x, y in zip(reqs, reqs_a))
+        # uneven step counts (uniform in [nsteps/2, 3 nsteps/2], seeded): per-step
+        # launches shrink each round to the shortest remaining problem
+        steps_u = [int(nsteps // 2 + u * nsteps) for u in inputs.uniform(3, count, stream=6)]
+        cells_u = float(sum(side * side * k for side, k in zip(sides, steps_u)))
+        uneven = {}
+        for mode in ("per_step_launches", "dependency_driven"):
+            R.ripple_batch_configure(ctx, layout=cfg["layout"], tile_variant=cfg["tile_variant"],
+                                     steps_per_sync=max(steps_u), use_graphs=True, staging=cfg["staging"],
+                                     async_queue=mode == "dependency_driven")
+            for rep_ in range(2):  # warm-up, then timed
+                rq = [R.euler_request(U, k, [1.0 / U.shape[2], 1.0 / U.shape[1]]) for U, k in zip(states, steps_u)]
+                s0 = R.ripple_batch_get_stats(ctx)
+                t0 = time.perf_counter()
+                inf = [R.ripple_wait(ctx, t, 600000) for t in R.ripple_batch_submit(ctx, rq)]
+                dt_u = time.perf_counter() - t0
+                s1 = R.ripple_batch_get_stats(ctx)
+            assert all(i["status"] == R.RIPPLE_OK for i in inf), "uneven batched run failed"
+            sp = max(i["finish_s"] for i in inf) - min(i["start_s"] for i in inf)
+            uneven[mode] = {"value": cells_u / dt_u, "value_compute_span": cells_u / sp,
+                            "value_device": cells_u / (s1["device_s"] - s0["device_s"]),
+                            "launches": s1["launches"] - s0["launches"],
+                            "outputs": [r["output"] for r in rq]}
+        uneven_same = all(np.array_equal(x, y) for x, y in zip(uneven["per_step_launches"].pop("outputs"),
+                                                               uneven["dependency_driven"].pop("outputs")))
     finally:
         R.ripple_ctx_destroy(ctx)
     return {
@@ -376,6 +409,15 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
         "roofline": {"bound": "hbm", "achieved": 32.0 * cells * nsteps / span / 1e9, "peak": load_peaks()[0],
                      "unit": "GB/s", "frac": 32.0 * cells * nsteps / span / 1e9 / load_peaks()[0],
                      "algorithmic_bytes_per_cell_update": 32, "timing": "compute span of the 100 global steps"},
+        "batched_value_device": cells * nsteps / (st1["device_s"] - st0["device_s"]),
+        "dependency_driven_round": {
+            "value": cells * nsteps / t_async, "value_compute_span": cells * nsteps / span_a,
+            "value_device": cells * nsteps / (sa1["device_s"] - sa0["device_s"]),
+            "launches": sa1["launches"] - sa0["launches"], "speedup_vs_per_step_launches": t_batch / t_async,
+            "bitwise_equal_to_per_step_launches": same,
+            "uneven_steps": dict(uneven, workload=f"same instances, steps uniform in [{nsteps // 2}, {3 * nsteps // 2}]",
+                                 bitwise_equal=uneven_same,
+                                 speedup=uneven["dependency_driven"]["value"] / uneven["per_step_launches"]["value"])},
         "per_instance_loop_value": cells * nsteps / t_loop, "per_instance_loop_seconds": t_loop,
         "per_instance_loop_launches": count * nsteps,
         "speedup_vs_loop": t_loop / t_batch,

@@ -272,6 +272,14 @@ typedef struct {
                                  remaining work (0 = step every resident problem) */
     int staging;              /* halo staging of the Euler step: 0 = TMA tile loads by a producer warp
                                  into a shared-memory ring; 1 = direct loads by every thread */
+    int async_queue;          /* 1 = dependency-driven rounds: ONE persistent launch runs up to
+                                 steps_per_sync steps of every stepped Euler problem (each runs
+                                 min(steps_per_sync, its remaining steps), so a round does not
+                                 shrink when one problem ends); a tile of step n of a problem
+                                 starts as soon as that problem has completed step n - 1 (its dt
+                                 is the CFL limit of its whole state), with no barrier between
+                                 problems or global steps.  Uses TMA staging whatever `staging`
+                                 says.  0 = one launch per global step (default). */
 } ripple_batch_config;
 
 typedef struct {
@@ -279,11 +287,13 @@ typedef struct {
     int64_t global_steps, launches, graph_replays;
     double now_s;             /* runtime clock now */
     int64_t fim_iterations;   /* eikonal iterations issued */
+    double device_s;          /* GPU time of the compute rounds (CUDA events around each round's
+                                 launches on the compute stream) */
 } ripple_batch_stats;
 
 /* Set the batch configuration (defaults: SoA, 32x8, 16 steps per sync, graphs
- * on, F32, 4 FIM iterations per step, no cell budget, TMA staging).  Only
- * while no request is in flight. */
+ * on, F32, 4 FIM iterations per step, no cell budget, TMA staging, one launch
+ * per global step).  Only while no request is in flight. */
 RIPPLE_API ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* cfg);
 
 /* Queue n requests; tickets_out[i] identifies request i.  Validates every

@@ -42,12 +42,14 @@ constexpr int kBatchStagingDirect = 1;  // every thread loads from global memory
 
 template <typename T, int LAYOUT, int V>
 static cudaError_t step_v(int staging, int grid, cudaStream_t s, const BatchEuler* e, const void* f,
-                          const int* table, BatchCtl* c, int kind)
+                          const int* table, BatchCtl* c, int kind, BatchAsync* q)
 {
     constexpr int TX = kBatchVariants[V].tx, TY = kBatchVariants[V].ty;
     using BC = BatchEulerCfg<T, LAYOUT, TX, TY>;
     if (kind != 0)
         batch_fim_kernel<T><<<grid, 256, 0, s>>>(static_cast<const BatchFim<T>*>(f), table, c);
+    else if (q)  // a dependency-driven round (TMA staging)
+        batch_euler_kernel<T, LAYOUT, TX, TY, true><<<grid, BC::NTHREADS, BC::SMEM, s>>>(e, table, c, q);
     else if (staging == kBatchStagingDirect)
         batch_euler_direct_kernel<T, LAYOUT, TX, TY><<<grid, 256, 0, s>>>(e, table, c);
     else
@@ -66,27 +68,32 @@ static int occ_v(int staging)
         return n;
     }
     using BC = BatchEulerCfg<T, LAYOUT, TX, TY>;
-    auto k = batch_euler_kernel<T, LAYOUT, TX, TY>;
+    auto k = batch_euler_kernel<T, LAYOUT, TX, TY, false>;
+    auto ka = batch_euler_kernel<T, LAYOUT, TX, TY, true>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, BC::SMEM) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, BC::SMEM) != cudaSuccess) return 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, BC::NTHREADS, BC::SMEM);
     return n;
 }
 template <typename T, int LAYOUT>
 static cudaError_t step_l(int v, int staging, int grid, cudaStream_t s, const BatchEuler* e, const void* f,
-                          const int* t, BatchCtl* c, int kind)
+                          const int* t, BatchCtl* c, int kind, BatchAsync* q)
 {
-    if (v == 1) return step_v<T, LAYOUT, 1>(staging, grid, s, e, f, t, c, kind);
-    if (v == 2) return step_v<T, LAYOUT, 2>(staging, grid, s, e, f, t, c, kind);
-    return step_v<T, LAYOUT, 0>(staging, grid, s, e, f, t, c, kind);
+    if (v == 1) return step_v<T, LAYOUT, 1>(staging, grid, s, e, f, t, c, kind, q);
+    if (v == 2) return step_v<T, LAYOUT, 2>(staging, grid, s, e, f, t, c, kind, q);
+    return step_v<T, LAYOUT, 0>(staging, grid, s, e, f, t, c, kind, q);
 }
+// One launch: a global step of every Euler (kind 0) or eikonal (kind 1)
+// instance, or with q (Euler only) a whole dependency-driven round.
 static cudaError_t launch_batch_step(ripple_dtype dt, int layout, int v, int staging, int grid, cudaStream_t s,
-                                     const BatchEuler* e, const void* f, const int* t, BatchCtl* c, int kind)
+                                     const BatchEuler* e, const void* f, const int* t, BatchCtl* c, int kind,
+                                     BatchAsync* q = nullptr)
 {
     if (dt == RIPPLE_F32)
-        return layout == LAYOUT_SOA ? step_l<float, LAYOUT_SOA>(v, staging, grid, s, e, f, t, c, kind)
-                                    : step_l<float, LAYOUT_AOS>(v, staging, grid, s, e, f, t, c, kind);
-    return layout == LAYOUT_SOA ? step_l<double, LAYOUT_SOA>(v, staging, grid, s, e, f, t, c, kind)
-                                : step_l<double, LAYOUT_AOS>(v, staging, grid, s, e, f, t, c, kind);
+        return layout == LAYOUT_SOA ? step_l<float, LAYOUT_SOA>(v, staging, grid, s, e, f, t, c, kind, q)
+                                    : step_l<float, LAYOUT_AOS>(v, staging, grid, s, e, f, t, c, kind, q);
+    return layout == LAYOUT_SOA ? step_l<double, LAYOUT_SOA>(v, staging, grid, s, e, f, t, c, kind, q)
+                                : step_l<double, LAYOUT_AOS>(v, staging, grid, s, e, f, t, c, kind, q);
 }
 static int batch_occupancy(ripple_dtype dt, int layout, int v, int staging)
 {
@@ -130,6 +137,7 @@ __global__ void fill_uniform_euler(T* buf, const FieldGeom g)
 using Clock = std::chrono::steady_clock;
 
 constexpr int kSlots = 4096;  // concurrent problems (admitted, resident or completing)
+constexpr int kMaxRoundSteps = 4096;  // steps of one dependency-driven round
 
 struct Inst {
     uint64_t ticket = 0;
@@ -145,6 +153,7 @@ struct Inst {
     long long start_step = -1;  // Euler: launch index of local step 0 (recomputed on resume)
     long long steps_done = 0;   // Euler steps completed
     bool active = false;        // Euler: stepped in the current rounds
+    bool stepped = false;       // taken part in a compute round
     CUtensorMap map[2];         // Euler: TMA maps of buf[0], buf[1] (cached per tile variant and layout)
     int map_key = -1;
     cudaEvent_t ev = nullptr;
@@ -166,13 +175,14 @@ struct BatchRuntime {
     std::deque<Inst*> pending;                      // guarded by mu
     std::unordered_map<uint64_t, Ticket> tickets;   // guarded by mu
     uint64_t next_ticket = 1;                       // guarded by mu
-    ripple_batch_config cfg{RIPPLE_SOA, 0, 16, 1, RIPPLE_F32, 4, 0, 0};
+    ripple_batch_config cfg{RIPPLE_SOA, 0, 16, 1, RIPPLE_F32, 4, 0, 0, 0};
     ripple_batch_stats stats{};                     // guarded by mu
     Clock::time_point epoch = Clock::now();
     // scheduler-thread state
     std::vector<Inst*> uploading, resident, downloading;
     cudaStream_t compute = nullptr, copy = nullptr;
     cudaEvent_t ev_step = nullptr;
+    cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;  // timing of a compute round (device_s)
     bool started = false;
     // slot arrays: device, and pinned mirrors of status/counters/ctl
     FieldCtl* slot_ctl = nullptr;
@@ -192,11 +202,20 @@ struct BatchRuntime {
     void* h_fim = nullptr;
     int* h_table = nullptr;
     int cap_e = 0, cap_f = 0, cap_t = 0;
+    // dependency-driven rounds: control block, per-step task offsets, per-instance completions
+    BatchAsync* d_async = nullptr;
+    int* d_cum = nullptr;      // [kMaxRoundSteps + 1]
+    unsigned* d_done = nullptr;
+    int cap_done = 0;
+    BatchAsync* h_async = nullptr;  // pinned staging of the control block
+    int* h_cum = nullptr;           // pinned, [kMaxRoundSteps + 1]
+    std::vector<Inst*> euler_order;  // Euler instances in table order (set by rebuild_tables)
     bool dirty = true;
     bool has_e = false, has_f = false;  // resident kinds (set by rebuild_tables)
     long long gstep_e = 0;  // Euler steps issued (== device counter once they completed)
     long long gstep_f = 0;  // FIM iterations issued
-    int grid = 0;
+    int grid = 0;        // grid of the per-step launches (occupancy of the configured staging x SMs)
+    int grid_async = 0;  // grid of a dependency-driven round (TMA staging)
     std::map<int, cudaGraphExec_t> graphs;  // key: (steps << 2) | has_euler << 1 | has_fim
     int graph_variant = -1, graph_layout = -1, graph_fim = -1, graph_staging = -1;
 
@@ -458,6 +477,16 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
     std::vector<Inst*> order;
     for (Inst* in : rt->resident)
         if (in->req.kind == RIPPLE_REQ_EULER && in->active) order.push_back(in);
+    if (rt->cfg.async_queue) {
+        // dependency-driven rounds: most remaining steps first, so the instances
+        // still stepping at any step of a round are a prefix of the table (every
+        // instance that continues advances by the same K steps: the order holds
+        // until the resident set changes)
+        std::stable_sort(order.begin(), order.end(), [](const Inst* a, const Inst* b) {
+            return a->req.nsteps - a->steps_done > b->req.nsteps - b->steps_done;
+        });
+    }
+    rt->euler_order = order;
     for (Inst* in : rt->resident)
         if (in->req.kind != RIPPLE_REQ_EULER) order.push_back(in);
     int nt_e = 0;
@@ -471,6 +500,7 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
             e.g = in->g;
             e.tiles_x = in->tiles_x;
             e.tile_begin = t;
+            e.ntiles = in->ntiles;
             e.bc = (int)in->req.fv.bc;
             e.start_step = in->start_step;
             e.nsteps = in->req.nsteps;
@@ -577,8 +607,72 @@ static ripple_status launch_steps(BatchRuntime* rt, int K)
     return RIPPLE_OK;
 }
 
+// Queue one dependency-driven round on the compute stream: up to K steps of
+// every stepped Euler problem in ONE launch (each problem runs r = min(K, its
+// remaining steps)), then K x F FIM iterations of the eikonal problems.
+// steps[i] receives r of rt->euler_order[i].
+static ripple_status launch_round_async(BatchRuntime* rt, int K, std::vector<long long>& steps)
+{
+    const int ne = (int)rt->euler_order.size();
+    if (!rt->d_async) {
+        RIPPLE_CUDA(cudaMalloc(&rt->d_async, sizeof(BatchAsync)));
+        RIPPLE_CUDA(cudaMalloc(&rt->d_cum, (kMaxRoundSteps + 1) * sizeof(int)));
+        RIPPLE_CUDA(cudaMallocHost(&rt->h_async, sizeof(BatchAsync)));
+        RIPPLE_CUDA(cudaMallocHost(&rt->h_cum, (kMaxRoundSteps + 1) * sizeof(int)));
+    }
+    if (ne > rt->cap_done) {
+        RIPPLE_CUDA(cudaStreamSynchronize(rt->compute));
+        if (rt->d_done) cudaFree(rt->d_done);
+        rt->d_done = nullptr;
+        const int nc = std::max(ne, std::max(64, rt->cap_done * 2));
+        RIPPLE_CUDA(cudaMalloc(&rt->d_done, (size_t)nc * sizeof(unsigned)));
+        rt->cap_done = nc;
+    }
+    // tasks of round step n: the table prefix of the instances with r > n
+    steps.assign(ne, 0);
+    for (int i = 0; i < ne; ++i)
+        steps[i] = std::min<long long>(K, rt->euler_order[i]->req.nsteps - rt->euler_order[i]->steps_done);
+    rt->h_cum[0] = 0;
+    int m = ne;  // instances with r > n form the prefix [0, m)
+    long long tiles = 0;
+    for (int i = 0; i < ne; ++i) tiles += rt->euler_order[i]->ntiles;
+    for (int n = 0; n < K; ++n) {
+        while (m > 0 && steps[m - 1] <= n) {
+            --m;
+            tiles -= rt->euler_order[m]->ntiles;
+        }
+        for (int i = 0; i < m; ++i)
+            if (steps[i] <= n) return fail(RIPPLE_ERR_INTERNAL, "dependency-driven round: table not ordered");
+        if ((long long)rt->h_cum[n] + tiles > INT32_MAX) return fail(RIPPLE_ERR_INVALID, "round too large");
+        rt->h_cum[n + 1] = rt->h_cum[n] + (int)tiles;
+    }
+    BatchAsync& a = *rt->h_async;
+    a.next = 0;
+    a.total = rt->h_cum[K];
+    a.K = K;
+    a.pad = 0;
+    a.cum = rt->d_cum;
+    a.done = rt->d_done;
+    cudaStream_t s = rt->compute;
+    RIPPLE_CUDA(cudaMemcpyAsync(rt->d_cum, rt->h_cum, (K + 1) * sizeof(int), cudaMemcpyHostToDevice, s));
+    RIPPLE_CUDA(cudaMemcpyAsync(rt->d_async, rt->h_async, sizeof(BatchAsync), cudaMemcpyHostToDevice, s));
+    RIPPLE_CUDA(cudaMemsetAsync(rt->d_done, 0, (size_t)std::max(ne, 1) * sizeof(unsigned), s));
+    const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
+    RIPPLE_CUDA(launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, kBatchStagingTma, rt->grid_async, s,
+                                  rt->d_euler, rt->d_fim, rt->d_table, rt->d_bctl, 0, rt->d_async));
+    const int F = std::max(1, rt->cfg.fim_iters_per_step);
+    long long nf = 0;
+    for (long long k = 0; rt->has_f && k < (long long)K * F; ++k, ++nf)
+        RIPPLE_CUDA(launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->cfg.staging, rt->grid, s,
+                                      rt->d_euler, rt->d_fim, rt->d_table, rt->d_bctl, 1));
+    std::lock_guard<std::mutex> lk(rt->mu);
+    rt->stats.launches += 1 + nf;
+    return RIPPLE_OK;
+}
+
 // One scheduler round of compute: K units over the resident set (K is the
-// configured cap, lowered so that no Euler problem runs past its last step).
+// configured cap, lowered so that no Euler problem runs past its last step),
+// or one dependency-driven round (up to K steps of every Euler problem).
 static ripple_status compute_round(BatchRuntime* rt)
 {
     // Active set: resident Euler problems in order of least remaining work
@@ -612,11 +706,22 @@ static ripple_status compute_round(BatchRuntime* rt)
         if (st != RIPPLE_OK) return st;
     }
     long long K = std::max(1, rt->cfg.steps_per_sync);
-    for (Inst* in : rt->resident)
-        if (in->req.kind == RIPPLE_REQ_EULER && in->active) K = std::min(K, in->req.nsteps - in->steps_done);
+    const bool round_async = rt->cfg.async_queue && rt->has_e;
+    std::vector<long long> round_steps;
+    if (round_async) {
+        long long most = 1;
+        for (Inst* in : rt->euler_order) most = std::max(most, in->req.nsteps - in->steps_done);
+        K = std::min<long long>(std::min<long long>(K, kMaxRoundSteps), most);
+    } else {
+        for (Inst* in : rt->resident)
+            if (in->req.kind == RIPPLE_REQ_EULER && in->active) K = std::min(K, in->req.nsteps - in->steps_done);
+    }
     K = std::max(1LL, K);
-    ripple_status st = launch_steps(rt, (int)K);
+    RIPPLE_CUDA(cudaEventRecord(rt->ev_r0, rt->compute));
+    ripple_status st = round_async ? launch_round_async(rt, (int)K, round_steps) : launch_steps(rt, (int)K);
     if (st != RIPPLE_OK) return st;
+    RIPPLE_CUDA(cudaEventRecord(rt->ev_r1, rt->compute));
+    for (Inst* in : rt->resident) in->stepped = true;
     if (rt->has_f)
         RIPPLE_CUDA(cudaMemcpyAsync(rt->h_status, rt->slot_status, kSlots * sizeof(unsigned long long),
                                     cudaMemcpyDeviceToHost, rt->compute));
@@ -624,18 +729,25 @@ static ripple_status compute_round(BatchRuntime* rt)
                                 rt->compute));
     RIPPLE_CUDA(cudaEventRecord(rt->ev_step, rt->compute));
     RIPPLE_CUDA(cudaEventSynchronize(rt->ev_step));
+    float round_ms = 0.f;
+    RIPPLE_CUDA(cudaEventElapsedTime(&round_ms, rt->ev_r0, rt->ev_r1));
     if (*rt->h_berr) {
         RIPPLE_CUDA(cudaMemsetAsync(&rt->d_bctl->err, 0, sizeof(unsigned), rt->compute));
         return fail(RIPPLE_ERR_TIMEOUT, "a bounded wait of a batched launch ran out");
     }
     if (rt->has_e) rt->gstep_e += K;
-    for (Inst* in : rt->resident)
-        if (in->req.kind == RIPPLE_REQ_EULER && in->active) in->steps_done += K;
+    if (round_async) {
+        for (size_t i = 0; i < rt->euler_order.size(); ++i) rt->euler_order[i]->steps_done += round_steps[i];
+    } else {
+        for (Inst* in : rt->resident)
+            if (in->req.kind == RIPPLE_REQ_EULER && in->active) in->steps_done += K;
+    }
     if (rt->has_f) rt->gstep_f += K * std::max(1, rt->cfg.fim_iters_per_step);
     {
         std::lock_guard<std::mutex> lk(rt->mu);
         rt->stats.global_steps = rt->gstep_e;
         rt->stats.fim_iterations = rt->gstep_f;
+        rt->stats.device_s += 1e-3 * round_ms;
     }
     std::vector<Inst*> keep;
     for (Inst* in : rt->resident) {
@@ -719,6 +831,19 @@ static void scheduler(BatchRuntime* rt)
                 ++i;
             }
         }
+        // Requests submitted together start together: while nothing resident has
+        // stepped yet, the first round waits for the uploads already in flight
+        // (they complete in the copy stream's order), at most 50 ms.
+        bool fresh = !rt->resident.empty();
+        double joined = 1e300;
+        for (Inst* in : rt->resident) {
+            fresh = fresh && !in->stepped;
+            joined = std::min(joined, in->t_start);
+        }
+        if (fresh && !rt->uploading.empty() && rt->now() - joined < 0.05) {
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            continue;
+        }
         if (!rt->resident.empty()) {
             ripple_status st = compute_round(rt);
             if (st != RIPPLE_OK) {
@@ -764,6 +889,8 @@ static ripple_status rt_start(BatchRuntime* rt)
     RIPPLE_CUDA(cudaStreamCreateWithFlags(&rt->compute, cudaStreamNonBlocking));
     RIPPLE_CUDA(cudaStreamCreateWithFlags(&rt->copy, cudaStreamNonBlocking));
     RIPPLE_CUDA(cudaEventCreateWithFlags(&rt->ev_step, cudaEventDisableTiming));
+    RIPPLE_CUDA(cudaEventCreate(&rt->ev_r0));
+    RIPPLE_CUDA(cudaEventCreate(&rt->ev_r1));
     RIPPLE_CUDA(cudaMalloc(&rt->slot_ctl, kSlots * sizeof(FieldCtl)));
     RIPPLE_CUDA(cudaMalloc(&rt->slot_status, kSlots * sizeof(unsigned long long)));
     RIPPLE_CUDA(cudaMalloc(&rt->slot_counters, kSlots * 3 * sizeof(long long)));
@@ -780,6 +907,8 @@ static ripple_status rt_start(BatchRuntime* rt)
     const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
     const int occ = std::max(1, batch_occupancy(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->cfg.staging));
     rt->grid = occ * rt->ctx->sm_count;
+    rt->grid_async =
+        std::max(1, batch_occupancy(rt->cfg.dtype, layout, rt->cfg.tile_variant, kBatchStagingTma)) * rt->ctx->sm_count;
     rt->gstep_e = 0;
     rt->gstep_f = 0;
     rt->started = true;
@@ -946,11 +1075,18 @@ void batch_runtime_destroy(ripple_ctx ctx)
         cudaFree(rt->d_fim);
         cudaFree(rt->d_table);
         cudaFree(rt->d_bctl);
+        cudaFree(rt->d_async);
+        cudaFree(rt->d_cum);
+        cudaFree(rt->d_done);
+        if (rt->h_async) cudaFreeHost(rt->h_async);
+        if (rt->h_cum) cudaFreeHost(rt->h_cum);
         if (rt->h_berr) cudaFreeHost(rt->h_berr);
         cudaFreeHost(rt->h_euler);
         cudaFreeHost(rt->h_fim);
         cudaFreeHost(rt->h_table);
         cudaEventDestroy(rt->ev_step);
+        cudaEventDestroy(rt->ev_r0);
+        cudaEventDestroy(rt->ev_r1);
         cudaStreamDestroy(rt->compute);
         cudaStreamDestroy(rt->copy);
     }
@@ -968,6 +1104,7 @@ ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* 
     if (cfg->staging != kBatchStagingTma && cfg->staging != kBatchStagingDirect)
         return fail(RIPPLE_ERR_INVALID, "bad halo staging");
     if (cfg->steps_per_sync < 1) return fail(RIPPLE_ERR_INVALID, "steps_per_sync must be >= 1");
+    if (cfg->async_queue != 0 && cfg->async_queue != 1) return fail(RIPPLE_ERR_INVALID, "async_queue must be 0 or 1");
     if (cfg->fim_iters_per_step < 1 || cfg->fim_iters_per_step > 64)
         return fail(RIPPLE_ERR_INVALID, "fim_iters_per_step must be 1..64");
     if (cfg->dtype != RIPPLE_F32 && cfg->dtype != RIPPLE_F64) return fail(RIPPLE_ERR_INVALID, "bad dtype");
@@ -981,6 +1118,8 @@ ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* 
             // the kernel grid depends on the variant; the scheduler re-reads it
             const int layout = cfg->layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
             rt->grid = std::max(1, batch_occupancy(cfg->dtype, layout, cfg->tile_variant, cfg->staging)) * ctx->sm_count;
+            rt->grid_async =
+                std::max(1, batch_occupancy(cfg->dtype, layout, cfg->tile_variant, kBatchStagingTma)) * ctx->sm_count;
             if (cfg->dtype != rt->cfg.dtype) {
                 // descriptor arrays hold the element type: reallocate on next use
                 cudaFree(rt->d_fim);

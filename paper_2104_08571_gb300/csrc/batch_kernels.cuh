@@ -28,7 +28,7 @@ struct BatchEuler {  // aligned as CUtensorMap (at least 64 bytes)
     void* buf[2];
     FieldCtl* ctl;
     FieldGeom g;
-    int tiles_x, tile_begin;
+    int tiles_x, tile_begin, ntiles;
     int bc;
     long long start_step, nsteps;
     double gamma, gm1, cfl, inv_dx0, inv_dx1;  // gm1 = gamma - 1, formed on the host in FP64
@@ -57,6 +57,25 @@ struct BatchCtl {
     int ntiles_e;                 // table entries [0, ntiles_e) are Euler tiles
     int ntiles;                   // entries [ntiles_e, ntiles) are eikonal tiles
     unsigned int err;             // DEV_ERR_TIMEOUT: a bounded wait of a batched launch ran out
+};
+
+// Dependency-driven round of the batched Euler step (one persistent launch for
+// K steps).  The round's tasks are (round step n, table entry p) in step-major
+// order: step n holds the first cum[n + 1] - cum[n] Euler table entries (the
+// host orders Euler instances by remaining steps, so the instances still
+// stepping at round step n are a prefix).  CTAs take tasks in that order from
+// one atomic counter; a task of step n > 0 first waits until its instance has
+// completed step n - 1 (done[] counts consumer-warp completions, NCT / 32 per
+// tile), because its dt is the CFL limit of the instance's whole state after
+// that step.  Every dependency of a task precedes it in the order and tasks
+// are taken only by running CTAs, so the waits always end (bounded anyway).
+struct BatchAsync {
+    int next;            // next task (atomic); the host zeroes it before the launch
+    int total;           // tasks of the round: cum[K]
+    int K;               // steps of the round
+    int pad;
+    const int* cum;      // [K + 1] first task of each round step
+    unsigned* done;      // [Euler instances] consumer-warp completions this round
 };
 
 // Tile-table entry: (instance index << 1) | kind, kind 0 = Euler, 1 = eikonal.
@@ -93,11 +112,13 @@ struct BatchTileHdr {
     FieldCtl* ctl;   // the instance's control block
     T gamma, gm1, inv_dx0, inv_dx1, dt;
     int tile, x0, y0, bc, rs;  // rs: the instance's ring slot of this step's input
+    int inst;                  // Euler instance index (dependency counter of a dependency-driven round)
 };
 static_assert(sizeof(BatchTileHdr<double>) <= 192, "tile header fits the slot header");
 
-// The last CTA of a launch to finish advances the launch counter of its kind.
-__device__ __forceinline__ void batch_finish_launch(BatchCtl* bctl, int kind)
+// The last CTA of a launch to finish advances the step counter of its kind
+// (by the steps the launch ran: 1, or K for a dependency-driven round).
+__device__ __forceinline__ void batch_finish_launch(BatchCtl* bctl, int kind, unsigned long long steps = 1ull)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -105,10 +126,14 @@ __device__ __forceinline__ void batch_finish_launch(BatchCtl* bctl, int kind)
         if (atomicAdd(&bctl->done[kind], 1u) == gridDim.x - 1) {
             bctl->done[kind] = 0u;
             __threadfence();
-            atomicAdd(&bctl->gstep[kind], 1ull);
+            atomicAdd(&bctl->gstep[kind], steps);
         }
     }
 }
+
+constexpr uint32_t kDepSpinLimit = 1u << 23;  // dependency waits of a round (x 64 ns sleeps: about 0.5 s)
+constexpr int kAsyncChunk = 8;                // tasks a producer takes from a round's counter at once
+constexpr unsigned kPublishRun = 16;          // most completed tiles a consumer warp publishes at once
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
 {
@@ -143,10 +168,15 @@ __device__ __forceinline__ bool consumer_sync_or(bool p)
 // update one cell each (direct coalesced stores, ghost images), fold the new
 // wave speeds per warp into the instance's next ring slot, and release the
 // slot through its empty barrier.
-template <typename T, int LAYOUT, int TX, int TY>
+// ASYNC: the same pipeline runs a whole dependency-driven round (BatchAsync):
+// the producer takes tasks from the round's counter and waits for each task's
+// instance to finish the previous step before staging it; every consumer warp
+// publishes its part of a tile (fence, then an atomic on done[]).
+template <typename T, int LAYOUT, int TX, int TY, bool ASYNC = false>
 __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __restrict__ euler,
                                                           const int* __restrict__ table,
-                                                          BatchCtl* __restrict__ bctl)
+                                                          BatchCtl* __restrict__ bctl,
+                                                          BatchAsync* __restrict__ q = nullptr)
 {
     using B = BatchEulerCfg<T, LAYOUT, TX, TY>;
     using C = typename B::C;
@@ -183,14 +213,60 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
         if (tid == NCT) {
             unsigned seq = 0;
             bool ok = true;
+            // dependency-driven round: the current chunk of tasks [c_lo, c_hi), the
+            // cached task range [s_lo, s_hi) of round step s_n, the last dependency met
+            int c_lo = 0, c_hi = 0, s_lo = 0, s_hi = 0, s_n = 0, dep_inst = -1, dep_n = -1;
             for (int t = blockIdx.x;; t += gridDim.x) {
-                // next table entry whose instance steps in this launch
                 const BatchEuler* d = nullptr;
                 long long local = 0;
-                for (; t < end; t += gridDim.x) {
-                    d = &euler[__ldg(&table[t]) >> 1];
-                    local = (long long)gstep - d->start_step;
-                    if (local >= 0 && local < d->nsteps) break;
+                int inst = 0;
+                bool have = false;
+                if (!ASYNC) {
+                    // next table entry whose instance steps in this launch
+                    for (; t < end; t += gridDim.x) {
+                        inst = __ldg(&table[t]) >> 1;
+                        d = &euler[inst];
+                        local = (long long)gstep - d->start_step;
+                        if (local >= 0 && local < d->nsteps) break;
+                    }
+                    have = t < end;
+                } else {
+                    // next task of the round, taken kAsyncChunk at a time: round step
+                    // n (cum[n] <= k < cum[n + 1]) and table entry t = k - cum[n]
+                    if (c_lo == c_hi) {
+                        c_lo = atomicAdd(&q->next, kAsyncChunk);
+                        c_hi = min(c_lo + kAsyncChunk, q->total);
+                    }
+                    if (c_lo < c_hi) {
+                        const int k = c_lo++;
+                        if (k < s_lo || k >= s_hi) {
+                            int lo = 0, hi = q->K;
+                            while (hi - lo > 1) {
+                                const int mid = (lo + hi) >> 1;
+                                if (__ldg(&q->cum[mid]) <= k) lo = mid;
+                                else hi = mid;
+                            }
+                            s_n = lo;
+                            s_lo = __ldg(&q->cum[lo]);
+                            s_hi = __ldg(&q->cum[lo + 1]);
+                        }
+                        t = k - s_lo;
+                        inst = __ldg(&table[t]) >> 1;
+                        d = &euler[inst];
+                        local = (long long)gstep + s_n - d->start_step;
+                        if (s_n > 0 && (inst != dep_inst || s_n != dep_n)) {
+                            // the instance's previous step must be complete (its CFL maximum, its halos)
+                            const unsigned need = (unsigned)s_n * (unsigned)d->ntiles * (NCT / 32);
+                            uint32_t i = 0;
+                            while (ld_acquire_gpu(&q->done[inst]) < need && ++i < kDepSpinLimit) __nanosleep(64);
+                            if (i >= kDepSpinLimit) ok = false;
+                            // other CTAs' stores (generic proxy) before this CTA's TMA reads (async proxy)
+                            fence_proxy_async_global();
+                            dep_inst = inst;
+                            dep_n = s_n;
+                        }
+                        have = ok;
+                    }
                 }
                 const unsigned s = seq % NS;
                 if (seq >= NS && !mbar_wait_bounded(&empty[s], ((seq / NS) - 1) & 1u)) {
@@ -198,7 +274,7 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
                     break;
                 }
                 Hdr* h = slot_hdr(s);
-                if (t >= end) {
+                if (!have) {
                     h->tile = -1;
                     mbar_arrive(&full[s]);
                     ++seq;
@@ -222,6 +298,7 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
                 h->y0 = y0;
                 h->bc = d->bc;
                 h->rs = rs;
+                h->inst = inst;
                 if (lt == 0) {
                     ctl->t = local == 0 ? dt : ctl->t + dt;
                     ctl->dt_last = dt;
@@ -241,15 +318,32 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
             if (!ok) atomicOr(&bctl->err, DEV_ERR_TIMEOUT);
         }
         __syncwarp();
-        batch_finish_launch(bctl, 0);
+        batch_finish_launch(bctl, 0, ASYNC ? (unsigned long long)q->K : 1ull);
         return;
     }
 
     // ---------------- consumer warps ----------------
     const int lx = tid % TX, ly = tid / TX;
     bool timed_out = false;
+    // ASYNC: a warp publishes its parts of tiles late and in runs: the
+    // completed tiles of one instance accumulate (pend, npend) and one release
+    // publishes them after the faces of a tile of another instance, after
+    // kPublishRun tiles, or before the warp blocks waiting for its next tile
+    // (so no waiting warp holds unpublished tiles: the waits of a round end).
+    int pend = -1;
+    unsigned npend = 0;
+    auto publish = [&]() {
+        __syncwarp();
+        if ((tid & 31) == 0) red_release_gpu_add(&q->done[pend], npend);
+        pend = -1;
+        npend = 0;
+    };
     for (unsigned seq = 0;; ++seq) {
         const unsigned s = seq % NS;
+        if (ASYNC && pend >= 0) {
+            const bool ready = __shfl_sync(0xffffffffu, (tid & 31) == 0 && mbar_try_wait(&full[s], (seq / NS) & 1u), 0);
+            if (!ready) publish();
+        }
         const bool got = mbar_wait_bounded(&full[s], (seq / NS) & 1u);
         const Hdr& h = *slot_hdr(s);  // shared memory, valid until this warp releases the slot
         const bool stop = !got || h.tile < 0;  // taken by all consumers together at the barrier below
@@ -297,6 +391,7 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
         }
         __syncwarp();
         if (consumer_sync_or(stop)) break;  // faces of this tile written, unless a consumer stopped
+        if (ASYNC && pend >= 0 && (pend != h.inst || npend >= kPublishRun)) publish();
         const int gx = x0 + lx, gy = y0 + ly;
         const bool valid = (gx < g.n[0]) & (gy < g.n[1]);
         T smax = T(0);
@@ -333,13 +428,21 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
                 atomicOr(&ctl->err, DEV_ERR_NUMERIC);
             }
         }
+        // this warp's part of the tile (cells, ghost images, wave speeds) is
+        // published later: the warp barrier in publish() orders every lane's
+        // stores before lane 0's release, which the acquiring producer pairs with
+        if (ASYNC) {
+            pend = h.inst;
+            ++npend;
+        }
         // this warp's reads of the slot (tile and header) are done: release it
         __syncwarp();
         if ((tid & 31) == 0) mbar_arrive(&empty[s]);
     }
+    if (ASYNC && pend >= 0) publish();
     if (timed_out) atomicOr(&bctl->err, DEV_ERR_TIMEOUT);  // the runtime fails the resident set
     __syncwarp();
-    batch_finish_launch(bctl, 0);
+    batch_finish_launch(bctl, 0, ASYNC ? (unsigned long long)q->K : 1ull);
 }
 
 template <typename T>
