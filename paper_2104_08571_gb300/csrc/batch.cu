@@ -181,6 +181,9 @@ struct BatchRuntime {
     // scheduler-thread state
     std::vector<Inst*> uploading, resident, downloading;
     cudaStream_t compute = nullptr, copy = nullptr;
+    // the runtime's own stream-ordered pool: freed instance memory stays mapped
+    // for the next admission (no release to the driver at each synchronisation)
+    cudaMemPool_t pool = nullptr;
     cudaEvent_t ev_step = nullptr;
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;  // timing of a compute round (device_s)
     bool started = false;
@@ -230,11 +233,11 @@ static ripple_status rt_alloc(BatchRuntime* rt, size_t bytes, void** p)
     if (fault_injected("alloc")) return fail(RIPPLE_ERR_OOM, "device allocation failed (injected: RIPPLE_FAULT=alloc)");
     bytes = (bytes + 255) / 256 * 256;
     if (!budget_reserve(rt->ctx, bytes)) return RIPPLE_ERR_BUDGET;
-    cudaError_t e = cudaMallocAsync(p, bytes, rt->copy);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, rt->pool, rt->copy);
     if (e != cudaSuccess) {
         rt->ctx->used -= bytes;
         *p = nullptr;
-        return cuda_fail(e, "cudaMallocAsync");
+        return cuda_fail(e, "cudaMallocFromPoolAsync");
     }
     return RIPPLE_OK;
 }
@@ -833,14 +836,14 @@ static void scheduler(BatchRuntime* rt)
         }
         // Requests submitted together start together: while nothing resident has
         // stepped yet, the first round waits for the uploads already in flight
-        // (they complete in the copy stream's order), at most 50 ms.
+        // (they complete in the copy stream's order), at most one second.
         bool fresh = !rt->resident.empty();
         double joined = 1e300;
         for (Inst* in : rt->resident) {
             fresh = fresh && !in->stepped;
             joined = std::min(joined, in->t_start);
         }
-        if (fresh && !rt->uploading.empty() && rt->now() - joined < 0.05) {
+        if (fresh && !rt->uploading.empty() && rt->now() - joined < 1.0) {
             std::this_thread::sleep_for(std::chrono::microseconds(20));
             continue;
         }
@@ -888,6 +891,16 @@ static ripple_status rt_start(BatchRuntime* rt)
     RIPPLE_CUDA(cudaSetDevice(rt->ctx->device));
     RIPPLE_CUDA(cudaStreamCreateWithFlags(&rt->compute, cudaStreamNonBlocking));
     RIPPLE_CUDA(cudaStreamCreateWithFlags(&rt->copy, cudaStreamNonBlocking));
+    {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = rt->ctx->device;
+        RIPPLE_CUDA(cudaMemPoolCreate(&rt->pool, &props));
+        // keep up to the context budget (all of it when unlimited) mapped between uses
+        cuuint64_t keep = rt->ctx->budget ? (cuuint64_t)rt->ctx->budget : ~(cuuint64_t)0;
+        RIPPLE_CUDA(cudaMemPoolSetAttribute(rt->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
     RIPPLE_CUDA(cudaEventCreateWithFlags(&rt->ev_step, cudaEventDisableTiming));
     RIPPLE_CUDA(cudaEventCreate(&rt->ev_r0));
     RIPPLE_CUDA(cudaEventCreate(&rt->ev_r1));
@@ -1085,6 +1098,7 @@ void batch_runtime_destroy(ripple_ctx ctx)
         cudaFreeHost(rt->h_fim);
         cudaFreeHost(rt->h_table);
         cudaEventDestroy(rt->ev_step);
+        if (rt->pool) cudaMemPoolDestroy(rt->pool);
         cudaEventDestroy(rt->ev_r0);
         cudaEventDestroy(rt->ev_r1);
         cudaStreamDestroy(rt->compute);
