@@ -4,6 +4,7 @@
 #include <type_traits>
 
 #include "euler_sweep_pair.cuh"
+#include "euler_sweep_pair3.cuh"
 #include "runtime.h"
 
 namespace ripple {
@@ -19,14 +20,18 @@ struct SweepKernel {
     static constexpr int TY = kSweepVariants[V].ty;
     // the pair kernel covers the unsplit FP32 schemes; FORCE (split step) runs one cell per item
     static constexpr bool exists = !pair || (std::is_same<T, float>::value && SCHEME != SCHEME_FORCE);
+    // 3D MUSCL-Hancock: the split-barrier schedule (euler_sweep_pair3.cuh)
+    static constexpr bool pair3 = pair && DIM == 3 && SCHEME == SCHEME_MUSCL;
     static constexpr int smem()
     {
-        if constexpr (pair) return PairCfg<DIM, LAYOUT, SCHEME>::SMEM;
+        if constexpr (pair3) return Pair3Cfg<LAYOUT>::SMEM;
+        else if constexpr (pair) return PairCfg<DIM, LAYOUT, SCHEME>::SMEM;
         else return SweepCfg<T, DIM, LAYOUT, SCHEME, TX, TY>::SMEM;
     }
     static auto fn()
     {
-        if constexpr (pair && std::is_same<T, float>::value) return euler_sweep_pair_kernel<DIM, LAYOUT, SCHEME>;
+        if constexpr (pair3 && std::is_same<T, float>::value) return euler_sweep_pair3_kernel<LAYOUT>;
+        else if constexpr (pair && std::is_same<T, float>::value) return euler_sweep_pair_kernel<DIM, LAYOUT, SCHEME>;
         else return euler_sweep_kernel<T, DIM, LAYOUT, SCHEME, TX, TY>;
     }
 };
