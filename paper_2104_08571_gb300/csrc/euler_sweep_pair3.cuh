@@ -22,8 +22,10 @@
 // it.  The pairing of every arrive with its sync, the absence of lapping and
 // of deadlock over any interleaving are checked by a model of this protocol.
 // A thread keeps its own cells of plane z from the z direction in registers
-// for the update, so plane z is dead once the faces of plane z are complete
-// and the 4-slot ring prefetches a plane further ahead.
+// for the update, so plane z is dead once the faces of plane z are complete.
+// The updated pairs leave by direct 64-bit stores (each row of a tile is 128
+// contiguous bytes per component), which frees the output staging buffers
+// for a fifth ring slot: planes are prefetched up to five ahead.
 //
 // A TMA wait that runs out only records the abort flag: every warp still runs
 // the same plane loop (so every barrier still pairs up) and the CTA stops
@@ -51,13 +53,14 @@ template <int LAYOUT>
 struct Pair3Cfg {
     using PC = PairCfg<3, LAYOUT, SCHEME_MUSCL>;
     using C = typename PC::C;
-    static constexpr int NS = 4;  // ring slots: planes z+1..z+4 while the faces of plane z are formed
-    static constexpr int SMEM = C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * C::OUT_BYTES + 2 * PC::P_BYTES + PC::F_BYTES;
+    static constexpr int NS = 5;  // ring slots: planes z+1..z+5 while the faces of plane z are formed
+    static constexpr int SMEM = C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * PC::P_BYTES + PC::F_BYTES;
     static_assert(SMEM <= 113 * 1024, "two CTAs per SM");
     // named barriers (0 is __syncthreads)
     static constexpr uint32_t BAR_PD0 = 1, BAR_PD1 = 2, BAR_UD = 3, BAR_FD = 4;
 };
 
+// map_out is part of the sweep launch signature; this kernel stores directly.
 template <int LAYOUT>
 __global__ void __launch_bounds__(256, 2)
     euler_sweep_pair3_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out,
@@ -82,10 +85,8 @@ __global__ void __launch_bounds__(256, 2)
     double* red = reinterpret_cast<double*>(smem + 64);
     int* flags = reinterpret_cast<int*>(smem + 64 + 8 * 16);
     float* ring = reinterpret_cast<float*>(smem + C::HDR_BYTES);
-    float* stage = reinterpret_cast<float*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES);
-    float* Pbuf = reinterpret_cast<float*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * C::OUT_BYTES);
-    float* Fs =
-        reinterpret_cast<float*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * C::OUT_BYTES + 2 * PC::P_BYTES);
+    float* Pbuf = reinterpret_cast<float*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES);
+    float* Fs = reinterpret_cast<float*>(smem + C::HDR_BYTES + NS * C::SLOT_BYTES + 2 * PC::P_BYTES);
     float* FX = Fs;
     float* FY = Fs + NC * PC::NFX;
     auto PLb = [&](unsigned par) { return Pbuf + par * (PC::P_BYTES / sizeof(float)); };
@@ -132,7 +133,6 @@ __global__ void __launch_bounds__(256, 2)
         flags[0] = 0;
         fence_mbar_init();
         prefetch_tensormap(&map_in);
-        prefetch_tensormap(&map_out);
     }
     __syncthreads();
     const f2 gamma = splat<f2>((float)prm.gamma), gm1 = splat<f2>((float)(prm.gamma - 1.0));
@@ -182,20 +182,6 @@ __global__ void __launch_bounds__(256, 2)
             ok &= mbar_wait_bounded(&bars[sq % NS], (uint32_t)((sq / NS) & 1));
         if (need + 1 > ready_upto) ready_upto = need + 1;
         if (!ok) flags[0] = 1;  // recorded; the CTA stops at the next full barrier
-    };
-
-    // output staging (thread 0 stores a plane once its update is complete)
-    unsigned oc = 0;  // planes updated by this CTA (staging buffer oc & 1)
-    bool st_pend = false;
-    int st_x = 0, st_y = 0, st_z = 0;
-    unsigned st_slot = 0;
-    auto store_pending = [&]() {
-        if (!st_pend) return;
-        const float* src = stage + (size_t)st_slot * (C::OUT_BYTES / sizeof(float));
-        if (LAYOUT == LAYOUT_SOA) tma_store_4d(&map_out, src, st_x, st_y, st_z, 0);
-        else tma_store_3d(&map_out, src, st_x * NC, st_y, st_z);
-        bulk_commit();
-        st_pend = false;
     };
 
     auto load_pair = [&](const float* S, int o, f2 (&q)[NC]) {
@@ -269,7 +255,6 @@ __global__ void __launch_bounds__(256, 2)
         const int gx = x0 + lx, gy = y0 + ly;
         const bool vx0 = pthr && (gx < g.n[0]) && (gy < g.n[1]);
         const bool vx1 = pthr && (gx + 1 < g.n[0]) && (gy < g.n[1]);
-        const bool tma_store_ok = x0 + TX <= g.n[0];
         const bool near_xy = (x0 < g.h) || (x0 + TX > g.n[0] - g.h) || (y0 < g.h) || (y0 + TY > g.n[1] - g.h);
         float chk = 1.f;
 
@@ -279,11 +264,7 @@ __global__ void __launch_bounds__(256, 2)
 
         // ---- item start: every plane of the previous item is dead ----
         __syncthreads();
-        if (tid == 0) {
-            store_pending();
-            bulk_wait_read<0>();
-            issue_until(seq_base + NS);  // planes 0..3 (z0-2 .. z0+1)
-        }
+        if (tid == 0) issue_until(seq_base + NS);  // planes 0..4 (z0-2 .. z0+2)
         wait_planes(seq_base + 3);
         __syncthreads();
         if (flags[0]) {
@@ -305,7 +286,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll 1
         for (int k = 0; k < np_items; ++k) p_item(k, plane_ptr(seq_base + R), PLb(0), chk);
         __syncthreads();
-        if (tid == 0) issue_until(seq_base + 2 + NS);  // planes 0, 1 are dead: planes 4, 5
+        if (tid == 0) issue_until(seq_base + 2 + NS);  // planes 0, 1 are dead: planes 5, 6
 
         for (int zl = 0; zl < zn; ++zl) {
             const int z = z0 + zl;
@@ -330,15 +311,11 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
                     for (int m = 0; m < NC; ++m) zR[m] = Rn[m];
                 }
-                if (tid == 0) bulk_wait_read<0>();  // the staging buffer of this plane is free
                 named_sync(P3::BAR_FD, NT);
-                if (tid == 0) {
-                    store_pending();                    // plane z-1
-                    issue_until(seq_base + jc + 1 + NS);  // planes up to z are dead
-                }
+                if (tid == 0) issue_until(seq_base + jc + 1 + NS);  // planes up to z are dead
                 // ---- update of plane z ----
-                float* st = stage + (size_t)(oc & 1u) * (C::OUT_BYTES / sizeof(float));
                 f2 qn[NC];
+                const long long obase = geom_cell(g, gx, gy, z) * g.cell_stride;
 #pragma unroll
                 for (int m = 0; m < NC; ++m) {
                     const float* fxr = FX + m * PC::NFX + ly * PC::FXR + lx;
@@ -350,16 +327,18 @@ __global__ void __launch_bounds__(256, 2)
                     acc = fma_v(fyh - fyl, inv_dx[1], acc);
                     acc = fma_v(Fzp[m] - Fzm[m], inv_dx[2], acc);
                     qn[m] = fma_v(f2{-dtv.x, -dtv.y}, acc, qz[m]);
-                    if (tma_store_ok) {
-                        if (LAYOUT == LAYOUT_SOA) st2(st + (m * TY + ly) * TX + lx, qn[m]);
+                    // both cells in the domain: one store per component (SoA: an aligned
+                    // pair, x of the pair even and rows 16-byte aligned)
+                    if (vx1) {
+                        if (LAYOUT == LAYOUT_SOA)
+                            *reinterpret_cast<f2*>(out + obase + (long long)m * g.comp_stride) = qn[m];
                         else {
-                            st[(ly * TX + lx) * NC + m] = qn[m].x;
-                            st[(ly * TX + lx + 1) * NC + m] = qn[m].y;
+                            out[obase + m] = qn[m].x;
+                            out[obase + NC + m] = qn[m].y;
                         }
                     }
                     Fzm[m] = Fzp[m];
                 }
-                fence_proxy_async_smem();
                 if (more) named_arrive(P3::BAR_UD, NT);
                 bool ok0, ok1;
                 const f2 sw = wave_sum2<DIM>(qn, gamma, gm1, inv_dx, ok0, ok1);
@@ -369,14 +348,15 @@ __global__ void __launch_bounds__(256, 2)
                     bad = true;
                     record_bad(ctl, BAD_CELL, bad0 ? gx : gx + 1, gy, z);
                 }
-                if (!tma_store_ok || near_xy || z < g.h || z >= g.n[2] - g.h) {
+                if (near_xy || z < g.h || z >= g.n[2] - g.h || (vx0 && !vx1)) {
+                    // edge tiles: ghost images; a ragged last column: its single cell
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {
                         if (!(h == 0 ? vx0 : vx1)) continue;
                         float q1[NC];
 #pragma unroll
                         for (int m = 0; m < NC; ++m) q1[m] = h == 0 ? qn[m].x : qn[m].y;
-                        if (!tma_store_ok) {
+                        if (vx0 && !vx1) {
                             const long long base = geom_cell(g, gx + h, gy, z) * g.cell_stride;
 #pragma unroll
                             for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = q1[m];
@@ -384,13 +364,6 @@ __global__ void __launch_bounds__(256, 2)
                         if (near_xy || z < g.h || z >= g.n[2] - g.h)
                             write_ghost_images<float, DIM>(out, g, prm.bc, gx + h, gy, z, q1);
                     }
-                }
-                if (tid == 0 && tma_store_ok) {
-                    st_pend = true;
-                    st_x = x0;
-                    st_y = y0;
-                    st_z = z;
-                    st_slot = oc & 1u;
                 }
             } else {
                 if (zl > 0) {
@@ -446,15 +419,12 @@ __global__ void __launch_bounds__(256, 2)
                 record_bad(ctl, BAD_STATE, x0, y0, z);
                 chk = 1.f;
             }
-            if (pthr) ++oc;
         }
         seq_base += (unsigned)(zn + 2 * R);
     }
 
     __syncthreads();
     if (tid == 0) {
-        if (!aborted) store_pending();
-        bulk_wait<0>();
         if (aborted) {
             for (unsigned sq = ready_upto; sq < ld_seq; ++sq)
                 mbar_wait_bounded(&bars[sq % NS], (uint32_t)((sq / NS) & 1));
