@@ -103,10 +103,12 @@ def test_blast_fp32_parity(ctx, layout):
     assert rel_l1(got, ref) <= 2e-5
 
 
+@pytest.mark.parametrize("nz", [70, 33])
 @pytest.mark.parametrize("layout", [R.RIPPLE_SOA, R.RIPPLE_AOS])
-def test_blast_fp32_parity_several_z_chunks(ctx, layout):
-    # 70 planes: three z chunks per tile (32, 32, 6) with ragged x and y tiles
-    U0 = inputs.euler3d_blast(70, seed=2, dims=(37, 21, 70)).astype(np.float32)
+def test_blast_fp32_parity_several_z_chunks(ctx, layout, nz):
+    # 70 planes: three z chunks per tile (32, 32, 6); 33: a last chunk of one
+    # plane; ragged x and y tiles
+    U0 = inputs.euler3d_blast(nz, seed=2, dims=(37, 21, nz)).astype(np.float32)
     got, _ = gpu_euler(ctx, U0, 6, dtype=R.RIPPLE_F32, scheme=MUSCL, bc=TRA, layout=layout)
     ref, _ = oracle.euler_run(U0.astype(np.float64), 6, scheme=MUSCL, bc=TRA)
     assert rel_l1(got, ref) <= 2e-5
