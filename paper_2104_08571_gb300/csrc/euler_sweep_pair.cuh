@@ -43,13 +43,28 @@ struct PairCfg {
     static constexpr int KF = (NXFr + NYFr + (NT - NPT) - 1) / (NT - NPT);  // on the non-pair threads
     static constexpr int P_BYTES = SCHEME == SCHEME_MUSCL ? ((2 * NC * NP * 4 + 127) / 128) * 128 : 0;
     static constexpr int F_BYTES = ((NC * (NFX + NFY) * 4 + 127) / 128) * 128;
-    static constexpr int SMEM = C::HDR_BYTES + C::NS * C::SLOT_BYTES + 2 * C::OUT_BYTES + P_BYTES + F_BYTES;
+    // ring slots: 2D items are single planes, so the ring prefetches whole tiles ahead
+    static constexpr int NSR = DIM == 2 ? 6 : C::NS;
+    // CTAs per SM: the 2D first-order sweeps (Rusanov, the split FORCE sweep) need
+    // fewer registers and their short per-tile work wants more CTAs in flight
+    static constexpr int MIN_CTAS = DIM == 2 && SCHEME != SCHEME_MUSCL ? 3 : 2;
+    static constexpr int SMEM = C::HDR_BYTES + NSR * C::SLOT_BYTES + 2 * C::OUT_BYTES + P_BYTES + F_BYTES;
     static_assert(C::OFF + R == 4 || LAYOUT == LAYOUT_AOS, "pairs at even x need an even in-slot x offset");
     static_assert(C::BX % 2 == 0 && NP % 2 == 0 && NFX % 2 == 0 && NFY % 2 == 0, "64-bit aligned pairs");
 };
 
+// First-order face flux of a scheme along D on cell pairs: Rusanov, or FORCE
+// for the split step.
+template <int SCHEME, int DIM, int D>
+__device__ __forceinline__ void pair_flux1(const f2 (&a)[DIM + 2], const f2 (&b)[DIM + 2], f2 gamma, f2 gm1,
+                                           f2 half_dtdx, f2 half_inv_dtdx, f2 (&F)[DIM + 2], float& chk)
+{
+    if constexpr (SCHEME == SCHEME_FORCE) force<f2, DIM, D>(a, b, gm1, half_dtdx, half_inv_dtdx, F, chk);
+    else rus<f2, DIM, D>(a, b, gamma, gm1, F, chk);
+}
+
 template <int DIM, int LAYOUT, int SCHEME>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, PairCfg<DIM, LAYOUT, SCHEME>::MIN_CTAS)
     euler_sweep_pair_kernel(const __grid_constant__ CUtensorMap map_in, const __grid_constant__ CUtensorMap map_out,
                             float* __restrict__ out, FieldCtl* __restrict__ ctl, const SweepGeom sg,
                             const SweepParams prm)
@@ -57,8 +72,9 @@ __global__ void __launch_bounds__(256, 2)
     using PC = PairCfg<DIM, LAYOUT, SCHEME>;
     using C = typename PC::C;
     using PV = PlaneView<C, LAYOUT>;
-    constexpr int TX = PC::TX, TY = PC::TY, NC = PC::NC, R = PC::R, NS = C::NS, NT = PC::NT;
+    constexpr int TX = PC::TX, TY = PC::TY, NC = PC::NC, R = PC::R, NS = PC::NSR, NT = PC::NT;
     constexpr bool MUSCL = SCHEME == SCHEME_MUSCL;
+    constexpr bool FORCE = SCHEME == SCHEME_FORCE;  // one sweep of the split step per launch
     constexpr int SX = LAYOUT == LAYOUT_SOA ? 1 : NC;
     constexpr int SY = LAYOUT == LAYOUT_SOA ? C::BX : C::BX * NC;
     constexpr int SM = LAYOUT == LAYOUT_SOA ? C::BX * C::BY : 1;
@@ -134,8 +150,11 @@ __global__ void __launch_bounds__(256, 2)
         // dt from the max wave-speed sum of the input state, in FP64 once per CTA
         const double dt = prm.cfl / __longlong_as_double((long long)ctl->smax[prm.slot_in]);
         sdt[0] = dt;
-        for (int d = 0; d < 3; ++d) sdt[1 + d] = 0.5 * dt * prm.inv_dx[d];
-        if (blockIdx.x == 0) {
+        for (int d = 0; d < 3; ++d) {
+            sdt[1 + d] = 0.5 * dt * prm.inv_dx[d];
+            sdt[4 + d] = prm.inv_dx[d] > 0.0 ? 0.5 / (dt * prm.inv_dx[d]) : 0.0;  // (dx/dt)/2 (FORCE)
+        }
+        if (blockIdx.x == 0 && prm.last) {
             ctl->t = prm.first ? dt : ctl->t + dt;
             ctl->dt_last = dt;
             ctl->smax[(prm.slot_in + 2) % 3] = 0ull;
@@ -149,12 +168,18 @@ __global__ void __launch_bounds__(256, 2)
     __syncthreads();
     const f2 gamma = splat<f2>((float)prm.gamma), gm1 = splat<f2>((float)(prm.gamma - 1.0));
     const f2 dtv = splat<f2>((float)sdt[0]);
-    f2 inv_dx[3], half_dtdx[3];
+    f2 inv_dx[3], half_dtdx[3], half_inv_dtdx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         inv_dx[d] = splat<f2>((float)prm.inv_dx[d]);
         half_dtdx[d] = splat<f2>((float)sdt[1 + d]);
+        half_inv_dtdx[d] = splat<f2>((float)sdt[4 + d]);
     }
+    // axes of this launch: all (unsplit step) or one sweep of the split step
+    const bool ax0 = prm.axis < 0 || prm.axis == 0;
+    const bool ax1 = prm.axis < 0 || prm.axis == 1;
+    const bool ax2 = DIM == 3 && (prm.axis < 0 || prm.axis == 2);
+
 
     auto item_planes = [&](int item) -> int {
         if (DIM == 2) return 1;
@@ -312,10 +337,12 @@ __global__ void __launch_bounds__(256, 2)
             if (flags[0]) { aborted = true; break; }
             if (pthr) {
                 if (!MUSCL) {
-                    f2 q0[NC], q1[NC];
-                    load_pair(plane_ptr(seq_base + 0), my_off, q0);
-                    load_pair(plane_ptr(seq_base + 1), my_off, q1);
-                    rus<f2, DIM, 2 % DIM>(q0, q1, gamma, gm1, Fzm, chk);
+                    if (ax2) {
+                        f2 q0[NC], q1[NC];
+                        load_pair(plane_ptr(seq_base + 0), my_off, q0);
+                        load_pair(plane_ptr(seq_base + 1), my_off, q1);
+                        pair_flux1<SCHEME, DIM, 2 % DIM>(q0, q1, gamma, gm1, half_dtdx[2], half_inv_dtdx[2], Fzm, chk);
+                    }
                 } else {
                     f2 q0[NC], q1[NC], q2[NC], q3[NC], L1[NC], R1[NC], L2[NC];
                     load_pair(plane_ptr(seq_base + 0), my_off, q0);
@@ -343,10 +370,12 @@ __global__ void __launch_bounds__(256, 2)
             // ---------------- phase F: z work (pair threads), x/y face pairs (others) ----------------
             if (DIM == 3 && pthr) {
                 if (!MUSCL) {
-                    f2 q0[NC], q1[NC];
-                    load_pair(S, my_off, q0);
-                    load_pair(plane_ptr(seq_base + jc + 1), my_off, q1);
-                    rus<f2, DIM, 2 % DIM>(q0, q1, gamma, gm1, Fzp, chk);
+                    if (ax2) {
+                        f2 q0[NC], q1[NC];
+                        load_pair(S, my_off, q0);
+                        load_pair(plane_ptr(seq_base + jc + 1), my_off, q1);
+                        pair_flux1<SCHEME, DIM, 2 % DIM>(q0, q1, gamma, gm1, half_dtdx[2], half_inv_dtdx[2], Fzp, chk);
+                    }
                 } else {
                     // predicted states of plane z + 1 and the face z + 1/2
                     f2 q0[NC], q1[NC], q2[NC], L[NC], Rn[NC];
@@ -364,6 +393,7 @@ __global__ void __launch_bounds__(256, 2)
                 if (pthr) break;
                 const int base = (warp - PC::NPT / 32) * 32 + k * (NT - PC::NPT);  // warp-uniform
                 if (base < PC::NXFr) {
+                    if (FORCE && !ax0) continue;
                     // x faces (f, f + 1), f = 2q, between cells f - 1 | f and f | f + 1
                     f2 a[NC], b[NC], F[NC];
                     if (MUSCL) {
@@ -390,11 +420,12 @@ __global__ void __launch_bounds__(256, 2)
                             b[m] = B;
                         }
                     }
-                    rus<f2, DIM, 0>(a, b, gamma, gm1, F, chk);
+                    pair_flux1<SCHEME, DIM, 0>(a, b, gamma, gm1, half_dtdx[0], half_inv_dtdx[0], F, chk);
                     const int fi = f_dst[k];
 #pragma unroll
                     for (int m = 0; m < NC; ++m) st2(FX + m * PC::NFX + fi, F[m]);
                 } else if (base < PC::NXFr + PC::NYFr) {
+                    if (FORCE && !ax1) continue;
                     f2 a[NC], b[NC], F[NC];
                     if (MUSCL) {
                         const int il = f_src[k], ir = il + TX;
@@ -408,7 +439,7 @@ __global__ void __launch_bounds__(256, 2)
                         load_pair(S, o, a);
                         load_pair(S, o + SY, b);
                     }
-                    rus<f2, DIM, 1>(a, b, gamma, gm1, F, chk);
+                    pair_flux1<SCHEME, DIM, 1>(a, b, gamma, gm1, half_dtdx[1], half_inv_dtdx[1], F, chk);
                     const int fi = f_dst[k];
 #pragma unroll
                     for (int m = 0; m < NC; ++m) st2(FY + m * PC::NFY + fi, F[m]);
@@ -429,9 +460,16 @@ __global__ void __launch_bounds__(256, 2)
                     const f2 fr = f2{fl.y, fn.x};
                     const f2 fyl = ld2(FY + m * PC::NFY + ly * TX + lx);
                     const f2 fyh = ld2(FY + m * PC::NFY + (ly + 1) * TX + lx);
-                    f2 acc = (fr - fl) * inv_dx[0];
-                    acc = fma_v(fyh - fyl, inv_dx[1], acc);
-                    if (DIM == 3) acc = fma_v(Fzp[m] - Fzm[m], inv_dx[2], acc);
+                    f2 acc;
+                    if constexpr (FORCE) {  // one axis per sweep
+                        acc = ax0 ? (fr - fl) * inv_dx[0] : f2{0.f, 0.f};
+                        if (ax1) acc = fma_v(fyh - fyl, inv_dx[1], acc);
+                        if (ax2) acc = fma_v(Fzp[m] - Fzm[m], inv_dx[2], acc);
+                    } else {
+                        acc = (fr - fl) * inv_dx[0];
+                        acc = fma_v(fyh - fyl, inv_dx[1], acc);
+                        if (DIM == 3) acc = fma_v(Fzp[m] - Fzm[m], inv_dx[2], acc);
+                    }
                     qn[m] = fma_v(f2{-dtv.x, -dtv.y}, acc, qc[m]);
                     if (tma_store_ok) {
                         if (LAYOUT == LAYOUT_SOA) st2(st + (m * TY + ly) * TX + lx, qn[m]);
@@ -513,7 +551,7 @@ __global__ void __launch_bounds__(256, 2)
     if (tid == 0) {
         double m = 0.0;
         for (int w = 0; w < NT / 32; ++w) m = fmax(m, red[w]);
-        atomic_max_pos_double(&ctl->smax[(prm.slot_in + 1) % 3], m);
+        if (prm.last) atomic_max_pos_double(&ctl->smax[(prm.slot_in + 1) % 3], m);
         if (any_bad) atomicOr(&ctl->err, DEV_ERR_NUMERIC);
     }
 }

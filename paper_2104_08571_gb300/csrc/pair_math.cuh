@@ -171,6 +171,27 @@ __device__ __forceinline__ void rus(const V (&a)[DIM + 2], const V (&b)[DIM + 2]
     for (int m = 0; m < DIM + 2; ++m) F[m] = half * fma_v(s, a[m] - b[m], Fa[m] + Fb[m]);
 }
 
+// FORCE face flux along D (Toro): the mean of the Lax-Friedrichs flux and
+// the flux of the Richtmyer state q = (a + b)/2 - (dt/dx)/2 (F(b) - F(a));
+// dtdx = dt/dx, inv_dtdx = dx/dt.  Admissibility of a and b goes to chk (q is
+// an intermediate of the formula).  Products and sums round separately, so
+// the x and y faces of transposed data give transposed results.
+template <typename V, int DIM, int D>
+__device__ __forceinline__ void force(const V (&a)[DIM + 2], const V (&b)[DIM + 2], V gm1, V half_dtdx,
+                                      V half_inv_dtdx, V (&F)[DIM + 2], float& chk)
+{
+    V Fa[DIM + 2], Fb[DIM + 2], q[DIM + 2], Fq[DIM + 2], ia, ua, pa, ib, ub, pb, iq, uq, pq;
+    pflux<V, DIM, D>(a, gm1, Fa, ia, ua, pa);
+    pflux<V, DIM, D>(b, gm1, Fb, ib, ub, pb);
+    track4(chk, a[0], pa, b[0], pb);
+    const V half = splat<V>(0.5f);
+#pragma unroll
+    for (int m = 0; m < DIM + 2; ++m) q[m] = half * (a[m] + b[m]) - half_dtdx * (Fb[m] - Fa[m]);
+    pflux<V, DIM, D>(q, gm1, Fq, iq, uq, pq);
+#pragma unroll
+    for (int m = 0; m < DIM + 2; ++m) F[m] = half * (half * (Fa[m] + Fb[m]) - half_inv_dtdx * (b[m] - a[m]) + Fq[m]);
+}
+
 // MUSCL-Hancock face states of cells along D from (left, centre, right).
 template <typename V, int DIM, int D>
 __device__ __forceinline__ void muscl(const V (&qm)[DIM + 2], const V (&q)[DIM + 2], const V (&qp)[DIM + 2], V gm1,

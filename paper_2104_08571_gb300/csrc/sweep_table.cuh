@@ -18,8 +18,8 @@ struct SweepKernel {
     static constexpr bool pair = V == kPairVariant;
     static constexpr int TX = kSweepVariants[V].tx;
     static constexpr int TY = kSweepVariants[V].ty;
-    // the pair kernel covers the unsplit FP32 schemes; FORCE (split step) runs one cell per item
-    static constexpr bool exists = !pair || (std::is_same<T, float>::value && SCHEME != SCHEME_FORCE);
+    // the pair kernels cover every FP32 scheme (the split FORCE step one sweep per launch)
+    static constexpr bool exists = !pair || std::is_same<T, float>::value;
     // 3D MUSCL-Hancock: the split-barrier schedule (euler_sweep_pair3.cuh)
     static constexpr bool pair3 = pair && DIM == 3 && SCHEME == SCHEME_MUSCL;
     static constexpr int smem()
