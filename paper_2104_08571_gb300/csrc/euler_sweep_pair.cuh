@@ -14,6 +14,12 @@
 // high-face predicted state and the z face fluxes stay in registers.
 // Shared arrays are laid out so that every pair access of the SoA layout is
 // one 64-bit shared-memory access.  Tile: 32 x 8 cells.
+// Schemes: Rusanov (first order) and MUSCL-Hancock for the unsplit step (3D
+// MUSCL-Hancock runs the split-barrier kernel of euler_sweep_pair3.cuh), and
+// FORCE for one axis sweep of the split step (prm.axis; faces and update of
+// that axis only; dt, t and the CFL maximum are taken by the step's last sweep).
+// 2D items are single planes: the ring holds six, and the first-order 2D
+// sweeps run three CTAs per SM.
 #pragma once
 #include <cuda.h>
 #include <cstdint>
