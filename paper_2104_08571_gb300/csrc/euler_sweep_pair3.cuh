@@ -6,9 +6,9 @@
 //
 // Work per plane z of a tile (pairs of x-adjacent cells, 256 threads):
 //   pair warps 0-3 (each thread owns the columns (lx, lx+1) of row ly):
-//     one item of y-predicted states of plane z+1, the z direction (predicted
-//     states of plane z+1 from planes z..z+2 and the face z+1/2, registers),
-//     and the update of plane z;
+//     one item of y-predicted states of plane z+1 and the z direction
+//     (predicted states of plane z+1 from planes z..z+2 and the face z+1/2,
+//     registers), then the update of plane z;
 //   warps 4-7: the x/y face fluxes of plane z (2 or 3 items each) and the rest
 //     of the x/y predicted states of plane z+1 (1 or 2 items each).
 // The predicted-state arrays are double buffered (plane parity), so the
@@ -293,14 +293,13 @@ __global__ void __launch_bounds__(256, 2)
             const unsigned jc = (unsigned)(zl + R);
             const bool more = zl + 1 < zn;
             if (pthr) {
-                // predicted states (y) of plane z+1
-                if (more) {
-                    wait_planes(seq_base + jc + 1);
-                    p_item(0, plane_ptr(seq_base + jc + 1), PLb((zl + 1) & 1), chk);
-                    named_arrive(((zl + 1) & 1) ? P3::BAR_PD1 : P3::BAR_PD0, NT);
-                }
-                // z direction: predicted states of plane z+1 and the face z+1/2
                 wait_planes(seq_base + jc + 2);
+                // predicted states (y) of plane z+1, then the z direction (predicted
+                // states of plane z+1, face z+1/2): independent work in one block for
+                // the scheduler.  At the last plane of a tile the y item is computed
+                // too (plane z+1 is a staged halo plane; nothing reads that buffer
+                // any more), but not announced.
+                p_item(0, plane_ptr(seq_base + jc + 1), PLb((zl + 1) & 1), chk);
                 {
                     f2 q1[NC], q2[NC], L[NC], Rn[NC];
                     load_pair(plane_ptr(seq_base + jc), my_off, qz);
@@ -311,6 +310,7 @@ __global__ void __launch_bounds__(256, 2)
 #pragma unroll
                     for (int m = 0; m < NC; ++m) zR[m] = Rn[m];
                 }
+                if (more) named_arrive(((zl + 1) & 1) ? P3::BAR_PD1 : P3::BAR_PD0, NT);
                 named_sync(P3::BAR_FD, NT);
                 if (tid == 0) issue_until(seq_base + jc + 1 + NS);  // planes up to z are dead
                 // ---- update of plane z ----
