@@ -265,6 +265,12 @@ __global__ void __launch_bounds__(256, 2)
         // ---- item start: every plane of the previous item is dead ----
         __syncthreads();
         if (tid == 0) issue_until(seq_base + NS);  // planes 0..4 (z0-2 .. z0+2)
+        // Planes of earlier tiles that this thread never waited for (warps 4-7
+        // skip the last two planes of a tile) are complete: the pair warps
+        // waited for them before the barrier above.  Skip them: their slots are
+        // being reloaded, and a wait on a slot whose mbarrier has since moved two
+        // phases on would read the parity of a phase that never completes.
+        if (ready_upto < seq_base) ready_upto = seq_base;
         wait_planes(seq_base + 3);
         __syncthreads();
         if (flags[0]) {

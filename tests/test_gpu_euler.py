@@ -117,6 +117,24 @@ def test_blast_fp32_parity_several_z_chunks(ctx, layout, nz):
     assert rel_l1(per, ref_p) <= 2e-5
 
 
+def test_many_tiles_per_cta_many_launches(ctx):
+    # 1024 z-chunked tiles over the persistent CTAs (several tiles per CTA) for
+    # 200 launches: every tile boundary hands the plane ring over between warps
+    # that wait for different planes; no bounded wait may run out
+    dims = (128, 256, 256)
+    U0 = inputs.euler3d_blast(256, seed=4, dims=dims).astype(np.float32)
+    f = R.ripple_field_create(ctx, dims, 5, R.RIPPLE_SOA, 2, R.RIPPLE_F32)
+    try:
+        R.ripple_field_upload(f, U0)
+        prm = R.make_fv_params([1 / 256] * 3, scheme=MUSCL, bc=TRA)
+        st = R.ripple_fv_step(f, prm, 200)
+        assert st["steps_done"] == 200
+        out = R.ripple_field_download(f)
+        assert np.isfinite(out).all()
+    finally:
+        R.ripple_field_destroy(f)
+
+
 @pytest.mark.parametrize("dtype", [R.RIPPLE_F32, R.RIPPLE_F64])
 @pytest.mark.parametrize("dims,scheme", [((45, 30), MUSCL), ((21, 17, 15), MUSCL), ((21, 17, 15), RUS)])
 def test_aos_equals_soa_bitwise(ctx, dtype, dims, scheme):
