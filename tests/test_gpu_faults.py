@@ -66,9 +66,11 @@ def _euler(n, steps=5):
     return R.euler_request(U, steps, [1.0 / n, 1.0 / n])
 
 
+@pytest.mark.parametrize("async_queue", [False, True])
 @pytest.mark.parametrize("step,status", [("admit", R.RIPPLE_ERR_OOM), ("upload", R.RIPPLE_ERR_CUDA),
                                          ("alloc", R.RIPPLE_ERR_OOM)])
-def test_batch_request_failure_then_recovery(ctx, step, status):
+def test_batch_request_failure_then_recovery(ctx, step, status, async_queue):
+    R.ripple_batch_configure(ctx, async_queue=async_queue)
     good = _euler(48)
     tickets = R.ripple_batch_submit(ctx, [good])
     assert R.ripple_wait(ctx, tickets[0], 60000)["status"] == R.RIPPLE_OK
