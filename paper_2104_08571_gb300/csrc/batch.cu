@@ -653,7 +653,11 @@ static ripple_status launch_round_async(BatchRuntime* rt, int K, std::vector<lon
     a.next = 0;
     a.total = rt->h_cum[K];
     a.K = K;
-    a.pad = 0;
+    // a step's tasks spread over the CTAs: take them several at a time only when
+    // every CTA gets that many (a small problem's step stays spread over many
+    // CTAs, so its next step is not held up behind one CTA's chunk)
+    const int per_cta = (int)std::min<long long>(kAsyncChunk, (long long)rt->h_cum[1] / std::max(1, rt->grid_async));
+    a.chunk = std::max(1, per_cta);
     a.cum = rt->d_cum;
     a.done = rt->d_done;
     cudaStream_t s = rt->compute;

@@ -73,7 +73,7 @@ struct BatchAsync {
     int next;            // next task (atomic); the host zeroes it before the launch
     int total;           // tasks of the round: cum[K]
     int K;               // steps of the round
-    int pad;
+    int chunk;           // tasks a producer takes at once (1..kAsyncChunk: fewer when a step has few tiles)
     const int* cum;      // [K + 1] first task of each round step
     unsigned* done;      // [Euler instances] consumer-warp completions this round
 };
@@ -132,7 +132,7 @@ __device__ __forceinline__ void batch_finish_launch(BatchCtl* bctl, int kind, un
 }
 
 constexpr uint32_t kDepSpinLimit = 1u << 23;  // dependency waits of a round (x 64 ns sleeps: about 0.5 s)
-constexpr int kAsyncChunk = 8;                // tasks a producer takes from a round's counter at once
+constexpr int kAsyncChunk = 8;                // most tasks a producer takes from a round's counter at once
 constexpr unsigned kPublishRun = 16;          // most completed tiles a consumer warp publishes at once
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar)
@@ -231,11 +231,12 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
                     }
                     have = t < end;
                 } else {
-                    // next task of the round, taken kAsyncChunk at a time: round step
+                    // next task of the round, taken q->chunk at a time: round step
                     // n (cum[n] <= k < cum[n + 1]) and table entry t = k - cum[n]
                     if (c_lo == c_hi) {
-                        c_lo = atomicAdd(&q->next, kAsyncChunk);
-                        c_hi = min(c_lo + kAsyncChunk, q->total);
+                        const int ch = q->chunk;
+                        c_lo = atomicAdd(&q->next, ch);
+                        c_hi = min(c_lo + ch, q->total);
                     }
                     if (c_lo < c_hi) {
                         const int k = c_lo++;
