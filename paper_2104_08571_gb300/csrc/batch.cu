@@ -47,7 +47,7 @@ static cudaError_t step_v(int staging, int grid, cudaStream_t s, const BatchEule
     constexpr int TX = kBatchVariants[V].tx, TY = kBatchVariants[V].ty;
     using BC = BatchEulerCfg<T, LAYOUT, TX, TY>;
     if (kind != 0)
-        batch_fim_kernel<T><<<grid, 256, 0, s>>>(static_cast<const BatchFim<T>*>(f), table, c);
+        batch_fim_kernel<T><<<grid, EikTile<2>::NT, 0, s>>>(static_cast<const BatchFim<T>*>(f), table, c);
     else if (q)  // a dependency-driven round (TMA staging)
         batch_euler_kernel<T, LAYOUT, TX, TY, true><<<grid, BC::NTHREADS, BC::SMEM, s>>>(e, table, c, q);
     else if (staging == kBatchStagingDirect)

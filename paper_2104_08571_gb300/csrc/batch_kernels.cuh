@@ -627,7 +627,7 @@ __global__ void __launch_bounds__(256) batch_euler_direct_kernel(const BatchEule
 
 // One FIM iteration of every resident eikonal problem.
 template <typename T>
-__global__ void __launch_bounds__(256) batch_fim_kernel(const BatchFim<T>* __restrict__ fim,
+__global__ void __launch_bounds__(EikTile<2>::NT) batch_fim_kernel(const BatchFim<T>* __restrict__ fim,
                                                         const int* __restrict__ table, BatchCtl* __restrict__ bctl)
 {
     __shared__ FimSmem<T, 2> sm;

@@ -70,7 +70,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) fim_kernel(const FimProblem<T> a, const EikArgs e)
+__global__ void __launch_bounds__(EikTile<DIM>::NT) fim_kernel(const FimProblem<T> a, const EikArgs e)
 {
     __shared__ FimSmem<T, DIM> sm;
     __shared__ int sflag[2];
@@ -214,7 +214,7 @@ static ripple_status run_fim(FimProblem<T>& a, EikArgs& e, ripple_ctx ctx, int t
     cudaStream_t s = ctx->stream;
     auto kern = fim_kernel<T, DIM>;
     int per_sm = 0;
-    RIPPLE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0));
+    RIPPLE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, EikTile<DIM>::NT, 0));
     if (per_sm < 1) return fail(RIPPLE_ERR_INTERNAL, "FIM kernel cannot be resident");
     int grid = std::min(per_sm * ctx->sm_count, a.ntiles);
     grid = std::max(grid, 1);
@@ -222,7 +222,7 @@ static ripple_status run_fim(FimProblem<T>& a, EikArgs& e, ripple_ctx ctx, int t
     const int igrid = (int)std::min<long long>((total + 255) / 256, 8LL * ctx->sm_count);
     RIPPLE_CUDA(launch_fim_init<T>(a, ts, igrid, s));
     void* args[] = {&a, &e};
-    RIPPLE_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(256), args, 0, s));
+    RIPPLE_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(EikTile<DIM>::NT), args, 0, s));
     return RIPPLE_OK;
 }
 

@@ -66,7 +66,9 @@ __device__ __forceinline__ T godunov(T a0, T a1, T a2, T f)
 template <int DIM>
 struct EikTile {
     static constexpr int TS = DIM == 2 ? 32 : 8;
-    static constexpr int NT = 256;
+    // threads per tile: a tile visit is a chain of Jacobi sweeps, so more threads
+    // per 32 x 32 tile (two cells each) shorten every sweep; 8^3 tiles keep 256
+    static constexpr int NT = DIM == 2 ? 512 : 256;
     static constexpr int CELLS = DIM == 2 ? TS * TS : TS * TS * TS;
     static constexpr int CPT = CELLS / NT;  // cells per thread
     static constexpr int P = TS + 2;        // padded tile side
