@@ -95,6 +95,17 @@ static cudaError_t launch_batch_step(ripple_dtype dt, int layout, int v, int sta
     return layout == LAYOUT_SOA ? step_l<double, LAYOUT_SOA>(v, staging, grid, s, e, f, t, c, kind, q)
                                 : step_l<double, LAYOUT_AOS>(v, staging, grid, s, e, f, t, c, kind, q);
 }
+// CTAs per SM of the batched FIM iteration kernel.
+static int fim_occupancy(ripple_dtype dt)
+{
+    int n = 0;
+    if (dt == RIPPLE_F32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_fim_kernel<float>, EikTile<2>::NT, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_fim_kernel<double>, EikTile<2>::NT, 0);
+    return std::max(1, n);
+}
+
 static int batch_occupancy(ripple_dtype dt, int layout, int v, int staging)
 {
     auto pick = [&](auto tag) -> int {
@@ -219,8 +230,9 @@ struct BatchRuntime {
     long long gstep_f = 0;  // FIM iterations issued
     int grid = 0;        // grid of the per-step launches (occupancy of the configured staging x SMs)
     int grid_async = 0;  // grid of a dependency-driven round (TMA staging)
+    int grid_fim = 0;    // grid of the FIM iteration launches (one wave of the FIM kernel)
     std::map<int, cudaGraphExec_t> graphs;  // key: (steps << 2) | has_euler << 1 | has_fim
-    int graph_variant = -1, graph_layout = -1, graph_fim = -1, graph_staging = -1;
+    int graph_variant = -1, graph_layout = -1, graph_fim = -1, graph_staging = -1, graph_dtype = -1;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - epoch).count(); }
 };
@@ -561,7 +573,7 @@ static ripple_status launch_steps(BatchRuntime* rt, int K)
                                   rt->compute, rt->d_euler,
                                   rt->d_fim, rt->d_table, rt->d_bctl, 0);
         for (int f = 0; f < F && rt->has_f && e == cudaSuccess; ++f)
-            e = launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->cfg.staging, rt->grid,
+            e = launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->cfg.staging, rt->grid_fim,
                                   rt->compute, rt->d_euler,
                                   rt->d_fim, rt->d_table, rt->d_bctl, 1);
         return e;
@@ -574,12 +586,13 @@ static ripple_status launch_steps(BatchRuntime* rt, int K)
         return RIPPLE_OK;
     }
     if (rt->graph_variant != rt->cfg.tile_variant || rt->graph_layout != layout || rt->graph_fim != F ||
-        rt->graph_staging != rt->cfg.staging) {
+        rt->graph_staging != rt->cfg.staging || rt->graph_dtype != (int)rt->cfg.dtype) {
         for (auto& g : rt->graphs) cudaGraphExecDestroy(g.second);
         rt->graphs.clear();
         rt->graph_variant = rt->cfg.tile_variant;
         rt->graph_layout = layout;
         rt->graph_staging = rt->cfg.staging;
+        rt->graph_dtype = (int)rt->cfg.dtype;
         rt->graph_fim = F;
     }
     // K as a sum of powers of two, each replayed from a captured graph
@@ -670,7 +683,7 @@ static ripple_status launch_round_async(BatchRuntime* rt, int K, std::vector<lon
     const int F = std::max(1, rt->cfg.fim_iters_per_step);
     long long nf = 0;
     for (long long k = 0; rt->has_f && k < (long long)K * F; ++k, ++nf)
-        RIPPLE_CUDA(launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->cfg.staging, rt->grid, s,
+        RIPPLE_CUDA(launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->cfg.staging, rt->grid_fim, s,
                                       rt->d_euler, rt->d_fim, rt->d_table, rt->d_bctl, 1));
     std::lock_guard<std::mutex> lk(rt->mu);
     rt->stats.launches += 1 + nf;
@@ -924,6 +937,7 @@ static ripple_status rt_start(BatchRuntime* rt)
     const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
     const int occ = std::max(1, batch_occupancy(rt->cfg.dtype, layout, rt->cfg.tile_variant, rt->cfg.staging));
     rt->grid = occ * rt->ctx->sm_count;
+    rt->grid_fim = fim_occupancy(rt->cfg.dtype) * rt->ctx->sm_count;
     rt->grid_async =
         std::max(1, batch_occupancy(rt->cfg.dtype, layout, rt->cfg.tile_variant, kBatchStagingTma)) * rt->ctx->sm_count;
     rt->gstep_e = 0;
@@ -1136,6 +1150,7 @@ ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* 
             // the kernel grid depends on the variant; the scheduler re-reads it
             const int layout = cfg->layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
             rt->grid = std::max(1, batch_occupancy(cfg->dtype, layout, cfg->tile_variant, cfg->staging)) * ctx->sm_count;
+            rt->grid_fim = fim_occupancy(cfg->dtype) * ctx->sm_count;
             rt->grid_async =
                 std::max(1, batch_occupancy(cfg->dtype, layout, cfg->tile_variant, kBatchStagingTma)) * ctx->sm_count;
             if (cfg->dtype != rt->cfg.dtype) {
