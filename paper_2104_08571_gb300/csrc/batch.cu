@@ -1,17 +1,20 @@
 // Batched and served execution of many independent 2D problems (Euler and
 // eikonal) on one GPU: admission by device-memory budget, resident state,
-// continuous batching of every resident problem into one launch per global
-// step, and completion tickets with timestamps.  The paper has no counterpart
-// (its scheduler runs one graph; this runtime replaces a request loop).
+// continuous batching of every resident problem, and completion tickets with
+// timestamps.  The paper has no counterpart (its scheduler runs one graph;
+// this runtime replaces a request loop).
 //
-// A scheduler thread per context owns two streams: the compute stream runs the
-// batched step kernel (batch_kernels.cuh) K global steps at a time (optionally
-// replayed from a CUDA graph), the copy stream runs admissions (host -> device
-// copy, layout scatter, padding fill / FIM initialisation) and completions
-// (device -> host gather and copy).  Device memory comes from the stream-ordered
-// pool (cudaMallocAsync / cudaFreeAsync on the copy stream), counted against
-// the context budget: a request waits while its memory does not fit, so
-// problems join and leave the resident set while others keep running.
+// A scheduler thread per context owns two streams: the compute stream runs
+// rounds of up to K Euler steps of the resident set, either one launch of the
+// batched step kernel (batch_kernels.cuh) per global step (optionally replayed
+// from a CUDA graph) or one dependency-driven launch for the whole round
+// (async_queue), each followed by the eikonal FIM iterations; the copy stream
+// runs admissions (host -> device copy, layout scatter, padding fill / FIM
+// initialisation) and completions (device -> host gather and copy).  Device
+// memory comes from the runtime's own stream-ordered pool (on the copy stream),
+// counted against the context budget: a request waits while its memory does
+// not fit, so problems join and leave the resident set while others keep
+// running.
 #include <algorithm>
 #include <chrono>
 #include <cstring>

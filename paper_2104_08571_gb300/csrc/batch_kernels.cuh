@@ -9,7 +9,9 @@
 // double-buffer parity and its own FIM iteration counter, all derived from the
 // device-side global step counter and the step at which the problem joined.
 // The last CTA of a launch advances that counter, so K launches can be queued
-// (or captured in a CUDA graph) without host involvement.
+// (or captured in a CUDA graph) without host involvement.  A dependency-driven
+// round (BatchAsync below) runs K steps of every Euler problem in one launch
+// of the same kernel instead.
 #pragma once
 #include <cstdint>
 
