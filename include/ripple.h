@@ -119,7 +119,9 @@ RIPPLE_API ripple_status ripple_ctx_mem_used(ripple_ctx ctx, size_t* bytes);
  * of every axis, stored in `layout` with element type `dtype`.  Device memory
  * holds two padded buffers (the double buffer of Section 5.4, in -> out, then
  * swap); the second is allocated on first use by a solver.  Contents start
- * undefined; upload before use.
+ * undefined; upload before use.  RIPPLE_ERR_INVALID for dims outside
+ * 1..2^20, halo outside 0..8, or more than 2^32 padded cells per buffer;
+ * RIPPLE_ERR_OOM / RIPPLE_ERR_BUDGET when the memory is not there.
  */
 RIPPLE_API ripple_status ripple_field_create(ripple_ctx ctx, int ndim, const int64_t* dims, int ncomp,
                                   ripple_layout layout, int halo, ripple_dtype dtype,

@@ -410,6 +410,12 @@ ripple_status ripple_field_create(ripple_ctx ctx, int ndim, const int64_t* dims,
     f->dtype = dtype;
     f->geom = make_field_geom(ndim, dims, ncomp, layout, halo, dtype, &f->bytes);
     const FieldGeom& g = f->geom;
+    // at most 2^32 padded cells per buffer: byte counts stay far from overflow
+    // and every tile, item and table count of the kernels fits in 32 bits
+    if (g.px * g.py * g.pz > (1LL << 32)) {
+        delete f;
+        return fail(RIPPLE_ERR_INVALID, "field too large: more than 2^32 padded cells per buffer");
+    }
     f->elems = (size_t)(g.px * g.py * g.pz) * ncomp;
     ripple_status st = ctx_alloc(ctx, f->bytes, &f->buf[0]);
     if (st == RIPPLE_OK) st = ctx_alloc(ctx, sizeof(FieldCtl), reinterpret_cast<void**>(&f->ctl));

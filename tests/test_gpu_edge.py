@@ -63,6 +63,13 @@ def test_empty_and_invalid_fields_are_refused(ctx):
     assert lib.ripple_field_create(ctx, 4, d, 6, R.RIPPLE_SOA, 1, R.RIPPLE_F32, ctypes.byref(out)) == \
         R.RIPPLE_ERR_INVALID  # ndim 4
     assert lib.ripple_field_create(ctx, 2, d, 4, 7, 1, R.RIPPLE_F32, ctypes.byref(out)) == R.RIPPLE_ERR_INVALID
+    # maximum sizes: more than 2^32 padded cells per buffer is refused before any
+    # allocation (a 2^20-cube would overflow a 64-bit byte count)
+    for dims in ((1 << 20, 1 << 20), (1 << 20, 1 << 20, 1 << 20), (70000, 70000)):
+        d = (ctypes.c_int64 * len(dims))(*dims)
+        assert lib.ripple_field_create(ctx, len(dims), d, len(dims) + 2, R.RIPPLE_SOA, 2, R.RIPPLE_F32,
+                                       ctypes.byref(out)) == R.RIPPLE_ERR_INVALID
+    d = (ctypes.c_int64 * 2)(8, 8)
     # a periodic axis narrower than the halo cannot be padded
     f = R.ripple_field_create(ctx, (1, 6), 4, R.RIPPLE_SOA, 2, R.RIPPLE_F64)
     try:
