@@ -1,0 +1,340 @@
+// FP32 2D sweep of the dimensionally split FORCE step (the paper's own Euler
+// solver, Section 7.3, Listing euler_graph) on strip walks, sm_103a.
+//
+// One sweep of the split step reads the one-cell neighbours along a single
+// axis, so it needs no 2D tile and no block barrier.  Each warp walks a strip
+// 64 cells wide along the swept axis, one chunk of 64 cells (one row
+// segment) at a time; every lane owns a pair of x-adjacent cells held as
+// f32x2 values, so the flux and update arithmetic issues once for two cells
+// (pair_math.cuh).
+//   x sweep (AXIS 0): a walk runs along a row.  Lane l evaluates the right
+//     faces of its two cells as one pair; the left faces are lane l - 1's
+//     right faces (a shuffle) and, for lane 0, the last face of the previous
+//     chunk, carried in registers.  The right neighbour of lane 31 is the
+//     first cell after the chunk, staged with it.
+//   y sweep (AXIS 1): a walk runs down the rows of a 64-column strip; the
+//     face below a row is the face above the next one.
+// Either way every face of a walk is evaluated once; the first face of a walk
+// is evaluated again by the walk before it (the host makes walks long enough
+// that this stays a few per cent of the arithmetic).
+//
+// Staging: every warp owns a ring of NS shared-memory slots of one chunk
+// (1 KB) each, filled by per-thread asynchronous copies (cp.async, 16 bytes
+// per copy for whole chunks) NS - 1 chunks (x) or NS - 2 rows (y) ahead of
+// the arithmetic, so the loads in flight cost no registers.  A thread waits
+// for its own copy groups only and __syncwarp publishes the lanes' copies to
+// each other, so no wait can hang and no CTA barrier is needed.  Stores are
+// coalesced and direct.  dt, t and the CFL maximum follow the tiled sweep: dt
+// from the wave-speed maximum of the step's input state; the last sweep of a
+// step advances t and reduces the maximum of the new state.  Cells on the
+// boundary write their ghost images for the next sweep, as in every sweep.
+#pragma once
+#include <cstdint>
+
+#include "euler_sweep.cuh"
+#include "pair_math.cuh"
+
+namespace ripple {
+
+template <int NS_>
+struct WalkCfg {
+    static constexpr int NS = NS_;                           // ring slots per warp
+    static constexpr int SLOT = 64 * 4 + 4;                  // floats: a chunk + lane 31's right neighbour
+    static constexpr int SMEM = kWalkWarps * NS * SLOT * 4;  // dynamic shared memory per CTA
+    static_assert(NS >= 3, "the y sweep keeps two rows resident");
+};
+constexpr int kWalkSlots = 6;
+
+template <int LAYOUT, int AXIS, int NS>
+__global__ void __launch_bounds__(kWalkWarps * 32, 2)
+    euler_force_walk2d_kernel(const float* __restrict__ in, float* __restrict__ out, FieldCtl* __restrict__ ctl,
+                              const WalkGeom wg, const SweepParams prm)
+{
+    constexpr int NC = 4, SLOT = WalkCfg<NS>::SLOT;
+    const FieldGeom& g = wg.f;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
+    extern __shared__ __align__(128) float wsm[];
+    float* ring = wsm + warp * NS * SLOT;
+    __shared__ double sdt[4];
+    __shared__ double red[kWalkWarps];
+    if (tid == 0) {
+        // dt from the max wave-speed sum of the step's input state (FP64, as the tiled sweep)
+        const double dt = prm.cfl / __longlong_as_double((long long)ctl->smax[prm.slot_in]);
+        sdt[0] = dt;
+        sdt[1] = 0.5 * dt * prm.inv_dx[AXIS];
+        sdt[2] = 0.5 / (dt * prm.inv_dx[AXIS]);  // (dx/dt)/2
+        if (blockIdx.x == 0 && prm.last) {
+            ctl->t = prm.first ? dt : ctl->t + dt;
+            ctl->dt_last = dt;
+            ctl->smax[(prm.slot_in + 2) % 3] = 0ull;
+        }
+    }
+    __syncthreads();
+    const f2 gamma = splat<f2>((float)prm.gamma), gm1 = splat<f2>((float)(prm.gamma - 1.0));
+    const f2 hdt = splat<f2>((float)sdt[1]), hidt = splat<f2>((float)sdt[2]);
+    const float dtf = (float)sdt[0];
+    const f2 ndt = f2{-dtf, -dtf};
+    f2 ivx[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ivx[d] = splat<f2>((float)prm.inv_dx[d]);
+    const f2 iv = ivx[AXIS];
+    const int nx = g.n[0], ny = g.n[1];
+    const long long cs = g.comp_stride;
+    float smax_local = 0.f;
+    bool bad = false;
+
+    // Stage the chunk of 64 cells from x0 of the row whose x = 0 cell is the
+    // padded cell rb into slot s.  Slot layout: SoA component m at [64 m, 64 m
+    // + 64); AoS cell i at [4 i, 4 i + 4).  Whole chunks move as 16-byte
+    // copies, two per lane; a chunk past the last cell copies each lane's two
+    // cells with the index clamped to the ghost cell x = nx (never stored).
+    auto stage = [&](float* s, long long rb, int x0) {
+        if (x0 + 64 <= nx) {
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                const int i = lane + 32 * t;
+                if constexpr (LAYOUT == LAYOUT_SOA) {
+                    const int m = i >> 4, part = i & 15;
+                    cp_async16(s + 64 * m + 4 * part, in + rb + x0 + 4 * part + m * cs);
+                } else {
+                    cp_async16(s + 4 * i, in + (rb + x0 + i) * NC);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c = 2 * lane + h;
+                const long long src = rb + min(x0 + c, nx);
+                if constexpr (LAYOUT == LAYOUT_SOA) {
+#pragma unroll
+                    for (int m = 0; m < NC; ++m) cp_async4(s + 64 * m + c, in + src + m * cs);
+                } else {
+                    cp_async16(s + 4 * c, in + src * NC);
+                }
+            }
+        }
+    };
+    // lane 31: the cell after the chunk (the next chunk's first, or the ghost
+    // x = nx), components at [256, 260) of the slot
+    auto stage_next = [&](float* s, long long rb, int x0) {
+        if (lane != 31) return;
+        const long long src = rb + min(x0 + 64, nx);
+        if constexpr (LAYOUT == LAYOUT_SOA) {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) cp_async4(s + 256 + m, in + src + m * cs);
+        } else {
+            cp_async16(s + 256, in + src * NC);
+        }
+    };
+    // the lane's pair of cells (2 lane, 2 lane + 1) of a staged chunk
+    auto read_pair = [&](const float* s, f2 (&q)[NC]) {
+        if constexpr (LAYOUT == LAYOUT_SOA) {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) {
+                const float2 v = *reinterpret_cast<const float2*>(s + 64 * m + 2 * lane);
+                q[m] = f2{v.x, v.y};
+            }
+        } else {
+            const float4 A = *reinterpret_cast<const float4*>(s + 8 * lane);
+            const float4 B = *reinterpret_cast<const float4*>(s + 8 * lane + 4);
+            q[0] = f2{A.x, B.x}; q[1] = f2{A.y, B.y}; q[2] = f2{A.z, B.z}; q[3] = f2{A.w, B.w};
+        }
+    };
+    auto load_cell = [&](long long c, float (&v)[NC]) {
+        if constexpr (LAYOUT == LAYOUT_SOA) {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) v[m] = in[c + m * cs];
+        } else {
+            const float4 A = *reinterpret_cast<const float4*>(in + c * NC);
+            v[0] = A.x; v[1] = A.y; v[2] = A.z; v[3] = A.w;
+        }
+    };
+    // updated pair of cells (x, x + 1) of row y: checks, CFL maximum, store, ghost images
+    auto finish = [&](const f2 (&qn)[NC], long long c, int x, int y, bool v0, bool v1, bool near) {
+        bool ok0, ok1;
+        const f2 sw = wave_sum2<2>(qn, gamma, gm1, ivx, ok0, ok1);
+        smax_local = fmaxf(smax_local, fmaxf(v0 ? sw.x : 0.f, v1 ? sw.y : 0.f));
+        const bool b0 = v0 && !ok0, b1 = v1 && !ok1;
+        if (b0 || b1) {
+            bad = true;
+            record_bad(ctl, BAD_CELL, b0 ? x : x + 1, y, 0);
+        }
+        if (v0 && v1) {
+            if constexpr (LAYOUT == LAYOUT_SOA) {
+#pragma unroll
+                for (int m = 0; m < NC; ++m)
+                    *reinterpret_cast<float2*>(out + c + m * cs) = make_float2(qn[m].x, qn[m].y);
+            } else {
+                *reinterpret_cast<float4*>(out + c * NC) = make_float4(qn[0].x, qn[1].x, qn[2].x, qn[3].x);
+                *reinterpret_cast<float4*>(out + c * NC + NC) = make_float4(qn[0].y, qn[1].y, qn[2].y, qn[3].y);
+            }
+        } else if (v0) {
+#pragma unroll
+            for (int m = 0; m < NC; ++m) out[c * g.cell_stride + m * cs] = qn[m].x;
+        }
+        if (near) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (!(h == 0 ? v0 : v1)) continue;
+                float q1[NC];
+#pragma unroll
+                for (int m = 0; m < NC; ++m) q1[m] = h == 0 ? qn[m].x : qn[m].y;
+                write_ghost_images<float, 2>(out, g, prm.bc, x + h, y, 0, q1);
+            }
+        }
+    };
+
+    for (int w = blockIdx.x * kWalkWarps + warp; w < wg.walks; w += gridDim.x * kWalkWarps) {
+        float chk = 1.f;
+        int wx, wy;    // first cell of the walk (reported with a non-admissible face state)
+        __syncwarp();  // the previous walk's reads of the ring come before its refill
+        if constexpr (AXIS == 0) {
+            const int y = w / wg.nseg, xs = (w % wg.nseg) * wg.seg;
+            const int xe = min(xs + wg.seg, nx);
+            const int nch = (xe - xs + 63) >> 6;
+            const long long rb = (long long)(g.h + y) * g.px + g.lead + g.h;  // padded cell of x = 0
+            const bool row_near = y < g.h || y >= ny - g.h;
+            wx = xs;
+            wy = y;
+            // chunk k in slot k % NS, staged NS - 1 chunks ahead (one copy group per chunk)
+#pragma unroll
+            for (int k = 0; k < NS - 1; ++k) {
+                if (k < nch) {
+                    stage(ring + k * SLOT, rb, xs + 64 * k);
+                    stage_next(ring + k * SLOT, rb, xs + 64 * k);
+                }
+                cp_async_commit();
+            }
+            // face xs - 1/2, the left face of lane 0's first chunk (every lane the
+            // same), in the packed arithmetic of the walk before, which gives the
+            // same bits: the two walks agree on their common face exactly
+            float carry[NC];
+            {
+                float l[NC], r[NC];
+                load_cell(rb + xs - 1, l);
+                load_cell(rb + xs, r);
+                f2 a[NC], b[NC], F[NC];
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    a[m] = splat<f2>(l[m]);
+                    b[m] = splat<f2>(r[m]);
+                }
+                force<f2, 2, 0>(a, b, gm1, hdt, hidt, F, chk);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) carry[m] = F[m].x;
+            }
+            int slot = 0;  // slot of chunk k
+#pragma unroll 1
+            for (int k = 0; k < nch; ++k) {
+                const int x0 = xs + (k << 6), x = x0 + 2 * lane;
+                {
+                    // refill the slot read in the previous iteration with chunk k + NS - 1
+                    const int kn = k + NS - 1;
+                    float* s = ring + (slot == 0 ? NS - 1 : slot - 1) * SLOT;
+                    __syncwarp();
+                    if (kn < nch) {
+                        stage(s, rb, xs + 64 * kn);
+                        stage_next(s, rb, xs + 64 * kn);
+                    }
+                    cp_async_commit();
+                }
+                cp_async_wait<NS - 1>();  // chunk k's copies (this thread's) have landed
+                __syncwarp();             // ... and every lane's
+                const float* s = ring + slot * SLOT;
+                f2 q[NC], b[NC], Fr[NC], qn[NC];
+                read_pair(s, q);
+                // right faces of the lane's cells: (x | x + 1) and (x + 1 | x + 2)
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    float rn = __shfl_down_sync(0xffffffffu, q[m].x, 1);
+                    if (lane == 31) rn = s[256 + m];
+                    b[m] = f2{q[m].y, rn};
+                }
+                force<f2, 2, 0>(q, b, gm1, hdt, hidt, Fr, chk);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    float fl = __shfl_up_sync(0xffffffffu, Fr[m].y, 1);
+                    if (lane == 0) fl = carry[m];
+                    carry[m] = __shfl_sync(0xffffffffu, Fr[m].y, 31);
+                    qn[m] = fma_v(ndt, (Fr[m] - f2{fl, Fr[m].x}) * iv, q[m]);
+                }
+                finish(qn, rb + x, x, y, x < xe, x + 1 < xe, row_near || x0 < g.h || x0 + 64 > nx - g.h);
+                slot = slot == NS - 1 ? 0 : slot + 1;
+            }
+        } else {
+            const int strip = w % wg.nstrips, ys = (w / wg.nstrips) * wg.seg;
+            const int ye = min(ys + wg.seg, ny);
+            const int x0 = strip << 6, x = x0 + 2 * lane;
+            const bool v0 = x < nx, v1 = x + 1 < nx;
+            const bool col_near = x0 < g.h || x0 + 64 > nx - g.h;
+            const long long base = (long long)g.h * g.px + g.lead + g.h;  // padded cell of (0, 0)
+            wx = x0;
+            wy = ys;
+            // row ys - 1 + i in slot i % NS, i = 0 .. ye - ys + 1 (rows ys - 1 and ye
+            // are ghost rows at the field's edges), staged NS - 2 rows ahead
+            const int nrows = ye - ys + 2;
+#pragma unroll
+            for (int i = 0; i < NS - 1; ++i) {
+                if (i < nrows) stage(ring + i * SLOT, base + (long long)(ys - 1 + i) * g.px, x0);
+                cp_async_commit();
+            }
+            cp_async_wait<NS - 3>();  // rows ys - 1 and ys
+            __syncwarp();
+            f2 Fl[NC];  // face above row y
+            {
+                f2 up[NC], q0[NC];
+                read_pair(ring, up);
+                read_pair(ring + SLOT, q0);
+                force<f2, 2, 1>(up, q0, gm1, hdt, hidt, Fl, chk);
+            }
+            int slot = 1;  // slot of row y
+#pragma unroll 1
+            for (int y = ys; y < ye; ++y) {
+                const int i = y - ys + 1;
+                {
+                    // refill the slot of row i - 2 (read in the previous iteration) with row i + NS - 2
+                    const int ir = i + NS - 2;
+                    const int sr = slot >= 2 ? slot - 2 : slot + NS - 2;
+                    __syncwarp();
+                    if (ir < nrows) stage(ring + sr * SLOT, base + (long long)(ys - 1 + ir) * g.px, x0);
+                    cp_async_commit();
+                }
+                cp_async_wait<NS - 3>();  // rows y and y + 1
+                __syncwarp();
+                const int sn = slot == NS - 1 ? 0 : slot + 1;
+                f2 q[NC], qd[NC], Fr[NC], qn[NC];
+                read_pair(ring + slot * SLOT, q);
+                read_pair(ring + sn * SLOT, qd);
+                force<f2, 2, 1>(q, qd, gm1, hdt, hidt, Fr, chk);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) {
+                    qn[m] = fma_v(ndt, (Fr[m] - Fl[m]) * iv, q[m]);
+                    Fl[m] = Fr[m];
+                }
+                finish(qn, base + (long long)y * g.px + x, x, y, v0, v1, col_near || y < g.h || y >= ny - g.h);
+                slot = sn;
+            }
+        }
+        if (!(chk > 0.f)) {
+            bad = true;
+            record_bad(ctl, BAD_STATE, wx, wy, 0);
+        }
+    }
+    cp_async_wait<0>();
+
+    double v = (double)smax_local;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int any_bad = __syncthreads_or(bad ? 1 : 0);
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (tid == 0) {
+        double m = 0.0;
+        for (int k = 0; k < kWalkWarps; ++k) m = fmax(m, red[k]);
+        if (prm.last) atomic_max_pos_double(&ctl->smax[(prm.slot_in + 1) % 3], m);
+        if (any_bad) atomicOr(&ctl->err, DEV_ERR_NUMERIC);
+    }
+}
+
+}  // namespace ripple

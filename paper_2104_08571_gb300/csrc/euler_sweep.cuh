@@ -55,6 +55,15 @@ struct SweepGeom {
     int items;  // tiles_x * tiles_y * chunks_z
 };
 
+// Strip walks of a one-axis sweep (euler_force_walk.cuh): walk w covers `seg`
+// cells of row w / nseg from x = (w % nseg) * seg (x sweep), or `seg` rows of
+// the 64-column strip w % nstrips from y = (w / nstrips) * seg (y sweep).
+struct WalkGeom {
+    FieldGeom f;
+    int seg, nseg, nstrips, walks;
+};
+constexpr int kWalkWarps = 8;  // walks in flight per CTA (one per warp)
+
 struct SweepParams {
     double gamma, cfl;
     double inv_dx[3];

@@ -545,6 +545,34 @@ ripple_status ripple_field_describe(ripple_field f, ripple_field_desc* out)
     return RIPPLE_OK;
 }
 
+// Walks of a one-axis sweep of a 2D field (euler_force_walk.cuh): about 16 per
+// resident warp, so that the grid-stride walks spread evenly over the SMs, and
+// at least 4 chunks (x) or 16 rows (y) long, so that the first face of a walk
+// (evaluated by the walk before it too) stays a few per cent of the arithmetic.
+static WalkGeom walk_geom(const FieldGeom& g, int axis, long long resident_warps)
+{
+    WalkGeom w{};
+    w.f = g;
+    const long long target = std::max(1LL, 16 * resident_warps);
+    const long long nch = (g.n[0] + 63) / 64, ny = g.n[1];
+    if (axis == 0) {
+        long long cpw = nch * ny / target;
+        cpw = std::max(std::min(cpw, nch), std::min(4LL, nch));
+        w.seg = (int)(64 * cpw);
+        w.nseg = (int)((nch + cpw - 1) / cpw);
+        w.nstrips = 0;
+        w.walks = (int)(w.nseg * ny);
+    } else {
+        long long rows = nch * ny / target;
+        rows = std::max(std::min(rows, ny), std::min(16LL, ny));
+        w.seg = (int)rows;
+        w.nseg = (int)((ny + rows - 1) / rows);
+        w.nstrips = (int)nch;
+        w.walks = (int)(w.nseg * nch);
+    }
+    return w;
+}
+
 ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t nsteps, ripple_fv_stats* stats)
 {
     if (!U || !p) return fail(RIPPLE_ERR_INVALID, "NULL argument");
@@ -641,9 +669,35 @@ ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t 
     // one launch per step (unsplit), or one sweep per axis (split: x, then y, then z;
     // each sweep writes the ghost images its successor reads; all read the same dt)
     const int sweeps = split ? U->ndim : 1;
+    // the split step of a 2D FP32 field sweeps on strip walks (no tile staging)
+    const bool walk = split && U->ndim == 2 && U->dtype == RIPPLE_F32 && U->variant < 0;
+    WalkLaunch W[2]{};
+    if (walk) {
+        for (int a = 0; a < 2; ++a) {
+            const int wocc = force_walk_occ_f32_2d(layout, a);
+            if (wocc <= 0) return fail(RIPPLE_ERR_INTERNAL, "walk sweep kernel does not fit");
+            W[a].wg = walk_geom(g, a, (long long)wocc * ctx->sm_count * kWalkWarps);
+            W[a].grid = (int)std::min<long long>((W[a].wg.walks + kWalkWarps - 1) / kWalkWarps,
+                                                 (long long)wocc * ctx->sm_count);
+            W[a].ctl = U->ctl;
+            W[a].stream = s;
+            W[a].prm = L.prm;
+        }
+    }
     for (int64_t n = 0; n < nsteps; ++n) {
         for (int a = 0; a < sweeps; ++a) {
             const int in = U->cur, outb = 1 - U->cur;
+            if (walk) {
+                W[a].in = U->buf[in];
+                W[a].out = U->buf[outb];
+                W[a].prm.slot_in = (int)(U->steps_total % 3);
+                W[a].prm.first = n == 0;
+                W[a].prm.axis = a;
+                W[a].prm.last = a == sweeps - 1;
+                RIPPLE_CUDA(force_walk_launch_f32_2d(layout, a, W[a]));
+                U->cur = outb;
+                continue;
+            }
             L.map_in = field_map(U, in, 0, R, tx, ty, &st);
             if (!L.map_in) return st;
             L.map_out = field_map(U, outb, 1, R, tx, ty, &st);

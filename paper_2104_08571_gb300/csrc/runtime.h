@@ -67,6 +67,21 @@ int sweep_occ_f32_3d(int layout, int scheme, int v);
 int sweep_occ_f64_2d(int layout, int scheme, int v);
 int sweep_occ_f64_3d(int layout, int scheme, int v);
 
+// One sweep of the split FORCE step of a 2D FP32 field on strip walks
+// (euler_force_walk.cuh), along axis 0 or 1; defined with the 2D FP32 sweeps.
+struct WalkLaunch {
+    const void* in;
+    void* out;
+    FieldCtl* ctl;
+    WalkGeom wg;
+    SweepParams prm;
+    int grid;
+    cudaStream_t stream;
+};
+cudaError_t force_walk_launch_f32_2d(int layout, int axis, const WalkLaunch& L);
+// Resident CTAs per SM of the walk kernel (0 on error).
+int force_walk_occ_f32_2d(int layout, int axis);
+
 // Aux kernels (f32/f64 x 2D/3D), defined in aux.cu.
 cudaError_t launch_prep(int dtype, int dim, void* buf, FieldCtl* ctl, const FieldGeom& g, int bc, double gamma,
                         const double inv_dx[3], int slot, int grid, cudaStream_t s);

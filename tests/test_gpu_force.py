@@ -61,6 +61,26 @@ def test_force_split_parity(ctx, dims, dtype, bc, layout):
     assert rel_l1(got, ref) <= tol
 
 
+_LONG_WALK_REF = {}
+
+
+@pytest.mark.parametrize("layout", [R.RIPPLE_SOA, R.RIPPLE_AOS])
+@pytest.mark.parametrize("bc", [R.RIPPLE_BC_PERIODIC, R.RIPPLE_BC_TRANSMISSIVE])
+def test_force_split_fp32_2d_long_walks(ctx, layout, bc):
+    """2D FP32 split sweeps run on strip walks: on a 2000 x 1500 grid a walk
+    spans several 64-cell chunks (faces carried from chunk to chunk), rows and
+    strips are cut into several walks, and the last chunk and segment are
+    ragged."""
+    dims = (2000, 1500)
+    U0 = _random_state(dims, seed=11, amp=0.3).astype(np.float32).astype(np.float64)
+    if bc not in _LONG_WALK_REF:
+        _LONG_WALK_REF[bc] = oracle.euler_run(U0, 3, scheme=oracle.FORCE_SPLIT, bc=bc)
+    ref, info = _LONG_WALK_REF[bc]
+    got, st = gpu_euler(ctx, U0, 3, dtype=R.RIPPLE_F32, layout=layout, scheme=FORCE, bc=bc)
+    assert rel_l1(got, ref) <= 2e-5
+    assert st["t"] == pytest.approx(info["t"], rel=1e-5)
+
+
 @pytest.mark.parametrize("ndim,dims", [(2, (40, 21)), (3, (18, 9, 12))])
 @pytest.mark.parametrize("dtype", [R.RIPPLE_F64, R.RIPPLE_F32])
 def test_force_split_uniform_state_bit_exact(ctx, ndim, dims, dtype):
