@@ -433,7 +433,7 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
     }
 
 
-def bench_force_split(R, torch, local, par=None):
+def bench_force_split(R, torch, local, par=None, legs=None):
     """The paper's own Euler solver (dimensionally split x then y sweeps, FORCE
     face flux): 2D FP32 8192^2 periodic sine density (a Table flux size), and
     the 2D FP64 128^2 workload.  One step = one sweep per axis."""
@@ -443,7 +443,9 @@ def bench_force_split(R, torch, local, par=None):
     R.ripple_set_stream(ctx, stream)
     out = {}
     try:
-        for name, n, dtype, steps in (("fp32_8192", 8192, R.RIPPLE_F32, 20), ("fp64_128", 128, R.RIPPLE_F64, 100)):
+        if legs is None:
+            legs = (("fp32_8192", 8192, R.RIPPLE_F32, 20), ("fp64_128", 128, R.RIPPLE_F64, 100))
+        for name, n, dtype, steps in legs:
             npdt = np.float32 if dtype == R.RIPPLE_F32 else np.float64
             U0 = inputs.euler2d_sine(n).astype(npdt)
             f = R.ripple_field_create(ctx, (n, n), 4, R.RIPPLE_SOA, 1, dtype)
@@ -717,6 +719,9 @@ def main():
     ap.add_argument("--sweep-only", action="store_true",
                     help="time only the SoA sweep (a small case for profiling; not the headline line)")
     ap.add_argument("--sweep-dims", type=int, nargs=3, default=[N3, N3, N3], metavar=("NX", "NY", "NZ"))
+    ap.add_argument("--force-only", action="store_true",
+                    help="time only the split FORCE step, 2D FP32 SoA (profiling; not the headline line)")
+    ap.add_argument("--force-n", type=int, default=8192)
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 512-instance batched workload (profiling; not the headline line)")
     args = ap.parse_args()
@@ -757,6 +762,16 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.force_only:
+        import torch
+        import paper_2104_08571_gb300 as R
+        torch.cuda.set_device(local)
+        fs = bench_force_split(R, torch, local, legs=(("fp32", args.force_n, R.RIPPLE_F32, args.steps),))
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": fs["fp32"]["cell_updates_per_s"], "unit": METRIC,
+                              "n_gpus": world, "config": {"workload": f"force_split_2d_fp32_{args.force_n}^2_sine"},
+                              "force_split": fs}))
+        return
     if args.batched_only:
         import torch
         import paper_2104_08571_gb300 as R

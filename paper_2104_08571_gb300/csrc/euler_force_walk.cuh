@@ -56,14 +56,15 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
     const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
     extern __shared__ __align__(128) float wsm[];
     float* ring = wsm + warp * NS * SLOT;
-    __shared__ double sdt[4];
+    __shared__ float sdt[4];
     __shared__ double red[kWalkWarps];
     if (tid == 0) {
-        // dt from the max wave-speed sum of the step's input state (FP64, as the tiled sweep)
+        // dt from the max wave-speed sum of the step's input state (FP64, as the
+        // tiled sweep); its FP32 forms rounded here once
         const double dt = prm.cfl / __longlong_as_double((long long)ctl->smax[prm.slot_in]);
-        sdt[0] = dt;
-        sdt[1] = 0.5 * dt * prm.inv_dx[AXIS];
-        sdt[2] = 0.5 / (dt * prm.inv_dx[AXIS]);  // (dx/dt)/2
+        sdt[0] = (float)dt;
+        sdt[1] = (float)(0.5 * dt * prm.inv_dx[AXIS]);
+        sdt[2] = (float)(0.5 / (dt * prm.inv_dx[AXIS]));  // (dx/dt)/2
         if (blockIdx.x == 0 && prm.last) {
             ctl->t = prm.first ? dt : ctl->t + dt;
             ctl->dt_last = dt;
@@ -71,13 +72,13 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
         }
     }
     __syncthreads();
-    const f2 gamma = splat<f2>((float)prm.gamma), gm1 = splat<f2>((float)(prm.gamma - 1.0));
-    const f2 hdt = splat<f2>((float)sdt[1]), hidt = splat<f2>((float)sdt[2]);
-    const float dtf = (float)sdt[0];
+    const f2 gamma = splat<f2>(prm.gamma_f), gm1 = splat<f2>(prm.gm1_f);
+    const f2 hdt = splat<f2>(sdt[1]), hidt = splat<f2>(sdt[2]);
+    const float dtf = sdt[0];
     const f2 ndt = f2{-dtf, -dtf};
     f2 ivx[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) ivx[d] = splat<f2>((float)prm.inv_dx[d]);
+    for (int d = 0; d < 3; ++d) ivx[d] = splat<f2>(prm.inv_dx_f[d]);
     const f2 iv = ivx[AXIS];
     const int nx = g.n[0], ny = g.n[1];
     const long long cs = g.comp_stride;

@@ -72,6 +72,12 @@ struct SweepParams {
     int first;    // first step of a call: t = dt instead of t += dt
     int axis;     // -1: all axes (the unsplit step); 0/1/2: one sweep of a split step along that axis
     int last;     // this launch completes the step: advance t, reduce the new wave speeds
+    // FP32 copies of gamma, gamma - 1 and 1/dx, rounded once on the host: FP32
+    // kernels read them as constant operands instead of converting the FP64
+    // values on the device (a conversion runs on the narrow FP64 pipe, and the
+    // compiler may repeat it wherever it rematerialises the value)
+    float gamma_f, gm1_f;
+    float inv_dx_f[3];
 };
 
 // ---------------------------------------------------------------------------

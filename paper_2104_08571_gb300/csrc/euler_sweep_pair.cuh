@@ -151,14 +151,15 @@ __global__ void __launch_bounds__(256, PairCfg<DIM, LAYOUT, SCHEME>::MIN_CTAS)
         }
     }
 
-    double* sdt = reinterpret_cast<double*>(smem + 256);  // step scalars formed by thread 0
+    // step scalars formed by thread 0 in FP64 and rounded to FP32 once
+    float* sdt = reinterpret_cast<float*>(smem + 256);
     if (tid == 0) {
         // dt from the max wave-speed sum of the input state, in FP64 once per CTA
         const double dt = prm.cfl / __longlong_as_double((long long)ctl->smax[prm.slot_in]);
-        sdt[0] = dt;
+        sdt[0] = (float)dt;
         for (int d = 0; d < 3; ++d) {
-            sdt[1 + d] = 0.5 * dt * prm.inv_dx[d];
-            sdt[4 + d] = prm.inv_dx[d] > 0.0 ? 0.5 / (dt * prm.inv_dx[d]) : 0.0;  // (dx/dt)/2 (FORCE)
+            sdt[1 + d] = (float)(0.5 * dt * prm.inv_dx[d]);
+            sdt[4 + d] = prm.inv_dx[d] > 0.0 ? (float)(0.5 / (dt * prm.inv_dx[d])) : 0.f;  // (dx/dt)/2 (FORCE)
         }
         if (blockIdx.x == 0 && prm.last) {
             ctl->t = prm.first ? dt : ctl->t + dt;
@@ -172,14 +173,14 @@ __global__ void __launch_bounds__(256, PairCfg<DIM, LAYOUT, SCHEME>::MIN_CTAS)
         prefetch_tensormap(&map_out);
     }
     __syncthreads();
-    const f2 gamma = splat<f2>((float)prm.gamma), gm1 = splat<f2>((float)(prm.gamma - 1.0));
-    const f2 dtv = splat<f2>((float)sdt[0]);
+    const f2 gamma = splat<f2>(prm.gamma_f), gm1 = splat<f2>(prm.gm1_f);
+    const f2 dtv = splat<f2>(sdt[0]);
     f2 inv_dx[3], half_dtdx[3], half_inv_dtdx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        inv_dx[d] = splat<f2>((float)prm.inv_dx[d]);
-        half_dtdx[d] = splat<f2>((float)sdt[1 + d]);
-        half_inv_dtdx[d] = splat<f2>((float)sdt[4 + d]);
+        inv_dx[d] = splat<f2>(prm.inv_dx_f[d]);
+        half_dtdx[d] = splat<f2>(sdt[1 + d]);
+        half_inv_dtdx[d] = splat<f2>(sdt[4 + d]);
     }
     // axes of this launch: all (unsplit step) or one sweep of the split step
     const bool ax0 = prm.axis < 0 || prm.axis == 0;

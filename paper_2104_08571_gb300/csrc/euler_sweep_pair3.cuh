@@ -119,11 +119,12 @@ __global__ void __launch_bounds__(256, 2)
         return warp == 4 ? 96 : 128;
     };
 
-    double* sdt = reinterpret_cast<double*>(smem + 256);  // step scalars formed by thread 0
+    // step scalars formed by thread 0 in FP64 and rounded to FP32 once
+    float* sdt = reinterpret_cast<float*>(smem + 256);
     if (tid == 0) {
         const double dt = prm.cfl / __longlong_as_double((long long)ctl->smax[prm.slot_in]);
-        sdt[0] = dt;
-        for (int d = 0; d < 3; ++d) sdt[1 + d] = 0.5 * dt * prm.inv_dx[d];
+        sdt[0] = (float)dt;
+        for (int d = 0; d < 3; ++d) sdt[1 + d] = (float)(0.5 * dt * prm.inv_dx[d]);
         if (blockIdx.x == 0) {
             ctl->t = prm.first ? dt : ctl->t + dt;
             ctl->dt_last = dt;
@@ -135,13 +136,13 @@ __global__ void __launch_bounds__(256, 2)
         prefetch_tensormap(&map_in);
     }
     __syncthreads();
-    const f2 gamma = splat<f2>((float)prm.gamma), gm1 = splat<f2>((float)(prm.gamma - 1.0));
-    const f2 dtv = splat<f2>((float)sdt[0]);
+    const f2 gamma = splat<f2>(prm.gamma_f), gm1 = splat<f2>(prm.gm1_f);
+    const f2 dtv = splat<f2>(sdt[0]);
     f2 inv_dx[3], half_dtdx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        inv_dx[d] = splat<f2>((float)prm.inv_dx[d]);
-        half_dtdx[d] = splat<f2>((float)sdt[1 + d]);
+        inv_dx[d] = splat<f2>(prm.inv_dx_f[d]);
+        half_dtdx[d] = splat<f2>(sdt[1 + d]);
     }
 
     // ---- TMA ring (thread 0): planes of the CTA's items in order ----

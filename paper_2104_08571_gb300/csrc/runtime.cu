@@ -664,6 +664,9 @@ ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t 
     L.prm.gamma = p->gamma;
     L.prm.cfl = p->cfl;
     for (int d = 0; d < 3; ++d) L.prm.inv_dx[d] = inv_dx[d];
+    L.prm.gamma_f = (float)p->gamma;
+    L.prm.gm1_f = (float)(p->gamma - 1.0);
+    for (int d = 0; d < 3; ++d) L.prm.inv_dx_f[d] = (float)inv_dx[d];
     L.prm.bc = (int)p->bc;
 
     // one launch per step (unsplit), or one sweep per axis (split: x, then y, then z;
