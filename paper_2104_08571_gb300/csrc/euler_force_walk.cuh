@@ -19,11 +19,15 @@
 // that this stays a few per cent of the arithmetic).
 //
 // Staging: every warp owns a ring of NS shared-memory slots of one chunk
-// (1 KB) each, filled by per-thread asynchronous copies (cp.async, 16 bytes
-// per copy for whole chunks) NS - 1 chunks (x) or NS - 2 rows (y) ahead of
-// the arithmetic, so the loads in flight cost no registers.  A thread waits
-// for its own copy groups only and __syncwarp publishes the lanes' copies to
-// each other, so no wait can hang and no CTA barrier is needed.  Stores are
+// (1 KB) each, filled by per-thread asynchronous copies (cp.async) NS - 1
+// chunks (x) or NS - 2 rows (y) ahead of the arithmetic, so the loads in
+// flight cost no registers.  A thread waits for its own copy groups only
+// (cp.async.wait_group), so no wait can hang, and no CTA barrier is needed.
+// AoS lanes copy exactly the cells they read (two 16-byte cells); SoA chunks
+// move as 16-byte copies that span two lanes' pairs (half the copies of
+// per-lane 8-byte ones, measured 2 % faster), so there __syncwarp publishes
+// the lanes' copies to each other and ends their reads of a slot before it
+// is refilled (AoS without the barrier: 1 % faster).  Stores are
 // coalesced and direct.  dt, t and the CFL maximum follow the tiled sweep: dt
 // from the wave-speed maximum of the step's input state; the last sweep of a
 // step advances t and reduces the maximum of the new state.  Cells on the
@@ -87,20 +91,23 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
 
     // Stage the chunk of 64 cells from x0 of the row whose x = 0 cell is the
     // padded cell rb into slot s.  Slot layout: SoA component m at [64 m, 64 m
-    // + 64); AoS cell i at [4 i, 4 i + 4).  Whole chunks move as 16-byte
-    // copies, two per lane; a chunk past the last cell copies each lane's two
-    // cells with the index clamped to the ghost cell x = nx (never stored).
+    // + 64); AoS cell i at [4 i, 4 i + 4).  A whole chunk moves as 16-byte
+    // copies, two per lane, coalesced across the warp (SoA: 16 lanes per
+    // component row; AoS: the lane's own two cells); a chunk past the last
+    // cell copies each lane's two cells with the index clamped to the ghost
+    // cell x = nx (never stored).
     auto stage = [&](float* s, long long rb, int x0) {
         if (x0 + 64 <= nx) {
+            if constexpr (LAYOUT == LAYOUT_SOA) {
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                const int i = lane + 32 * t;
-                if constexpr (LAYOUT == LAYOUT_SOA) {
-                    const int m = i >> 4, part = i & 15;
+                for (int t = 0; t < 2; ++t) {
+                    const int i = lane + 32 * t, m = i >> 4, part = i & 15;
                     cp_async16(s + 64 * m + 4 * part, in + rb + x0 + 4 * part + m * cs);
-                } else {
-                    cp_async16(s + 4 * i, in + (rb + x0 + i) * NC);
                 }
+            } else {
+                const long long c = rb + x0 + 2 * lane;
+                cp_async16(s + 8 * lane, in + c * NC);
+                cp_async16(s + 8 * lane + 4, in + (c + 1) * NC);
             }
         } else {
 #pragma unroll
@@ -127,6 +134,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
         } else {
             cp_async16(s + 256, in + src * NC);
         }
+    };
+    // SoA lanes read cells that other lanes copied (see above)
+    auto ring_sync = [&]() {
+        if constexpr (LAYOUT == LAYOUT_SOA) __syncwarp();
     };
     // the lane's pair of cells (2 lane, 2 lane + 1) of a staged chunk
     auto read_pair = [&](const float* s, f2 (&q)[NC]) {
@@ -188,8 +199,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
 
     for (int w = blockIdx.x * kWalkWarps + warp; w < wg.walks; w += gridDim.x * kWalkWarps) {
         float chk = 1.f;
-        int wx, wy;    // first cell of the walk (reported with a non-admissible face state)
-        __syncwarp();  // the previous walk's reads of the ring come before its refill
+        int wx, wy;   // first cell of the walk (reported with a non-admissible face state)
+        ring_sync();  // the previous walk's reads of the ring come before its refill
         if constexpr (AXIS == 0) {
             const int y = w / wg.nseg, xs = (w % wg.nseg) * wg.seg;
             const int xe = min(xs + wg.seg, nx);
@@ -233,15 +244,15 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
                     // refill the slot read in the previous iteration with chunk k + NS - 1
                     const int kn = k + NS - 1;
                     float* s = ring + (slot == 0 ? NS - 1 : slot - 1) * SLOT;
-                    __syncwarp();
+                    ring_sync();
                     if (kn < nch) {
                         stage(s, rb, xs + 64 * kn);
                         stage_next(s, rb, xs + 64 * kn);
                     }
                     cp_async_commit();
                 }
-                cp_async_wait<NS - 1>();  // chunk k's copies (this thread's) have landed
-                __syncwarp();             // ... and every lane's
+                cp_async_wait<NS - 1>();  // chunk k has landed
+                ring_sync();
                 const float* s = ring + slot * SLOT;
                 f2 q[NC], b[NC], Fr[NC], qn[NC];
                 read_pair(s, q);
@@ -281,7 +292,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
                 cp_async_commit();
             }
             cp_async_wait<NS - 3>();  // rows ys - 1 and ys
-            __syncwarp();
+            ring_sync();
             f2 Fl[NC];  // face above row y
             {
                 f2 up[NC], q0[NC];
@@ -297,12 +308,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
                     // refill the slot of row i - 2 (read in the previous iteration) with row i + NS - 2
                     const int ir = i + NS - 2;
                     const int sr = slot >= 2 ? slot - 2 : slot + NS - 2;
-                    __syncwarp();
+                    ring_sync();
                     if (ir < nrows) stage(ring + sr * SLOT, base + (long long)(ys - 1 + ir) * g.px, x0);
                     cp_async_commit();
                 }
                 cp_async_wait<NS - 3>();  // rows y and y + 1
-                __syncwarp();
+                ring_sync();
                 const int sn = slot == NS - 1 ? 0 : slot + 1;
                 f2 q[NC], qd[NC], Fr[NC], qn[NC];
                 read_pair(ring + slot * SLOT, q);
