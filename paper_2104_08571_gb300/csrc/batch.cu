@@ -527,6 +527,10 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
             e.cfl = in->req.fv.cfl;
             e.inv_dx0 = 1.0 / in->req.fv.dx[0];
             e.inv_dx1 = 1.0 / in->req.fv.dx[1];
+            e.gamma_f = (float)e.gamma;
+            e.gm1_f = (float)e.gm1;
+            e.inv_dx0_f = (float)e.inv_dx0;
+            e.inv_dx1_f = (float)e.inv_dx1;
             const int key = rt->cfg.tile_variant * 2 + (rt->cfg.layout == RIPPLE_SOA ? 1 : 0);
             if (in->map_key != key) {
                 st = encode_batch_maps(e, rt->cfg.layout, rt->cfg.dtype, rt->cfg.tile_variant);
@@ -1023,6 +1027,9 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
                 h[i].gm1 = 1.4 - 1.0;
                 h[i].cfl = 0.4;
                 h[i].inv_dx0 = h[i].inv_dx1 = (double)sides[i];
+                h[i].gamma_f = (float)h[i].gamma;
+                h[i].gm1_f = (float)h[i].gm1;
+                h[i].inv_dx0_f = h[i].inv_dx1_f = (float)h[i].inv_dx0;
                 if (status == RIPPLE_OK) status = encode_batch_maps(h[i], lay, dt, v);
                 const int nt = h[i].tiles_x * (int)((sides[i] + ty - 1) / ty);
                 for (int k = 0; k < nt; ++k) table.push_back(i << 1);

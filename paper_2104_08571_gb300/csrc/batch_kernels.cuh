@@ -34,7 +34,17 @@ struct BatchEuler {  // aligned as CUtensorMap (at least 64 bytes)
     int bc;
     long long start_step, nsteps;
     double gamma, gm1, cfl, inv_dx0, inv_dx1;  // gm1 = gamma - 1, formed on the host in FP64
+    float gamma_f, gm1_f, inv_dx0_f, inv_dx1_f;  // the same rounded to FP32 on the host
 };
+
+// A descriptor constant in the field precision: FP32 kernels take the
+// host-rounded copy (no conversion on the device's narrow FP64 pipe).
+template <typename T>
+__device__ __forceinline__ T field_const(double v, float vf)
+{
+    if constexpr (std::is_same<T, float>::value) return vf;
+    else return v;
+}
 
 // One resident 2D eikonal instance.
 template <typename T>
@@ -218,6 +228,11 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
             // dependency-driven round: the current chunk of tasks [c_lo, c_hi), the
             // cached task range [s_lo, s_hi) of round step s_n, the last dependency met
             int c_lo = 0, c_hi = 0, s_lo = 0, s_hi = 0, s_n = 0, dep_inst = -1, dep_n = -1;
+            // dt of the last (instance, step) a tile was issued for
+            int dt_inst = -1;
+            long long dt_local = -1;
+            double dt = 0.0;
+            T dtT = T(0);
             for (int t = blockIdx.x;; t += gridDim.x) {
                 const BatchEuler* d = nullptr;
                 long long local = 0;
@@ -287,15 +302,21 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
                 const int x0 = (lt % d->tiles_x) * TX, y0 = (lt / d->tiles_x) * TY;
                 const int rs = (int)(local % 3);
                 FieldCtl* ctl = d->ctl;
-                const double dt = d->cfl / __longlong_as_double((long long)__ldcg(&ctl->smax[rs]));
+                if (inst != dt_inst || local != dt_local) {
+                    // dt once per (instance, step) run of tiles: an FP64 division
+                    dt_inst = inst;
+                    dt_local = local;
+                    dt = d->cfl / __longlong_as_double((long long)__ldcg(&ctl->smax[rs]));
+                    dtT = (T)dt;
+                }
                 h->g = d->g;
                 h->out = static_cast<T*>(d->buf[(local & 1) ^ 1]);
                 h->ctl = ctl;
-                h->gamma = (T)d->gamma;
-                h->gm1 = (T)d->gm1;
-                h->inv_dx0 = (T)d->inv_dx0;
-                h->inv_dx1 = (T)d->inv_dx1;
-                h->dt = (T)dt;
+                h->gamma = field_const<T>(d->gamma, d->gamma_f);
+                h->gm1 = field_const<T>(d->gm1, d->gm1_f);
+                h->inv_dx0 = field_const<T>(d->inv_dx0, d->inv_dx0_f);
+                h->inv_dx1 = field_const<T>(d->inv_dx1, d->inv_dx1_f);
+                h->dt = dtT;
                 h->tile = t;
                 h->x0 = x0;
                 h->y0 = y0;
@@ -546,10 +567,10 @@ __global__ void __launch_bounds__(256) batch_euler_direct_kernel(const BatchEule
         }
         if (tid == 0) {
             const double dt = d.cfl / __longlong_as_double((long long)__ldcg(&ctl->smax[rs]));
-            sp[0] = (T)d.gamma;
-            sp[1] = (T)d.gm1;
-            sp[2] = (T)d.inv_dx0;
-            sp[3] = (T)d.inv_dx1;
+            sp[0] = field_const<T>(d.gamma, d.gamma_f);
+            sp[1] = field_const<T>(d.gm1, d.gm1_f);
+            sp[2] = field_const<T>(d.inv_dx0, d.inv_dx0_f);
+            sp[3] = field_const<T>(d.inv_dx1, d.inv_dx1_f);
             sp[4] = (T)dt;
             if (lt == 0) {
                 ctl->t = local == 0 ? dt : ctl->t + dt;
