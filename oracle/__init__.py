@@ -21,6 +21,12 @@ Parity status of each function (what pins it, see ``tests/test_oracle_*.py``):
       2D == 3D reduction.  The 3D spherical blast itself has no closed form
       (its parity beyond oracle agreement is unpinned; only the invariants
       above and conservation before waves reach the boundary pin it).
+  euler_run with FORCE_SPLIT (the split step with the FORCE flux) -- pinned:
+      uniform state bit-exact, periodic conservation, the advected sine
+      density keeping u, v, p uniform with first-order convergence, on a
+      contact the mass update equal to the mean of the Lax-Friedrichs and
+      Lax-Wendroff updates at the same Courant number, Sod L1 error
+      shrinking under refinement, 1-D Sod along x, y, z bit-identical.
   eikonal_fmm -- pinned: exact k*h on 1-D strips and grid axes, |x - x0|
       under refinement, equality with Jacobi iteration to its fixed point,
       and the 4-neighbour graph-Dijkstra upper bound.
