@@ -5,9 +5,10 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 this package.  It shares no code with the CUDA library in
 ``paper_2104_08571_gb300`` and never imports it.
 
-The arithmetic lives in ``ripple_oracle.c`` (plain C, double precision, one
-thread, ``-ffp-contract=off``); this module only compiles it (``build()``) and
-marshals numpy arrays through ctypes.
+The arithmetic lives in ``ripple_oracle.c`` (plain C, double precision,
+``-ffp-contract=off``; one thread unless ``set_threads`` splits the independent
+grid lines of an Euler step, which changes no bit of a result); this module
+only compiles it (``build()``) and marshals numpy arrays through ctypes.
 
 Array convention: interior cells only, component-major, x fastest, i.e. a
 numpy array of shape ``(ncomp, nz, ny, nx)`` (3D) or ``(ncomp, ny, nx)`` (2D)
@@ -71,9 +72,12 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-           "-shared", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+            "-shared", "-o", tmp, _SRC, "-lm"]
+    # OpenMP only splits independent lines of a step over threads; without it
+    # the oracle is the same single-threaded program
+    if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+        subprocess.run(base, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -101,6 +105,10 @@ def _load():
         lib.oracle_eikonal_fmm.restype = ctypes.c_int
         lib.oracle_godunov.argtypes = [ctypes.c_int, dp, ctypes.c_double]
         lib.oracle_godunov.restype = ctypes.c_double
+        lib.oracle_set_threads.argtypes = [ctypes.c_int]
+        lib.oracle_set_threads.restype = ctypes.c_int
+        lib.oracle_threads.argtypes = []
+        lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -209,8 +217,15 @@ def godunov(a, f):
 
 
 def threads_used() -> int:
-    """The oracle is single-threaded."""
-    return 1
+    """Threads the Euler steps run on (1 unless set_threads was called)."""
+    return int(_load().oracle_threads())
+
+
+def set_threads(n: int) -> int:
+    """Let the Euler steps split their independent grid lines over n threads
+    (results are bitwise the same for any n); returns the count in effect
+    (1 if the oracle was built without OpenMP)."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 if __name__ == "__main__":  # pragma: no cover

@@ -6,8 +6,12 @@
  * leg (and bench.py --impl reference) use it.  It shares no code, header,
  * table or helper with the CUDA library.
  *
- * Plain, slow, obviously correct: double precision, scalar loops, one thread,
- * compiled with -ffp-contract=off so that x86-64 and aarch64 give identical bits.
+ * Plain, slow, obviously correct: double precision, scalar loops, compiled
+ * with -ffp-contract=off so that x86-64 and aarch64 give identical bits.  One
+ * thread by default; oracle_set_threads(n) lets OpenMP split the independent
+ * grid lines (and cells) of an Euler step over n threads.  Every cell's value
+ * is computed by the same operations in the same order whatever the thread
+ * count, and a maximum is exact, so the results do not depend on it.
  *
  * What it computes
  *  - Euler (2D/3D, conserved variables (rho, rho*u_1..rho*u_d, E), ideal gas):
@@ -42,6 +46,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORACLE_OK 0
 #define ORACLE_INVALID 1
@@ -307,19 +314,28 @@ static int max_wavespeed(const grid_t* g, const double* U, int ncomp, double gam
 {
     int ndim = ncomp - 2;
     double best = 0.0;
-    int64_t c[3] = {0, 0, 0};
-    for (c[2] = 0; c[2] < g->n[2]; c[2]++)
+    int ok = 1;
+    /* cells are independent and a maximum does not depend on the order in
+       which it is taken, so the planes may be split over threads */
+#pragma omp parallel for schedule(static) reduction(max : best) reduction(&& : ok)
+    for (int64_t k = 0; k < g->n[2]; k++) {
+        int64_t c[3] = {0, 0, k};
         for (c[1] = 0; c[1] < g->n[1]; c[1]++)
             for (c[0] = 0; c[0] < g->n[0]; c[0]++) {
                 double q[MAXC], rho, u[3], p;
                 load_cell(g, U, ncomp, c, q);
                 primitives(ndim, q, gamma, &rho, u, &p);
-                if (!admissible(rho, p)) return 0;
+                if (!admissible(rho, p)) {
+                    ok = 0;
+                    continue;
+                }
                 double cs = sqrt(gamma * p / rho);
                 double s = 0.0;
                 for (int d = 0; d < ndim; d++) s += (fabs(u[d]) + cs) / dx[d];
                 if (s > best) best = s;
             }
+    }
+    if (!ok) return 0;
     *smax = best;
     return 1;
 }
@@ -367,46 +383,48 @@ static int euler_step(const grid_t* g, double* U, double* Unew, int ncomp, doubl
     int64_t nmax = g->n[0];
     if (g->n[1] > nmax) nmax = g->n[1];
     if (g->n[2] > nmax) nmax = g->n[2];
-    double* line = (double*)malloc(sizeof(double) * (size_t)((nmax + 1) * ncomp));
-    if (!acc || !line) {
-        free(acc);
-        free(line);
-        return ORACLE_OOM;
-    }
+    if (!acc) return ORACLE_OOM;
     int status = ORACLE_OK;
     for (int d = 0; d < g->ndim && status == ORACLE_OK; d++) {
-        /* iterate over all grid lines along axis d */
-        int64_t c[3] = {0, 0, 0};
+        /* all grid lines along axis d; a line writes only its own cells of
+           acc, so lines may run on different threads without changing a bit */
         int64_t ext[3] = {g->n[0], g->n[1], g->n[2]};
         ext[d] = 1;
-        for (int64_t b2 = 0; b2 < ext[2] && status == ORACLE_OK; b2++)
-            for (int64_t b1 = 0; b1 < ext[1] && status == ORACLE_OK; b1++)
-                for (int64_t b0 = 0; b0 < ext[0] && status == ORACLE_OK; b0++) {
-                    c[0] = b0;
-                    c[1] = b1;
-                    c[2] = b2;
-                    /* faces between cells f-1 and f for f = 0..n_d; slot f */
-                    for (int64_t f = 0; f <= g->n[d]; f++) {
-                        c[d] = f - 1;
-                        if (!face_flux(g, U, ncomp, d, c, dt / dx[d], scheme, gamma,
-                                       line + f * ncomp)) {
-                            status = ORACLE_NUMERIC;
-                            break;
-                        }
-                    }
-                    for (int64_t i = 0; i < g->n[d] && status == ORACLE_OK; i++) {
-                        c[d] = i;
-                        int64_t lin = (c[2] * g->n[1] + c[1]) * g->n[0] + c[0];
-                        for (int m = 0; m < ncomp; m++)
-                            acc[m * nint + lin] +=
-                                (line[(i + 1) * ncomp + m] - line[i * ncomp + m]) / dx[d];
+        int64_t nlines = ext[0] * ext[1] * ext[2];
+        int bad = 0, oom = 0;
+#pragma omp parallel reduction(|| : bad, oom)
+        {
+            double* line = (double*)malloc(sizeof(double) * (size_t)((nmax + 1) * ncomp));
+            if (!line) oom = 1;
+#pragma omp for schedule(static)
+            for (int64_t l = 0; l < nlines; l++) {
+                if (!line || bad) continue;
+                int64_t c[3] = {l % ext[0], (l / ext[0]) % ext[1], l / (ext[0] * ext[1])};
+                /* faces between cells f-1 and f for f = 0..n_d; slot f */
+                for (int64_t f = 0; f <= g->n[d]; f++) {
+                    c[d] = f - 1;
+                    if (!face_flux(g, U, ncomp, d, c, dt / dx[d], scheme, gamma, line + f * ncomp)) {
+                        bad = 1;
+                        break;
                     }
                 }
+                for (int64_t i = 0; i < g->n[d] && !bad; i++) {
+                    c[d] = i;
+                    int64_t lin = (c[2] * g->n[1] + c[1]) * g->n[0] + c[0];
+                    for (int m = 0; m < ncomp; m++)
+                        acc[m * nint + lin] += (line[(i + 1) * ncomp + m] - line[i * ncomp + m]) / dx[d];
+                }
+            }
+            free(line);
+        }
+        if (oom) status = ORACLE_OOM;
+        else if (bad) status = ORACLE_NUMERIC;
     }
     if (status == ORACLE_OK) {
         memcpy(Unew, U, sizeof(double) * (size_t)(g->ncell * ncomp));
-        int64_t c[3] = {0, 0, 0};
-        for (c[2] = 0; c[2] < g->n[2]; c[2]++)
+#pragma omp parallel for schedule(static)
+        for (int64_t k = 0; k < g->n[2]; k++) {
+            int64_t c[3] = {0, 0, k};
             for (c[1] = 0; c[1] < g->n[1]; c[1]++)
                 for (c[0] = 0; c[0] < g->n[0]; c[0]++) {
                     int64_t id = pidx(g, c);
@@ -414,9 +432,9 @@ static int euler_step(const grid_t* g, double* U, double* Unew, int ncomp, doubl
                     for (int m = 0; m < ncomp; m++)
                         Unew[m * g->ncell + id] = U[m * g->ncell + id] - dt * acc[m * nint + lin];
                 }
+        }
     }
     free(acc);
-    free(line);
     if (dt_out) *dt_out = dt;
     return status;
 }
@@ -441,52 +459,57 @@ static int euler_split_step(const grid_t* g, double* U, double* Unew, int ncomp,
     int64_t nmax = g->n[0];
     if (g->n[1] > nmax) nmax = g->n[1];
     if (g->n[2] > nmax) nmax = g->n[2];
-    double* line = (double*)malloc(sizeof(double) * (size_t)((nmax + 1) * ncomp));
-    if (!line) return ORACLE_OOM;
     double* src = U;
     double* dst = Unew;
     int status = ORACLE_OK;
     for (int d = 0; d < g->ndim && status == ORACLE_OK; d++) {
         fill_padding(g, src, ncomp, bc);
         memcpy(dst, src, sizeof(double) * (size_t)(g->ncell * ncomp));
-        int64_t c[3] = {0, 0, 0};
+        /* all grid lines along axis d; a line reads src and writes only its
+           own cells of dst, so lines may run on different threads */
         int64_t ext[3] = {g->n[0], g->n[1], g->n[2]};
         ext[d] = 1;
-        for (int64_t b2 = 0; b2 < ext[2] && status == ORACLE_OK; b2++)
-            for (int64_t b1 = 0; b1 < ext[1] && status == ORACLE_OK; b1++)
-                for (int64_t b0 = 0; b0 < ext[0] && status == ORACLE_OK; b0++) {
-                    c[0] = b0;
-                    c[1] = b1;
-                    c[2] = b2;
-                    /* faces between cells f-1 and f for f = 0..n_d; slot f */
-                    for (int64_t f = 0; f <= g->n[d] && status == ORACLE_OK; f++) {
-                        double qL[MAXC], qR[MAXC];
-                        c[d] = f - 1;
-                        load_cell(g, src, ncomp, c, qL);
-                        c[d] = f;
-                        load_cell(g, src, ncomp, c, qR);
-                        if (!force_flux(ncomp - 2, d, qL, qR, gamma, dt / dx[d], line + f * ncomp))
-                            status = ORACLE_NUMERIC;
-                    }
-                    for (int64_t i = 0; i < g->n[d] && status == ORACLE_OK; i++) {
-                        c[d] = i;
-                        int64_t id = pidx(g, c);
-                        double q[MAXC], rho, u[3], p;
-                        for (int m = 0; m < ncomp; m++) {
-                            q[m] = src[m * g->ncell + id] -
-                                   dt / dx[d] * (line[(i + 1) * ncomp + m] - line[i * ncomp + m]);
-                            dst[m * g->ncell + id] = q[m];
-                        }
-                        primitives(ncomp - 2, q, gamma, &rho, u, &p);
-                        if (!admissible(rho, p)) status = ORACLE_NUMERIC;
-                    }
+        int64_t nlines = ext[0] * ext[1] * ext[2];
+        int bad = 0, oom = 0;
+#pragma omp parallel reduction(|| : bad, oom)
+        {
+            double* line = (double*)malloc(sizeof(double) * (size_t)((nmax + 1) * ncomp));
+            if (!line) oom = 1;
+#pragma omp for schedule(static)
+            for (int64_t l = 0; l < nlines; l++) {
+                if (!line || bad) continue;
+                int64_t c[3] = {l % ext[0], (l / ext[0]) % ext[1], l / (ext[0] * ext[1])};
+                /* faces between cells f-1 and f for f = 0..n_d; slot f */
+                for (int64_t f = 0; f <= g->n[d] && !bad; f++) {
+                    double qL[MAXC], qR[MAXC];
+                    c[d] = f - 1;
+                    load_cell(g, src, ncomp, c, qL);
+                    c[d] = f;
+                    load_cell(g, src, ncomp, c, qR);
+                    if (!force_flux(ncomp - 2, d, qL, qR, gamma, dt / dx[d], line + f * ncomp)) bad = 1;
                 }
+                for (int64_t i = 0; i < g->n[d] && !bad; i++) {
+                    c[d] = i;
+                    int64_t id = pidx(g, c);
+                    double q[MAXC], rho, u[3], p;
+                    for (int m = 0; m < ncomp; m++) {
+                        q[m] = src[m * g->ncell + id] -
+                               dt / dx[d] * (line[(i + 1) * ncomp + m] - line[i * ncomp + m]);
+                        dst[m * g->ncell + id] = q[m];
+                    }
+                    primitives(ncomp - 2, q, gamma, &rho, u, &p);
+                    if (!admissible(rho, p)) bad = 1;
+                }
+            }
+            free(line);
+        }
+        if (oom) status = ORACLE_OOM;
+        else if (bad) status = ORACLE_NUMERIC;
         double* tmp = src;
         src = dst;
         dst = tmp;
     }
     if (status == ORACLE_OK && src != Unew) memcpy(Unew, src, sizeof(double) * (size_t)(g->ncell * ncomp));
-    free(line);
     return status;
 }
 
@@ -497,6 +520,22 @@ static int check_euler_args(int ndim, int ncomp, int scheme, int bc)
     if (bc != BC_PERIODIC && bc != BC_TRANSMISSIVE) return 0;
     return 1;
 }
+
+/* Threads used by the Euler steps (1 unless set; 1 if built without OpenMP). */
+static int g_threads = 1;
+
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    g_threads = n < 1 ? 1 : n;
+#else
+    (void)n;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+
+int oracle_threads(void) { return g_threads; }
 
 /*
  * Run nsteps steps in place on an interior-only component-major array.
@@ -524,6 +563,9 @@ int oracle_euler_run(int ndim, const int64_t* n, double* U, double gamma, double
         return ORACLE_OOM;
     }
     to_padded(&g, ncomp, U, A);
+#ifdef _OPENMP
+    omp_set_num_threads(g_threads);
+#endif
     double t = 0.0, dt = 0.0;
     int status = ORACLE_OK;
     int64_t s = 0;

@@ -345,6 +345,29 @@ def ripple_totals_noalloc(state, dims, ncomp, layout, dtype, totals_out, stream=
     """FP64 compensated totals of a dense CUDA tensor `state` into the CUDA tensor
     `totals_out` (ncomp doubles) without any device allocation by the library.
     Asynchronous on `stream` (a torch.cuda.Stream, a cudaStream_t int, or None)."""
+    import torch
+
+    want = torch.float32 if int(dtype) == RIPPLE_F32 else torch.float64 if int(dtype) == RIPPLE_F64 else None
+    if want is None:
+        raise ValueError("dtype must be RIPPLE_F32 or RIPPLE_F64")
+    for name, t in (("state", state), ("totals_out", totals_out)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must be on the current CUDA device")
+    if state.dtype != want:
+        raise ValueError(f"state must be {want}, got {state.dtype}")
+    if totals_out.dtype != torch.float64:
+        raise ValueError("totals_out must be float64")
+    cells = 1
+    for x in dims:
+        cells *= int(x)
+    if state.numel() < cells * int(ncomp):
+        raise ValueError(f"state holds {state.numel()} elements, dims x ncomp needs {cells * int(ncomp)}")
+    if totals_out.numel() < int(ncomp):
+        raise ValueError(f"totals_out holds {totals_out.numel()} elements, needs {int(ncomp)}")
     d = (ctypes.c_int64 * len(dims))(*[int(x) for x in dims])
     handle = None
     if stream is not None:

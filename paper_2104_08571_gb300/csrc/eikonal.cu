@@ -17,12 +17,14 @@
 //     across that face;
 //   * iterations are separated by a bounded grid barrier (co-residency from
 //     the cooperative launch); the run ends when no tile is active, or with
-//     DEV_ERR_TIMEOUT when the iteration cap is reached.
+//     DEV_ERR_TIMEOUT when the iteration cap is reached (DEV_ERR_BARRIER when
+//     a barrier wait runs out instead).
 // Outside-domain neighbours are +inf; sources stay at 0.
 #include <cooperative_groups.h>
 
 #include <algorithm>
 #include <type_traits>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -31,12 +33,15 @@
 
 namespace ripple {
 
+// Default bound on the polls of a grid-barrier wait (several seconds).  The
+// host may lower it (RIPPLE_GRID_SPIN_LIMIT) to exercise the timeout path.
 constexpr uint32_t kGridSpinLimit = 1u << 26;
 
 // Arguments of the persistent single-problem solve beyond the problem itself.
 struct EikArgs {
     long long max_iters;
     unsigned* bar;  // [2] grid barrier: arrivals, generation
+    unsigned spin_limit;  // polls of a barrier wait before it gives up
     FieldCtl* ctl;
 };
 
@@ -47,7 +52,7 @@ struct EikScratch {
 };
 
 // Bounded sense-reversal grid barrier.  Returns false if the wait ran out.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, int* sflag)
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned spin_limit, int* sflag)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -60,8 +65,13 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, in
             atomicAdd(bar + 1, 1u);
         } else {
             uint32_t i = 0;
-            while (*gen == g0 && ++i < kGridSpinLimit) __nanosleep(32);
-            if (i >= kGridSpinLimit) sflag[0] = 1;
+            while (*gen == g0) {
+                if (i++ >= spin_limit) {
+                    sflag[0] = 1;
+                    break;
+                }
+                __nanosleep(32);
+            }
         }
         __threadfence();
     }
@@ -80,13 +90,13 @@ __global__ void __launch_bounds__(EikTile<DIM>::NT) fim_kernel(const FimProblem<
 
     long long visits = 0, updates = 0;
     long long k = 0;
-    bool timed_out = false;
+    bool timed_out = false, barrier_out = false;
     for (;;) {
         if (blockIdx.x == 0 && tid == 0) a.count[(k + 2) % 3] = 0u;
         for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) fim_visit_tile<T, DIM>(sm, a, t, k, visits, updates);
 
-        if (!grid_barrier(e.bar, gridDim.x, sflag)) {
-            timed_out = true;
+        if (!grid_barrier(e.bar, gridDim.x, e.spin_limit, sflag)) {
+            barrier_out = true;
             break;
         }
         ++k;
@@ -101,7 +111,7 @@ __global__ void __launch_bounds__(EikTile<DIM>::NT) fim_kernel(const FimProblem<
         // has passed the barrier that ends iteration k + 1.
     }
 
-    if (!timed_out) {
+    if (!timed_out && !barrier_out) {
         // consolidate: every tile's current values into buffer 0
         using C = EikTile<DIM>;
         constexpr int TS = C::TS;
@@ -125,6 +135,7 @@ __global__ void __launch_bounds__(EikTile<DIM>::NT) fim_kernel(const FimProblem<
         atomicAdd((unsigned long long*)&e.ctl->counters[2], (unsigned long long)updates);
         if (blockIdx.x == 0) e.ctl->counters[0] = k;
         if (timed_out) atomicOr(&e.ctl->err, DEV_ERR_TIMEOUT);
+        if (barrier_out) atomicOr(&e.ctl->err, DEV_ERR_BARRIER);
     }
 }
 
@@ -264,6 +275,12 @@ extern "C" ripple_status ripple_eikonal_solve(ripple_field S, ripple_field Tf, c
     EikArgs e{};
     e.max_iters = p->max_iters > 0 ? p->max_iters : 1000000;
     e.bar = reinterpret_cast<unsigned*>(base + 16);
+    e.spin_limit = kGridSpinLimit;
+    if (const char* lim = std::getenv("RIPPLE_GRID_SPIN_LIMIT")) {
+        char* end = nullptr;
+        const unsigned long v = std::strtoul(lim, &end, 10);
+        if (end != lim && v < kGridSpinLimit) e.spin_limit = (unsigned)v;
+    }
     e.ctl = Tf->ctl;
     cudaStream_t s = ctx->stream;
     RIPPLE_CUDA(cudaMemsetAsync(Tf->eik->mem, 0, need, s));
@@ -307,6 +324,8 @@ extern "C" ripple_status ripple_eikonal_solve(ripple_field S, ripple_field Tf, c
     }
     if (host.err) {
         RIPPLE_CUDA(cudaMemsetAsync(&Tf->ctl->err, 0, sizeof(unsigned), s));
+        if (host.err & DEV_ERR_BARRIER)
+            return fail(RIPPLE_ERR_TIMEOUT, "FIM grid barrier wait ran out (a CTA was not resident or stalled)");
         if (host.err & DEV_ERR_TIMEOUT) return fail(RIPPLE_ERR_TIMEOUT, "FIM did not converge within max_iters");
         return fail(RIPPLE_ERR_INTERNAL, "FIM device error");
     }

@@ -21,7 +21,9 @@ namespace ripple {
 enum { LAYOUT_AOS = 0, LAYOUT_SOA = 1 };
 
 // Device-side error flags (FieldCtl::err), mapped to ripple_status by the host.
-enum : unsigned { DEV_ERR_NUMERIC = 1u, DEV_ERR_TIMEOUT = 2u, DEV_ERR_INTERNAL = 4u };
+// DEV_ERR_BARRIER: a bounded grid-barrier wait ran out (a CTA was not resident
+// or stalled), as distinct from an iteration cap reached (DEV_ERR_TIMEOUT).
+enum : unsigned { DEV_ERR_NUMERIC = 1u, DEV_ERR_TIMEOUT = 2u, DEV_ERR_INTERNAL = 4u, DEV_ERR_BARRIER = 8u };
 
 struct FieldGeom {
     int ndim, ncomp, h, lead;

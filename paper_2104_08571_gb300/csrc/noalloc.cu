@@ -100,23 +100,66 @@ __global__ void dense_totals_final_kernel(const double* __restrict__ partials, i
     out[m] = b.s + b.c;
 }
 
-// Device address of the scratch array on the current device, looked up once
-// per device with that device current.
+// Device address of the scratch array in the current context, looked up once
+// per (device, context) with that device current.  The address belongs to the
+// library's module as loaded in one context: a caller that makes its own
+// driver context current on the same device, or that resets the device and so
+// gets a new primary context, gets a fresh lookup instead of a stale pointer.
+typedef CUresult (*PFN_ctx_get_current)(CUcontext*);
+
+static PFN_ctx_get_current ctx_get_current_fn()
+{
+    static PFN_ctx_get_current fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_ctx_get_current>(p);
+    });
+    return fn;
+}
+
 static ripple_status scratch_address(double** out)
 {
+    struct Entry {
+        int dev;
+        CUcontext ctx;
+        double* addr;
+    };
     static std::mutex mu;
-    static double* addr[kMaxDevices] = {};
+    static Entry cache[kMaxDevices] = {};
+    static int ncache = 0;
     int dev = 0;
     RIPPLE_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(RIPPLE_ERR_INVALID, "device ordinal out of range");
+    auto get = ctx_get_current_fn();
+    if (!get) return fail(RIPPLE_ERR_CUDA, "cuCtxGetCurrent is unavailable");
+    CUcontext cu = nullptr;
+    if (get(&cu) != CUDA_SUCCESS) return fail(RIPPLE_ERR_CUDA, "cuCtxGetCurrent failed");
     std::lock_guard<std::mutex> lk(mu);
-    if (!addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_totals_partials);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_totals_partials)");
-        addr[dev] = static_cast<double*>(p);
+    for (int i = 0; i < ncache && cu; ++i)
+        if (cache[i].dev == dev && cache[i].ctx == cu) {
+            *out = cache[i].addr;
+            return RIPPLE_OK;
+        }
+    // set-up for this (device, context): the lookup also binds the device's
+    // primary context to this thread if no context was current yet
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_totals_partials);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_totals_partials)");
+    if (!cu && (get(&cu) != CUDA_SUCCESS || !cu)) return fail(RIPPLE_ERR_CUDA, "no current CUDA context");
+    // keep the table bounded: a context that replaced an earlier one on the
+    // same device takes over its entry
+    int slot = -1;
+    for (int i = 0; i < ncache && slot < 0; ++i)
+        if (cache[i].dev == dev) slot = i;
+    if (slot < 0) {
+        if (ncache == kMaxDevices) return fail(RIPPLE_ERR_INVALID, "too many devices");
+        slot = ncache++;
     }
-    *out = addr[dev];
+    cache[slot] = Entry{dev, cu, static_cast<double*>(p)};
+    *out = cache[slot].addr;
     return RIPPLE_OK;
 }
 

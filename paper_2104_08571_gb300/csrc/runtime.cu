@@ -246,6 +246,7 @@ ripple_status ensure_second_buffer(ripple_field f)
 static ripple_status map_dev_err(unsigned err, const FieldCtl* host = nullptr)
 {
     if (err & DEV_ERR_INTERNAL) return fail(RIPPLE_ERR_INTERNAL, "device-side invariant violated");
+    if (err & DEV_ERR_BARRIER) return fail(RIPPLE_ERR_TIMEOUT, "a device-side grid barrier wait ran out");
     if (err & DEV_ERR_TIMEOUT) return fail(RIPPLE_ERR_TIMEOUT, "a device-side bounded wait ran out");
     if (err & DEV_ERR_NUMERIC) {
         std::string msg = "non-positive or NaN density/pressure produced";

@@ -20,6 +20,48 @@ def rel_l1(got, ref):
     return out
 
 
+def max_rel(got, ref):
+    """Max over components of max|got - ref| / max|ref|: an element-wise bound
+    beside the relative L1, so that one wrong cell, a bad tile edge or a
+    missed ghost layer fails even when the mean error stays small."""
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    g = got.reshape(got.shape[0], -1)
+    r = ref.reshape(ref.shape[0], -1)
+    out = 0.0
+    for m in range(g.shape[0]):
+        den = np.abs(r[m]).max()
+        if den == 0.0:
+            den = max(np.abs(r).max(), 1e-300)
+        out = max(out, float(np.abs(g[m] - r[m]).max() / den))
+    return out
+
+
+# Element-wise bounds (max|gpu - oracle| / max|oracle| per component).
+# FP64 mode: rounding differences of ~1e-16 per operation, a few hundred
+# operations per cell update and at most 100 steps stay far below 1e-11.
+# FP32 mode: unit roundoff u = 6e-8; a MUSCL-Hancock update performs about 300
+# FP32 operations per cell (rounding errors of a few u per update after
+# cancellation), the scheme is stable (no growth beyond linear accumulation),
+# so 100 steps accumulate at most ~100 x 20 u = 1.2e-4 at any cell.
+LINF_F64 = 1e-11
+LINF_F32 = 2e-4
+# Eikonal travel times (max|T - T_fmm| / max T_fmm): FP32 rounding of about u
+# per Godunov update accumulates along a characteristic path of up to a few
+# thousand cells (~2048 u = 1.2e-4), plus the FIM stopping tolerance (1e-6
+# absolute per sweep); FP64 with a tight tolerance stays below 1e-8.
+LINF_EIK = 1e-3
+LINF_EIK_F64 = 1e-8
+
+
+def assert_parity(got, ref, l1, linf):
+    """Relative L1 (the workload's metric) and the element-wise bound together."""
+    e1 = rel_l1(got, ref)
+    ei = max_rel(got, ref)
+    assert e1 <= l1 and ei <= linf, f"rel L1 {e1:.3e} (bar {l1:.0e}), max {ei:.3e} (bar {linf:.0e})"
+    return e1, ei
+
+
 def gpu_euler(ctx, U0, nsteps, *, dtype=R.RIPPLE_F64, layout=R.RIPPLE_SOA, scheme=R.RIPPLE_RUSANOV1,
               bc=R.RIPPLE_BC_PERIODIC, dx=None, halo=None, gamma=1.4, cfl=0.4, variant=None, chunks=None):
     """Run nsteps on the GPU from the component-major state U0; returns (U, stats)."""

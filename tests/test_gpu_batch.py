@@ -10,7 +10,7 @@ import pytest
 import inputs
 import oracle
 import paper_2104_08571_gb300 as R
-from tests.gpu_util import rel_l1
+from tests.gpu_util import LINF_EIK, LINF_F32, LINF_F64, assert_parity, rel_l1
 
 pytestmark = pytest.mark.gpu
 
@@ -53,7 +53,7 @@ def test_batch_euler_matches_oracle(ctx):
     for req, info in zip(reqs, infos):
         assert info["status"] == R.RIPPLE_OK
         assert info["work"] == req["nsteps"]
-        assert rel_l1(req["output"], _oracle_euler(req)) <= 2e-5
+        assert_parity(req["output"], _oracle_euler(req), 2e-5, LINF_F32)
 
 
 def test_batch_eikonal_matches_fmm(ctx):
@@ -62,7 +62,7 @@ def test_batch_eikonal_matches_fmm(ctx):
     for req, info in zip(reqs, infos):
         assert info["status"] == R.RIPPLE_OK and info["work"] > 0
         ref = oracle.eikonal_fmm(req["input"].astype(np.float64), req["h"], req["sources"])
-        assert rel_l1(req["output"][None], ref[None]) <= 1e-4
+        assert_parity(req["output"][None], ref[None], 1e-4, LINF_EIK)
 
 
 def test_alone_equals_in_mix_bitwise(ctx):
@@ -134,7 +134,7 @@ def test_budget_admission_waits_for_memory():
         finishes = sorted(i["finish_s"] for i in infos)
         assert max(i["admit_s"] for i in infos) >= finishes[0]
         for req in reqs[:2]:
-            assert rel_l1(req["output"], _oracle_euler(req)) <= 2e-5
+            assert_parity(req["output"], _oracle_euler(req), 2e-5, LINF_F32)
         # a request that can never fit fails with RIPPLE_ERR_BUDGET
         big = _euler(2048, 2048, 0.1, 1)
         info = _run(c, [big])[0]
@@ -156,9 +156,9 @@ def test_requests_arriving_while_others_run(ctx):
     # the small late Euler request ran and finished while the long first one was resident
     assert info_late[0]["start_s"] < info_first[0]["finish_s"]
     assert info_late[0]["finish_s"] < info_first[0]["finish_s"]
-    assert rel_l1(late[0]["output"], _oracle_euler(late[0])) <= 2e-5
+    assert_parity(late[0]["output"], _oracle_euler(late[0]), 2e-5, LINF_F32)
     ref = oracle.eikonal_fmm(late[1]["input"].astype(np.float64), late[1]["h"], late[1]["sources"])
-    assert rel_l1(late[1]["output"][None], ref[None]) <= 1e-4
+    assert_parity(late[1]["output"][None], ref[None], 1e-4, LINF_EIK)
     # the long one equals the same problem on the single-field path
     f = R.ripple_field_create(ctx, (256, 256), 4, R.RIPPLE_SOA, 1, R.RIPPLE_F32)
     try:

@@ -9,7 +9,7 @@ import pytest
 import inputs
 import oracle
 import paper_2104_08571_gb300 as R
-from tests.gpu_util import gpu_euler, rel_l1
+from tests.gpu_util import LINF_EIK, LINF_F32, LINF_F64, assert_parity, gpu_euler, rel_l1
 
 pytestmark = pytest.mark.gpu
 MUSCL, RUS, FORCE = R.RIPPLE_MUSCL_HANCOCK_MINMOD, R.RIPPLE_RUSANOV1, R.RIPPLE_FORCE_SPLIT
@@ -42,7 +42,7 @@ def test_tiny_grids_match_oracle(ctx, dims, scheme, bc, dtype):
     oscheme = {RUS: oracle.RUSANOV1, MUSCL: oracle.MUSCL_HANCOCK, FORCE: oracle.FORCE_SPLIT}[scheme]
     got, _ = gpu_euler(ctx, U0, 7, dtype=dtype, scheme=scheme, bc=bc)
     ref, _ = oracle.euler_run(U0, 7, scheme=oscheme, bc=bc)
-    assert rel_l1(got, ref) <= (1e-12 if dtype == R.RIPPLE_F64 else 2e-5)
+    assert_parity(got, ref, *((1e-12, LINF_F64) if dtype == R.RIPPLE_F64 else (2e-5, LINF_F32)))
 
 
 def test_zero_steps_change_nothing(ctx):

@@ -11,7 +11,7 @@ import pytest
 import inputs
 import oracle
 import paper_2104_08571_gb300 as R
-from tests.gpu_util import gpu_euler, rel_l1
+from tests.gpu_util import LINF_EIK, LINF_F32, LINF_F64, assert_parity, gpu_euler, rel_l1
 
 pytestmark = pytest.mark.gpu
 FORCE = R.RIPPLE_FORCE_SPLIT
@@ -39,7 +39,7 @@ def test_force_split_config0_fp64(ctx):
     U0 = inputs.euler2d_sine(128)
     got, st = gpu_euler(ctx, U0, 100, scheme=FORCE)
     ref, info = oracle.euler_run(U0, 100, scheme=oracle.FORCE_SPLIT)
-    assert rel_l1(got, ref) <= 1e-12
+    assert_parity(got, ref, 1e-12, LINF_F64)
     assert st["t"] == pytest.approx(info["t"], rel=1e-13)
     for m in range(4):
         exact = math.fsum(ref[m].ravel())
@@ -58,7 +58,7 @@ def test_force_split_parity(ctx, dims, dtype, bc, layout):
     got, _ = gpu_euler(ctx, U0, steps, dtype=dtype, layout=layout, scheme=FORCE, bc=bc)
     ref, _ = oracle.euler_run(U0, steps, scheme=oracle.FORCE_SPLIT, bc=bc)
     tol = 1e-12 if dtype == R.RIPPLE_F64 else 2e-5
-    assert rel_l1(got, ref) <= tol
+    assert_parity(got, ref, tol, LINF_F64 if tol < 1e-9 else LINF_F32)
 
 
 _LONG_WALK_REF = {}
@@ -77,7 +77,7 @@ def test_force_split_fp32_2d_long_walks(ctx, layout, bc):
         _LONG_WALK_REF[bc] = oracle.euler_run(U0, 3, scheme=oracle.FORCE_SPLIT, bc=bc)
     ref, info = _LONG_WALK_REF[bc]
     got, st = gpu_euler(ctx, U0, 3, dtype=R.RIPPLE_F32, layout=layout, scheme=FORCE, bc=bc)
-    assert rel_l1(got, ref) <= 2e-5
+    assert_parity(got, ref, 2e-5, LINF_F32)
     assert st["t"] == pytest.approx(info["t"], rel=1e-5)
 
 

@@ -368,3 +368,26 @@ def test_force_split_negative_pressure_is_reported(oracle_lib):
     U0[3, 4, 4] = -1.0
     _, info = oracle_lib.euler_run(U0, 3, scheme=FORCE, allow_numeric=True)
     assert info["status"] == oracle_lib.NUMERIC and info["steps_done"] == 0
+
+
+@pytest.mark.parametrize("scheme,bc", [(0, 0), (1, 1), (FORCE, 1)])
+def test_thread_count_changes_no_bit(oracle_lib, scheme, bc):
+    """The Euler steps split independent grid lines over threads; every cell is
+    computed by the same operations in the same order, so 1 and 4 threads give
+    identical bits (and the same dt), also when a step stops on a bad state."""
+    U3 = inputs.euler3d_blast(20, seed=3, dims=(20, 14, 11))
+    U2 = inputs.euler2d_sine(36, ny=22)
+    bad = inputs.uniform_state((12, 10), 1.0, [0.0, 0.0], 1.0)
+    bad[3, 4, 5] = -1.0
+    try:
+        runs = []
+        for n in (1, 4):
+            oracle_lib.set_threads(n)
+            runs.append([oracle_lib.euler_run(U, 9, scheme=scheme, bc=bc) for U in (U3, U2)])
+            runs[-1].append(oracle_lib.euler_run(bad, 3, scheme=scheme, bc=bc, allow_numeric=True))
+        for (a, ia), (b, ib) in zip(runs[0], runs[1]):
+            assert np.array_equal(a, b)
+            assert ia == ib
+        assert runs[0][2][1]["status"] == oracle_lib.NUMERIC
+    finally:
+        oracle_lib.set_threads(1)
