@@ -156,6 +156,20 @@ typedef struct {
 
 RIPPLE_API ripple_status ripple_field_describe(ripple_field field, ripple_field_desc* out);
 
+/*
+ * Sweep kernel of a field's Euler steps (a tuning choice; every choice gives
+ * results within the FP32/FP64 parity bars, and the paper's tiling options of
+ * Section 5.4 are its prior art).  variant: -1 = automatic (the default), or
+ *   0 = one cell per thread, 32 x 8 tiles; 1 = the same, 32 x 4 tiles;
+ *   2 = packed cell pairs, 32 x 8 tiles (FP32); 3 = one warp per 64-cell row,
+ *   64 x 14 tiles (FP32 3D MUSCL-Hancock only).
+ * zchunk: planes per z work item of 3D sweeps (0 = automatic, 32).
+ * RIPPLE_ERR_INVALID for an unknown variant or a negative zchunk; a variant
+ * that does not exist for the field's dtype, dimension or scheme makes the
+ * next ripple_fv_step fall back to the automatic choice.
+ */
+RIPPLE_API ripple_status ripple_field_set_sweep(ripple_field field, int variant, int zchunk);
+
 /* ------------------------------------------------------------------------ */
 /* Finite-volume Euler step.                                                 */
 /* ------------------------------------------------------------------------ */

@@ -120,6 +120,7 @@ _SIGNATURES = {
     "ripple_field_upload_device": [_VP, _VP, ctypes.c_int],
     "ripple_field_download_device": [_VP, _VP, ctypes.c_int],
     "ripple_field_describe": [_VP, ctypes.POINTER(ripple_field_desc)],
+    "ripple_field_set_sweep": [_VP, ctypes.c_int, ctypes.c_int],
     "ripple_fv_step": [_VP, ctypes.POINTER(ripple_fv_params), ctypes.c_int64, ctypes.POINTER(ripple_fv_stats)],
     "ripple_eikonal_solve": [_VP, _VP, _I64P, ctypes.c_int, ctypes.POINTER(ripple_eik_params),
                              ctypes.POINTER(ripple_eik_stats)],
@@ -266,6 +267,11 @@ def ripple_field_describe(field) -> ripple_field_desc:
     out = ripple_field_desc()
     _check(load().ripple_field_describe(field, ctypes.byref(out)), "ripple_field_describe")
     return out
+
+
+def ripple_field_set_sweep(field, variant=-1, zchunk=0):
+    """Choose the field's sweep kernel variant and z chunk (-1 / 0 = automatic)."""
+    _check(load().ripple_field_set_sweep(field, int(variant), int(zchunk)), "ripple_field_set_sweep")
 
 
 def _np_dtype(desc):

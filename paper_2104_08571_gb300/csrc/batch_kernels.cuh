@@ -147,11 +147,6 @@ constexpr uint32_t kDepSpinLimit = 1u << 23;  // dependency waits of a round (x 
 constexpr int kAsyncChunk = 8;                // most tasks a producer takes from a round's counter at once
 constexpr unsigned kPublishRun = 16;          // most completed tiles a consumer warp publishes at once
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // Barrier among the 256 consumer threads only (the producer warp runs ahead),
 // returning the OR of a predicate over them: every consumer takes the same
 // decision at the same barrier.

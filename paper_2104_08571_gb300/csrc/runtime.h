@@ -33,10 +33,12 @@ struct TileShape {
     int tx, ty;
 };
 // Variants 0, 1: one cell per work item; variant 2 (FP32 only): packed f32x2
-// cell pairs (euler_sweep_pair.cuh).
-constexpr int kNumSweepVariants = 3;
+// cell pairs (euler_sweep_pair.cuh); variant 3 (FP32 3D MUSCL-Hancock only):
+// one warp per 64-cell row of a 64 x 14 tile (euler_sweep_row3.cuh).
+constexpr int kNumSweepVariants = 4;
 constexpr int kPairVariant = 2;
-constexpr TileShape kSweepVariants[kNumSweepVariants] = {{32, 8}, {32, 4}, {32, 8}};
+constexpr int kRowVariant = 3;
+constexpr TileShape kSweepVariants[kNumSweepVariants] = {{32, 8}, {32, 4}, {32, 8}, {64, 14}};
 
 // Launch description of one sweep (one explicit step of one field).
 struct SweepLaunch {

@@ -5,6 +5,7 @@
 
 #include "euler_sweep_pair.cuh"
 #include "euler_sweep_pair3.cuh"
+#include "euler_sweep_row3.cuh"
 #include "runtime.h"
 
 namespace ripple {
@@ -16,23 +17,29 @@ constexpr int kMaxDynSmem = 227 * 1024;
 template <typename T, int DIM, int LAYOUT, int SCHEME, int V>
 struct SweepKernel {
     static constexpr bool pair = V == kPairVariant;
+    static constexpr bool row = V == kRowVariant;
     static constexpr int TX = kSweepVariants[V].tx;
     static constexpr int TY = kSweepVariants[V].ty;
-    // the pair kernels cover every FP32 scheme (the split FORCE step one sweep per launch)
-    static constexpr bool exists = !pair || std::is_same<T, float>::value;
+    static constexpr bool f32 = std::is_same<T, float>::value;
+    // the pair kernels cover every FP32 scheme (the split FORCE step one sweep per
+    // launch); the row kernel only the FP32 3D MUSCL-Hancock step
+    static constexpr bool exists = row ? (f32 && DIM == 3 && SCHEME == SCHEME_MUSCL) : (!pair || f32);
     // 3D MUSCL-Hancock: the split-barrier schedule (euler_sweep_pair3.cuh)
     static constexpr bool pair3 = pair && DIM == 3 && SCHEME == SCHEME_MUSCL;
     static constexpr int smem()
     {
-        if constexpr (pair3) return Pair3Cfg<LAYOUT>::SMEM;
+        if constexpr (row) return Row3Cfg<LAYOUT>::SMEM;
+        else if constexpr (pair3) return Pair3Cfg<LAYOUT>::SMEM;
         else if constexpr (pair) return PairCfg<DIM, LAYOUT, SCHEME>::SMEM;
         else return SweepCfg<T, DIM, LAYOUT, SCHEME, TX, TY>::SMEM;
     }
+    static constexpr int nt() { return row ? Row3Cfg<LAYOUT>::NT : TX * TY; }
     static auto fn()
     {
-        if constexpr (pair3 && std::is_same<T, float>::value) return euler_sweep_pair3_kernel<LAYOUT>;
-        else if constexpr (pair && std::is_same<T, float>::value) return euler_sweep_pair_kernel<DIM, LAYOUT, SCHEME>;
-        else return euler_sweep_kernel<T, DIM, LAYOUT, SCHEME, TX, TY>;
+        if constexpr (row && exists) return euler_sweep_row3_kernel<LAYOUT>;
+        else if constexpr (pair3 && f32) return euler_sweep_pair3_kernel<LAYOUT>;
+        else if constexpr (pair && f32) return euler_sweep_pair_kernel<DIM, LAYOUT, SCHEME>;
+        else return euler_sweep_kernel<T, DIM, LAYOUT, SCHEME, (row ? 32 : TX), (row ? 8 : TY)>;
     }
 };
 
@@ -42,11 +49,11 @@ struct SweepEntry {
     static constexpr int TX = K::TX;
     static constexpr int TY = K::TY;
     struct SmemOnly {
-        static constexpr int SMEM = K::smem();
-        static constexpr int NT = TX * TY;
+        static constexpr int SMEM = K::exists ? K::smem() : 0;
+        static constexpr int NT = K::nt();
     };
     using C = SmemOnly;
-    static constexpr bool fits = K::exists && C::SMEM <= kMaxDynSmem;
+    static constexpr bool fits = K::exists && C::SMEM > 0 && C::SMEM <= kMaxDynSmem;
 
     static cudaError_t launch(const SweepLaunch& L)
     {

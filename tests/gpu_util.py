@@ -58,6 +58,7 @@ def assert_parity(got, ref, l1, linf):
     """Relative L1 (the workload's metric) and the element-wise bound together."""
     e1 = rel_l1(got, ref)
     ei = max_rel(got, ref)
+    print(f"parity: rel L1 {e1:.3e} (bar {l1:.0e}), max {ei:.3e} (bar {linf:.0e})")
     assert e1 <= l1 and ei <= linf, f"rel L1 {e1:.3e} (bar {l1:.0e}), max {ei:.3e} (bar {linf:.0e})"
     return e1, ei
 
@@ -74,6 +75,8 @@ def gpu_euler(ctx, U0, nsteps, *, dtype=R.RIPPLE_F64, layout=R.RIPPLE_SOA, schem
     npdt = np.float32 if dtype == R.RIPPLE_F32 else np.float64
     f = R.ripple_field_create(ctx, dims, ndim + 2, layout, halo, dtype)
     try:
+        if variant is not None or chunks is not None:
+            R.ripple_field_set_sweep(f, -1 if variant is None else variant, 0 if chunks is None else chunks)
         host = np.ascontiguousarray(U0, dtype=npdt)
         if layout == R.RIPPLE_AOS:
             R.ripple_field_upload(f, np.ascontiguousarray(np.moveaxis(host, 0, -1)), R.RIPPLE_AOS)

@@ -51,6 +51,7 @@ def max_rel(a, b):
 def check(T, ref, l1, linf):
     """Relative L1 over all cells and the element-wise bound beside it."""
     e1, ei = rel_l1(T, ref), max_rel(T, ref)
+    print(f"parity: rel L1 {e1:.3e} (bar {l1:.0e}), max {ei:.3e} (bar {linf:.0e})")
     assert e1 <= l1 and ei <= linf, f"rel L1 {e1:.3e} (bar {l1:.0e}), max {ei:.3e} (bar {linf:.0e})"
 
 

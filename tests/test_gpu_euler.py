@@ -96,24 +96,31 @@ def test_config0_fp32_parity(ctx):
     assert_parity(got, ref, 2e-5, LINF_F32)
 
 
+ROW, PAIR = 3, 2  # sweep variants of the FP32 3D MUSCL-Hancock step: row kernel (default), pair kernel
+
+
+@pytest.mark.parametrize("variant", [ROW, PAIR])
 @pytest.mark.parametrize("layout", [R.RIPPLE_SOA, R.RIPPLE_AOS])
-def test_blast_fp32_parity(ctx, layout):
+def test_blast_fp32_parity(ctx, layout, variant):
     U0 = inputs.euler3d_blast(40, seed=1, dims=(40, 36, 28)).astype(np.float32)
-    got, _ = gpu_euler(ctx, U0, 20, dtype=R.RIPPLE_F32, scheme=MUSCL, bc=TRA, layout=layout)
+    got, _ = gpu_euler(ctx, U0, 20, dtype=R.RIPPLE_F32, scheme=MUSCL, bc=TRA, layout=layout, variant=variant)
     ref, _ = oracle.euler_run(U0.astype(np.float64), 20, scheme=MUSCL, bc=TRA)
     assert_parity(got, ref, 2e-5, LINF_F32)
 
 
-@pytest.mark.parametrize("nz", [70, 33])
+@pytest.mark.parametrize("variant", [ROW, PAIR])
+@pytest.mark.parametrize("dims", [(37, 21, 70), (37, 21, 33), (130, 30, 9)])
 @pytest.mark.parametrize("layout", [R.RIPPLE_SOA, R.RIPPLE_AOS])
-def test_blast_fp32_parity_several_z_chunks(ctx, layout, nz):
+def test_blast_fp32_parity_several_z_chunks(ctx, layout, dims, variant):
     # 70 planes: three z chunks per tile (32, 32, 6); 33: a last chunk of one
-    # plane; ragged x and y tiles
-    U0 = inputs.euler3d_blast(nz, seed=2, dims=(37, 21, nz)).astype(np.float32)
-    got, _ = gpu_euler(ctx, U0, 6, dtype=R.RIPPLE_F32, scheme=MUSCL, bc=TRA, layout=layout)
+    # plane; ragged x and y tiles (130 x 30: three 64-wide row tiles, the last
+    # two cells wide, and a 2-row last tile)
+    nz = dims[2]
+    U0 = inputs.euler3d_blast(nz, seed=2, dims=dims).astype(np.float32)
+    got, _ = gpu_euler(ctx, U0, 6, dtype=R.RIPPLE_F32, scheme=MUSCL, bc=TRA, layout=layout, variant=variant)
     ref, _ = oracle.euler_run(U0.astype(np.float64), 6, scheme=MUSCL, bc=TRA)
     assert_parity(got, ref, 2e-5, LINF_F32)
-    per, _ = gpu_euler(ctx, U0, 6, dtype=R.RIPPLE_F32, scheme=MUSCL, bc=PER, layout=layout)
+    per, _ = gpu_euler(ctx, U0, 6, dtype=R.RIPPLE_F32, scheme=MUSCL, bc=PER, layout=layout, variant=variant)
     ref_p, _ = oracle.euler_run(U0.astype(np.float64), 6, scheme=MUSCL, bc=PER)
     assert_parity(per, ref_p, 2e-5, LINF_F32)
 
@@ -163,6 +170,20 @@ def test_blast_fp32_full_run_50_and_100_steps(ctx, dims, layout):
             assert st["dt_last"] == pytest.approx(info["dt_last"], rel=1e-5)
     finally:
         R.ripple_field_destroy(f)
+
+
+@pytest.mark.parametrize("layout", [R.RIPPLE_SOA, R.RIPPLE_AOS])
+@pytest.mark.parametrize("bc", [PER, TRA])
+def test_row_kernel_equals_pair_kernel_bitwise(ctx, layout, bc):
+    """The row kernel (one warp per 64-cell row, x faces by shuffles) and the
+    pair kernel evaluate every predicted state and face once, with the same
+    packed arithmetic in the same order, so they give identical bits; the
+    grid has a ragged 64-wide x tile, a ragged 14-row y tile and three z chunks."""
+    U0 = inputs.euler3d_blast(0, seed=9, dims=(150, 47, 70)).astype(np.float32)
+    a, sa = gpu_euler(ctx, U0, 8, dtype=R.RIPPLE_F32, scheme=MUSCL, bc=bc, layout=layout, variant=ROW)
+    b, sb = gpu_euler(ctx, U0, 8, dtype=R.RIPPLE_F32, scheme=MUSCL, bc=bc, layout=layout, variant=PAIR)
+    assert np.array_equal(a, b)
+    assert sa["t"] == sb["t"] and sa["dt_last"] == sb["dt_last"]
 
 
 def test_many_tiles_per_cta_many_launches(ctx):
