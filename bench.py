@@ -117,6 +117,47 @@ class ClockSampler:
                 "power_w_max": max(r["power"] for r in rows)}
 
 
+# Thread instructions per Godunov update of the FIM solve kernels, from one ncu
+# capture of each solve (smsp__inst_executed.sum x 32 / the solve's Godunov
+# updates); the eikonal roofline is issue-bound, so these set its achieved
+# rate.  Re-measure whenever the kernels change.
+FIM_INSTR_PER_UPDATE = {"2d_2048": None, "3d_192": None}
+
+
+def eikonal_roofline(name, updates_per_s, clocks, sms):
+    """Issue roofline of the FIM solve: thread instructions per second against
+    the SMs' issue rate (4 schedulers x 32 lanes per SM per clock, at the
+    median SM clock sampled during the solves)."""
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak = sms * 128 * mhz * 1e6
+    ipu = FIM_INSTR_PER_UPDATE.get(name)
+    out = {"bound": "issue", "peak": peak / 1e12, "unit": "T thread-instructions/s",
+           "peak_source": f"{sms} SMs x 128 lanes x {mhz:.0f} MHz (sampled)",
+           "instructions_per_update": ipu}
+    if ipu is None:
+        out.update(achieved=None, frac=None)
+    else:
+        out.update(achieved=ipu * updates_per_s / 1e12, frac=ipu * updates_per_s / peak)
+    return out
+
+
+def host_description():
+    """Host cores and CPU model of the machine the oracle runs on."""
+    model = None
+    try:
+        txt = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in txt.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
 def dist_setup(n_gpus):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -168,20 +209,24 @@ def bench_gpu(args, rank, world, local):
     U0_dev_aos = torch.from_numpy(np.ascontiguousarray(np.moveaxis(U0, 0, -1))).to(f"cuda:{local}")
     result = {}
 
-    def timed_steps(field, k, w):
+    def timed_steps(field, k, w, per_step=None):
+        """W warm-up steps, then K steps, each bracketed by CUDA events on the
+        library's stream: returns the total of the K steps (ms); the K per-step
+        times go to per_step."""
         for _ in range(w):
             R.ripple_fv_step(field, prm, 1, stats=False)
         torch.cuda.synchronize()
         barrier(world)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(k):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+        ev[0].record(stream)
+        for i in range(k):
             R.ripple_fv_step(field, prm, 1, stats=False)
-        e1.record(stream)
+            ev[i + 1].record(stream)
         torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
+        ms = ev[0].elapsed_time(ev[k])
+        if per_step is not None:
+            per_step.extend(ev[i].elapsed_time(ev[i + 1]) for i in range(k))
         barrier(world)
         return ms
 
@@ -190,9 +235,11 @@ def bench_gpu(args, rank, world, local):
     R.ripple_field_upload(f, U0_dev, R.RIPPLE_SOA)
     R.ripple_fv_step(f, prm, 1, stats=False)  # first call: second buffer, prep, tensor maps
     torch.cuda.synchronize()
+    per_step = []
     with ClockSampler(local) as clk:
-        ms = timed_steps(f, args.steps, args.warmup)
+        ms = timed_steps(f, args.steps, args.warmup, per_step)
     clocks = clk.summary()
+    result["per_step_ms"] = per_step
     ms_max = allreduce_max(ms, world)
     st = R.ripple_fv_step(f, prm, 0)  # synchronous error check + totals of the final state
     result["soa_ms_per_step"] = ms / args.steps
@@ -207,6 +254,17 @@ def bench_gpu(args, rank, world, local):
         par["headline"] = dict(Un=Un, cells=cells, gpu=R.ripple_field_download(f).reshape(5, -1)[:, cells].T,
                                dt=st1["dt_last"], dx=[1.0 / N3] * 3)
     R.ripple_field_destroy(f)
+    if "headline" in par:
+        # the whole field after a full 50-step run of the headline scheme at 128^3
+        # (SoA, the headline kernel), for the oracle's 50-step run of the same state
+        n1 = 128
+        U1 = inputs.euler3d_blast(n1, seed=1).astype(np.float32)
+        f1 = R.ripple_field_create(ctx, (n1, n1, n1), 5, R.RIPPLE_SOA, 2, R.RIPPLE_F32)
+        R.ripple_field_upload(f1, U1)
+        prm1 = R.make_fv_params([1.0 / n1] * 3, scheme=MUSCL, bc=TRA)
+        st50 = R.ripple_fv_step(f1, prm1, NSTEPS_SOLVE)
+        par["full_run_128"] = dict(U0=U1, gpu=R.ripple_field_download(f1), t=st50["t"], n=n1)
+        R.ripple_field_destroy(f1)
     hbm_peak, peak_kind = load_peaks()
     achieved = BYTES_PER_CELL_UPDATE * ncell / (ms / args.steps / 1e3) / 1e9
     if args.sweep_only:
@@ -219,7 +277,11 @@ def bench_gpu(args, rank, world, local):
     R.ripple_field_upload(fa, U0_dev_aos, R.RIPPLE_AOS)
     R.ripple_fv_step(fa, prm, 1, stats=False)
     torch.cuda.synchronize()
-    ms_aos = timed_steps(fa, args.steps, args.warmup)
+    per_step_aos = []
+    with ClockSampler(local) as clk_aos:
+        ms_aos = timed_steps(fa, args.steps, args.warmup, per_step_aos)
+    result["aos_per_step_ms"] = per_step_aos
+    result["aos_clocks"] = clk_aos.summary()
     R.ripple_fv_step(fa, prm, 0)
     R.ripple_field_destroy(fa)
 
@@ -237,11 +299,13 @@ def bench_gpu(args, rank, world, local):
     one_solve()  # warm-up
     torch.cuda.synchronize()
     barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(e2e_solves):
-        one_solve()
-    torch.cuda.synchronize()
-    e2e_s = allreduce_max(time.perf_counter() - t0, world)
+    with ClockSampler(local) as clk_e2e:
+        t0 = time.perf_counter()
+        for _ in range(e2e_solves):
+            one_solve()
+        torch.cuda.synchronize()
+        e2e_s = allreduce_max(time.perf_counter() - t0, world)
+    result["e2e_clocks"] = clk_e2e.summary()
     R.ripple_field_destroy(fe)
     e2e_value = world * e2e_solves * NSTEPS_SOLVE * ncell / e2e_s
 
@@ -254,11 +318,13 @@ def bench_gpu(args, rank, world, local):
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    R.ripple_fv_step(f2, prm2, 100, stats=False)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(local) as clk2:
+        e0.record(stream)
+        R.ripple_fv_step(f2, prm2, 100, stats=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
     ms2 = e0.elapsed_time(e1)
+    result["euler2d_clocks"] = clk2.summary()
     R.ripple_fv_step(f2, prm2, 0)
     if "headline" in par:  # 100 steps from the initial state, for the oracle comparison
         R.ripple_field_upload(f2, U2)
@@ -269,6 +335,32 @@ def bench_gpu(args, rank, world, local):
     # ---- secondary: eikonal FIM solves ----
     eik = {}
     if not args.skip_eikonal:
+        eik = bench_eikonal(R, torch, local, keep=par if "headline" in par else None, ctx=ctx, stream=stream)
+
+    R.ripple_ctx_destroy(ctx)
+    batched = None if args.skip_batched else bench_batched(R, torch, local, keep=par if "headline" in par else None)
+    serve = None if args.skip_serve else bench_serving(R, torch, local, count=args.serve_requests)
+    layout = None if args.skip_layout else bench_layout(R, torch, local)
+    force = bench_force_split(R, torch, local, par=par if "headline" in par else None)
+    value = world * args.steps * ncell / (ms_max / 1e3)
+    return dict(value=value, ms_per_step=ms_max / args.steps, clocks=clocks, ms_aos=ms_aos / args.steps,
+                e2e_value=e2e_value, e2e_s=e2e_s, e2e_solves=e2e_solves, ms2=ms2, eik=eik,
+                achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result, batched=batched,
+                serve=serve, layout=layout, force=force, parity_data=par)
+
+
+def bench_eikonal(R, torch, local, keep=None, ctx=None, stream=None, steps=5):
+    """FIM eikonal solves, FP32: 2048^2 and 192^3, seeded smoothed-Gaussian
+    slowness, 1-4 seeded sources, tol 1e-6.  Each solve is timed between CUDA
+    events on the library's stream; the median of `steps` solves is reported."""
+    own = ctx is None
+    if own:
+        ctx = R.ripple_ctx_create(local)
+        R.use_torch_allocator(ctx, local)
+        stream = torch.cuda.Stream(device=local)
+        R.ripple_set_stream(ctx, stream)
+    eik = {}
+    try:
         for name, edims in (("2d_2048", (2048, 2048)), ("3d_192", (192, 192, 192))):
             s = inputs.eikonal_slowness(edims, seed=1).astype(np.float32)
             src = inputs.eikonal_sources(edims, seed=1)
@@ -277,33 +369,32 @@ def bench_gpu(args, rank, world, local):
             R.ripple_field_upload(fs, s)
             R.ripple_eikonal_solve(fs, ft, src, 1.0 / edims[0], 1e-6)  # warm-up
             torch.cuda.synchronize()
-            reps = 3
-            t0 = time.perf_counter()
-            for _ in range(reps):
-                est = R.ripple_eikonal_solve(fs, ft, src, 1.0 / edims[0], 1e-6)
-            dt = (time.perf_counter() - t0) / reps
+            times = []
+            with ClockSampler(local) as clk_e:
+                for _ in range(max(1, steps)):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    est = R.ripple_eikonal_solve(fs, ft, src, 1.0 / edims[0], 1e-6)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1) / 1e3)
+            dt = float(np.median(times))
             ncells = int(np.prod(edims))
-            hbm = 8.0 * ncells / dt / 1e9  # algorithmic: read s, write T once per solve
-            eik[name] = {"solve_ms": dt * 1e3, "solved_cells_per_s": ncells / dt,
+            eik[name] = {"solve_ms": dt * 1e3, "solve_ms_min_max": [min(times) * 1e3, max(times) * 1e3],
+                         "solves": len(times), "solved_cells_per_s": ncells / dt,
                          "godunov_updates_per_s": est["cell_updates"] / dt, "iterations": est["iterations"],
                          "tile_visits": est["tile_visits"], "sources": len(src),
-                         "hbm_GB_s_algorithmic": hbm, "hbm_frac": hbm / load_peaks()[0],
-                         "bound": "latency of the active-list iterations (the front crosses the grid)"}
-            if "headline" in par:
-                par["eikonal_" + name] = dict(s=s, src=src, h=1.0 / edims[0], gpu=R.ripple_field_download(ft))
+                         "roofline": eikonal_roofline(name, est["cell_updates"] / dt, clk_e.summary(),
+                                                      torch.cuda.get_device_properties(local).multi_processor_count),
+                         "clocks": clk_e.summary()}
+            if keep is not None:
+                keep["eikonal_" + name] = dict(s=s, src=src, h=1.0 / edims[0], gpu=R.ripple_field_download(ft))
             R.ripple_field_destroy(fs)
             R.ripple_field_destroy(ft)
-
-    R.ripple_ctx_destroy(ctx)
-    batched = None if args.skip_batched else bench_batched(R, torch, local, keep=par if "headline" in par else None)
-    serve = None if args.skip_serve else bench_serving(R, torch, local)
-    layout = None if args.skip_layout else bench_layout(R, torch, local)
-    force = bench_force_split(R, torch, local, par=par if "headline" in par else None)
-    value = world * args.steps * ncell / (ms_max / 1e3)
-    return dict(value=value, ms_per_step=ms_max / args.steps, clocks=clocks, ms_aos=ms_aos / args.steps,
-                e2e_value=e2e_value, e2e_s=e2e_s, e2e_solves=e2e_solves, ms2=ms2, eik=eik,
-                achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result, batched=batched,
-                serve=serve, layout=layout, force=force, parity_data=par)
+    finally:
+        if own:
+            R.ripple_ctx_destroy(ctx)
+    return eik
 
 
 def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
@@ -332,7 +423,8 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
 
         run_batch()  # warm-up: table capacities, graph capture
         st0 = R.ripple_batch_get_stats(ctx)
-        reqs, infos, t_batch = run_batch()
+        with ClockSampler(local) as clk_b:
+            reqs, infos, t_batch = run_batch()
         st1 = R.ripple_batch_get_stats(ctx)
         if keep is not None:  # four instances (the smallest, two middle, the largest) for the oracle
             order = np.argsort(sides)
@@ -345,7 +437,8 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
                                  steps_per_sync=nsteps, use_graphs=True, staging=cfg["staging"], async_queue=True)
         run_batch()
         sa0 = R.ripple_batch_get_stats(ctx)
-        reqs_a, infos_a, t_async = run_batch()
+        with ClockSampler(local) as clk_a:
+            reqs_a, infos_a, t_async = run_batch()
         sa1 = R.ripple_batch_get_stats(ctx)
         span_a = max(i["finish_s"] for i in infos_a) - min(i["start_s"] for i in infos_a)
         same = all(np.array_equal(x["output"], y["output"]) for x, y in zip(reqs, reqs_a))
@@ -385,11 +478,12 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
         for f, U in zip(fields, states):
             R.ripple_field_upload(f, U)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for f, prm in zip(fields, prms):
-            R.ripple_fv_step(f, prm, nsteps, stats=False)
-        R.ripple_ctx_sync(ctx)
-        t_loop = time.perf_counter() - t0
+        with ClockSampler(local) as clk_l:
+            t0 = time.perf_counter()
+            for f, prm in zip(fields, prms):
+                R.ripple_fv_step(f, prm, nsteps, stats=False)
+            R.ripple_ctx_sync(ctx)
+            t_loop = time.perf_counter() - t0
         worst = 0.0
         for f, req in zip(fields, reqs):
             loop_out = R.ripple_field_download(f)
@@ -404,6 +498,7 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
         "instances": count, "total_cells": int(cells), "steps": nsteps,
         "value": cells * nsteps / t_batch, "unit": METRIC,
         "batched_seconds_end_to_end": t_batch,
+        "clocks": clk_b.summary(), "clocks_dependency_driven": clk_a.summary(), "clocks_loop": clk_l.summary(),
         "batched_compute_span_s": span,
         "batched_value_compute_span": cells * nsteps / span,
         "launches": st1["launches"] - st0["launches"], "graph_replays": st1["graph_replays"] - st0["graph_replays"],
@@ -454,16 +549,18 @@ def bench_force_split(R, torch, local, par=None, legs=None):
             R.ripple_fv_step(f, prm, 3)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            R.ripple_fv_step(f, prm, steps, stats=False)
-            e1.record(stream)
-            torch.cuda.synchronize()
+            with ClockSampler(local) as clk_f:
+                e0.record(stream)
+                R.ripple_fv_step(f, prm, steps, stats=False)
+                e1.record(stream)
+                torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / steps
             R.ripple_fv_step(f, prm, 0)
             es = 16 if dtype == R.RIPPLE_F32 else 32
             gbs = 2 * 2 * es * n * n / (ms / 1e3) / 1e9  # two sweeps, each reads and writes the state
             out[name] = {"cells": n * n, "ms_per_step": ms, "cell_updates_per_s": n * n / (ms / 1e3),
-                         "launches_per_step": 2, "GB_s_algorithmic": gbs, "hbm_frac": gbs / load_peaks()[0]}
+                         "launches_per_step": 2, "GB_s_algorithmic": gbs, "hbm_frac": gbs / load_peaks()[0],
+                         "clocks": clk_f.summary()}
             if name == "fp32_8192":
                 out[name]["paper_v100_flux_difference_ms_8k"] = {"ripple_s": 3.5533, "ripple_c": 5.5284,
                                                                    "kokkos": 12.919}
@@ -501,6 +598,7 @@ def bench_layout(R, torch, local, n_saxpy=1 << 30, n_particles=80_000_000, reps=
         st = R.ripple_ctx_sync(ctx)
         return e0.elapsed_time(e1) / reps
 
+    clk_lay = ClockSampler(local).__enter__()
     try:
         x = torch.rand(n_saxpy, device=f"cuda:{local}")
         y = torch.rand(n_saxpy, device=f"cuda:{local}")
@@ -522,7 +620,9 @@ def bench_layout(R, torch, local, n_saxpy=1 << 30, n_particles=80_000_000, reps=
             out["particle_update"][name] = {"ms": ms, "GB_s": gbs, "hbm_frac": gbs / peak}
         del p
     finally:
+        clk_lay.__exit__(None, None, None)
         R.ripple_ctx_destroy(ctx)
+    out["clocks"] = clk_lay.summary()
     return out
 
 
@@ -547,7 +647,10 @@ def _make_req(R, r, data, src):
     return R.eikonal_request(data, src, 1.0 / side, tol=1e-6)
 
 
-def bench_serving(R, torch, local, rates=(50, 500, 2000), count=160):
+SERVE_RATES = (50, 100, 200, 500, 1000, 2000)
+
+
+def bench_serving(R, torch, local, rates=SERVE_RATES, count=400):
     """Poisson arrivals of mixed requests (70 % 2D Euler side log-U[64,1024],
     50-500 steps; 30 % 2D eikonal side log-U[128,1024], 1-4 sources) under a
     40 GB budget.  Latency = submit -> result in host memory.  Baseline: the
@@ -595,17 +698,18 @@ def bench_serving(R, torch, local, rates=(50, 500, 2000), count=160):
                 R.ripple_wait(ctx, t, 600000)
             dest = result["rates"] if mode == "per_step_launches" else result.setdefault("rates_dependency_driven", {})
             for rate in rates:
-                arrivals = [r["t"] for r in inputs.serve_stream(rate, count, seed=1)]
-                reqs = [_make_req(R, r, d, s) for (r, d, s) in prepared]
-                tickets = []
-                t0 = time.perf_counter()
-                for a, req in zip(arrivals, reqs):
-                    delay = t0 + a - time.perf_counter()
-                    if delay > 0:
-                        time.sleep(delay)
-                    tickets.append(R.ripple_batch_submit(ctx, [req])[0])
-                infos = [R.ripple_wait(ctx, t, 600000) for t in tickets]
-                makespan = time.perf_counter() - t0
+                with ClockSampler(local) as clk_s:
+                    arrivals = [r["t"] for r in inputs.serve_stream(rate, count, seed=1)]
+                    reqs = [_make_req(R, r, d, s) for (r, d, s) in prepared]
+                    tickets = []
+                    t0 = time.perf_counter()
+                    for a, req in zip(arrivals, reqs):
+                        delay = t0 + a - time.perf_counter()
+                        if delay > 0:
+                            time.sleep(delay)
+                        tickets.append(R.ripple_batch_submit(ctx, [req])[0])
+                    infos = [R.ripple_wait(ctx, t, 600000) for t in tickets]
+                    makespan = time.perf_counter() - t0
                 ok = sum(1 for i in infos if i["status"] == R.RIPPLE_OK)
                 lat = np.array([i["finish_s"] - i["submit_s"] for i in infos]) * 1e3
                 # baseline queue: one request at a time in arrival order
@@ -623,6 +727,7 @@ def bench_serving(R, torch, local, rates=(50, 500, 2000), count=160):
                                             "cell_updates_per_s": work_euler / base_makespan,
                                             "p50_ms": float(np.percentile(blat, 50)),
                                             "p99_ms": float(np.percentile(blat, 99))},
+                    "clocks": clk_s.summary(),
                 }
     finally:
         R.ripple_ctx_destroy(ctx)
@@ -630,14 +735,32 @@ def bench_serving(R, torch, local, rates=(50, 500, 2000), count=160):
 
 
 def cpu_baseline_sample():
-    """The FP64 oracle, as it stands, on one full 256^3 step of the same workload."""
+    """The FP64 oracle, as it stands, on the host cores: one full 256^3 step of
+    the headline workload on all cores, and the whole 2D FP64 128^2 workload
+    (100 steps) on one thread and on all cores (the oracle's results do not
+    depend on its thread count)."""
     import oracle
-    U0 = inputs.euler3d_blast(N3, seed=1).astype(np.float32).astype(np.float64)
-    t0 = time.perf_counter()
-    oracle.euler_run(U0, 1, scheme=oracle.MUSCL_HANCOCK, bc=oracle.TRANSMISSIVE)
-    dt = time.perf_counter() - t0
-    return {"value": N3 ** 3 / dt, "unit": METRIC, "cores": oracle.threads_used(), "kind": "oracle",
-            "sample": f"one MUSCL-Hancock step of the 256^3 blast in FP64 ({dt:.1f} s)"}
+    oracle.build()
+    host = host_description()
+    ncores = oracle.set_threads(os.cpu_count() or 1)
+    try:
+        U0 = inputs.euler3d_blast(N3, seed=1).astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.euler_run(U0, 1, scheme=oracle.MUSCL_HANCOCK, bc=oracle.TRANSMISSIVE)
+        dt = time.perf_counter() - t0
+        U2 = inputs.euler2d_sine(128)
+        c0 = {}
+        for nt in (1, ncores):
+            oracle.set_threads(nt)
+            t0 = time.perf_counter()
+            oracle.euler_run(U2, 100)
+            t2 = time.perf_counter() - t0
+            c0[f"threads_{nt}"] = {"cell_updates_per_s": 128 * 128 * 100 / t2, "seconds": t2}
+    finally:
+        oracle.set_threads(1)
+    return {"value": N3 ** 3 / dt, "unit": METRIC, "cores": ncores, "kind": "oracle",
+            "sample": f"one MUSCL-Hancock step of the 256^3 blast in FP64 on {ncores} threads ({dt:.1f} s)",
+            "host": host, "euler2d_fp64_128_100_steps": c0}
 
 
 def rel_l1(a, b):
@@ -663,6 +786,25 @@ def oracle_legs(par):
         out["euler3d_256"] = {"rel_l1_vs_oracle": err, "tolerance": 2e-5,
                               "check": "one step from the GPU state after the timed steps, 4096 seeded cells",
                               "dt_rel_diff": abs(dt - p["dt"]) / dt, "oracle_seconds": t}
+    if "full_run_128" in par:
+        p = par["full_run_128"]
+        n1 = p["n"]
+        nt = oracle.set_threads(os.cpu_count() or 1)
+        try:
+            t0 = time.perf_counter()
+            ref, info = oracle.euler_run(p["U0"].astype(np.float64), NSTEPS_SOLVE, scheme=oracle.MUSCL_HANCOCK,
+                                         bc=oracle.TRANSMISSIVE)
+            t = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(1)
+        g = np.asarray(p["gpu"], dtype=np.float64).reshape(5, -1)
+        r_ = ref.reshape(5, -1)
+        linf = float((np.abs(g - r_).max(1) / np.abs(r_).max(1)).max())
+        out["euler3d_128_full_50_steps"] = {
+            "rel_l1_vs_oracle": rel_l1(p["gpu"], ref), "tolerance": 2e-5, "max_elementwise_rel": linf,
+            "elementwise_tolerance": 5e-5, "t_rel_diff": abs(p["t"] - info["t"]) / info["t"],
+            "check": f"whole {n1}^3 field after {NSTEPS_SOLVE} steps from the initial blast (SoA, the headline kernel)",
+            "oracle_cell_updates_per_s": n1 ** 3 * NSTEPS_SOLVE / t, "oracle_threads": nt, "oracle_seconds": t}
     if "force_split_fp64_128" in par:
         p = par["force_split_fp64_128"]
         t0 = time.perf_counter()
@@ -724,8 +866,18 @@ def main():
     ap.add_argument("--force-n", type=int, default=8192)
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 512-instance batched workload (profiling; not the headline line)")
+    ap.add_argument("--eikonal-only", action="store_true",
+                    help="run only the FIM eikonal solves (profiling; not the headline line)")
+    ap.add_argument("--serve-only", action="store_true",
+                    help="run only the serving workload (not the headline line)")
+    ap.add_argument("--serve-requests", type=int, default=400,
+                    help="requests per arrival rate of the serving workload")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="the serving workload as stated: 2,000 requests at each of the six rates")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.serve_full:
+        args.serve_requests = 2000
     rank, world, local = dist_setup(args.gpus)
     ncell = int(np.prod(args.sweep_dims))
     nx, ny, nz = args.sweep_dims
@@ -740,6 +892,7 @@ def main():
             return
         import oracle
         oracle.build()
+        ncores = oracle.set_threads(os.cpu_count() or 1)
         side = 128  # bounded sample: the central 128^3 crop of the blast, one step each
         U0 = inputs.euler3d_blast(N3, seed=1).astype(np.float32).astype(np.float64)
         lo = (N3 - side) // 2
@@ -756,8 +909,9 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": config,
-                "cpu_baseline": {"value": value, "unit": METRIC, "cores": oracle.threads_used(), "kind": "oracle",
-                                 "sample": f"one FP64 step of the central {side}^3 crop of the 256^3 blast per step"},
+                "cpu_baseline": {"value": value, "unit": METRIC, "cores": ncores, "kind": "oracle",
+                                 "sample": f"one FP64 step of the central {side}^3 crop of the 256^3 blast per step",
+                                 "host": host_description()},
                 "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -771,6 +925,26 @@ def main():
             print(json.dumps({"metric": METRIC, "value": fs["fp32"]["cell_updates_per_s"], "unit": METRIC,
                               "n_gpus": world, "config": {"workload": f"force_split_2d_fp32_{args.force_n}^2_sine"},
                               "force_split": fs}))
+        return
+    if args.serve_only:
+        import torch
+        import paper_2104_08571_gb300 as R
+        torch.cuda.set_device(local)
+        sv = bench_serving(R, torch, local, count=args.serve_requests)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": sv["rates"]["2000"]["cell_updates_per_s"], "unit": METRIC,
+                              "n_gpus": world, "config": {"workload": "served mix, Poisson arrivals"},
+                              "serve": sv}))
+        return
+    if args.eikonal_only:
+        import torch
+        import paper_2104_08571_gb300 as R
+        torch.cuda.set_device(local)
+        ek = bench_eikonal(R, torch, local, steps=args.steps)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": ek["2d_2048"]["godunov_updates_per_s"], "unit": METRIC,
+                              "n_gpus": world, "config": {"workload": "FIM eikonal 2048^2 and 192^3"},
+                              "eikonal": ek}))
         return
     if args.batched_only:
         import torch
@@ -812,15 +986,28 @@ def main():
                      "peak_source": r["peak_kind"],
                      "algorithmic_bytes_per_cell_update": BYTES_PER_CELL_UPDATE},
         "clocks": r["clocks"],
-        "e2e": {"value": r["e2e_value"], "unit": METRIC, "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes,
-                "step": f"one {NSTEPS_SOLVE}-step solve: pinned host -> device, {NSTEPS_SOLVE} sweeps, device -> pinned host",
-                "solves": r["e2e_solves"], "seconds": r["e2e_s"]},
+        "ms_per_step_median": float(np.median(r["extra"]["per_step_ms"])),
+        "ms_per_step_spread": {"min": float(np.min(r["extra"]["per_step_ms"])),
+                               "p10": float(np.percentile(r["extra"]["per_step_ms"], 10)),
+                               "p90": float(np.percentile(r["extra"]["per_step_ms"], 90)),
+                               "max": float(np.max(r["extra"]["per_step_ms"])),
+                               "repeats": len(r["extra"]["per_step_ms"]),
+                               "timing": "each step between its own CUDA events on the library stream"},
+        "e2e": {"value": r["e2e_value"], "unit": METRIC,
+                "h2d_bytes_per_step": state_bytes // NSTEPS_SOLVE, "d2h_bytes_per_step": state_bytes // NSTEPS_SOLVE,
+                "h2d_bytes_per_solve": state_bytes, "d2h_bytes_per_solve": state_bytes,
+                "step": f"one {NSTEPS_SOLVE}-step solve: pinned host -> device, {NSTEPS_SOLVE} sweeps, "
+                        "device -> pinned host; bytes per step = bytes per solve / steps per solve",
+                "solves": r["e2e_solves"], "seconds": r["e2e_s"], "clocks": r["extra"]["e2e_clocks"]},
         "cpu_baseline": cpu,
         "parity": parity,
-        "aos": {"value": ncell / (r["ms_aos"] / 1e3), "ms_per_step": r["ms_aos"]},
+        "aos": {"value": ncell / (r["ms_aos"] / 1e3), "ms_per_step": r["ms_aos"],
+                "ms_per_step_median": float(np.median(r["extra"]["aos_per_step_ms"])),
+                "kernel": "pair kernel (the row kernel's per-lane loads of AoS planes conflict in shared memory)",
+                "clocks": r["extra"]["aos_clocks"]},
         "euler2d_fp64_128": {"ms_per_100_steps": r["ms2"], "us_per_step": r["ms2"] * 10.0,
-                             "cell_updates_per_s": 100 * 128 * 128 / (r["ms2"] / 1e3)},
+                             "cell_updates_per_s": 100 * 128 * 128 / (r["ms2"] / 1e3),
+                             "clocks": r["extra"]["euler2d_clocks"]},
         "eikonal": r["eik"],
         "batched": r["batched"],
         "serve": r["serve"],
