@@ -496,7 +496,7 @@ __device__ __forceinline__ void batch_fim_tile(FimSmem<T, 2>& sm, const BatchFim
     }
     if (lt == 0 && tid == 0) a.count[(k + 2) % 3] = 0u;
     long long visits = 0, updates = 0;
-    fim_visit_tile<T, 2>(sm, a, lt, k, visits, updates);
+    fim_visit_tile<T, 2>(sm, a, lt, k, visits, updates, FimFlagBook<T>{a, k});
     if (tid == 0 && visits) {
         atomicAdd(reinterpret_cast<unsigned long long*>(&d.counters[1]), (unsigned long long)visits);
         atomicAdd(reinterpret_cast<unsigned long long*>(&d.counters[2]), (unsigned long long)updates);
