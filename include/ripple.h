@@ -296,6 +296,14 @@ typedef struct {
                                  is the CFL limit of its whole state), with no barrier between
                                  problems or global steps.  Uses TMA staging whatever `staging`
                                  says.  0 = one launch per global step (default). */
+    int solo_rounds;          /* 1 = a problem that is the only resident one runs on the single-problem
+                                 kernels (Euler: up to 64 steps per round of the field sweep kernel;
+                                 eikonal, before its first batched iteration: one persistent FIM solve),
+                                 lowering the latency of requests served at low load.  Eikonal results
+                                 are bitwise those of batched rounds; Euler results agree to FP32
+                                 rounding (the field kernel orders its arithmetic differently), so
+                                 bitwise equality of a result alone and in a mix holds with 0.
+                                 Default 1. */
 } ripple_batch_config;
 
 typedef struct {
@@ -309,7 +317,7 @@ typedef struct {
 
 /* Set the batch configuration (defaults: SoA, 32x8, 16 steps per sync, graphs
  * on, F32, 4 FIM iterations per step, no cell budget, TMA staging, one launch
- * per global step).  Only while no request is in flight. */
+ * per global step, solo rounds on).  Only while no request is in flight. */
 RIPPLE_API ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* cfg);
 
 /* Queue n requests; tickets_out[i] identifies request i.  Validates every

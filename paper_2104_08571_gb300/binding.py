@@ -95,7 +95,8 @@ class ripple_ticket_info(ctypes.Structure):
 class ripple_batch_config(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int), ("tile_variant", ctypes.c_int), ("steps_per_sync", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("dtype", ctypes.c_int), ("fim_iters_per_step", ctypes.c_int),
-                ("active_cells", ctypes.c_int64), ("staging", ctypes.c_int), ("async_queue", ctypes.c_int)]
+                ("active_cells", ctypes.c_int64), ("staging", ctypes.c_int), ("async_queue", ctypes.c_int),
+                ("solo_rounds", ctypes.c_int)]
 
 
 class ripple_batch_stats(ctypes.Structure):
@@ -411,9 +412,11 @@ def _info_dict(info):
 
 
 def ripple_batch_configure(ctx, layout=RIPPLE_SOA, tile_variant=0, steps_per_sync=16, use_graphs=True,
-                           dtype=RIPPLE_F32, fim_iters_per_step=4, active_cells=0, staging=0, async_queue=False):
+                           dtype=RIPPLE_F32, fim_iters_per_step=4, active_cells=0, staging=0, async_queue=False,
+                           solo_rounds=True):
     cfg = ripple_batch_config(int(layout), int(tile_variant), int(steps_per_sync), int(bool(use_graphs)), int(dtype),
-                              int(fim_iters_per_step), int(active_cells), int(staging), int(bool(async_queue)))
+                              int(fim_iters_per_step), int(active_cells), int(staging), int(bool(async_queue)),
+                              int(bool(solo_rounds)))
     _check(load().ripple_batch_configure(ctx, ctypes.byref(cfg)), "ripple_batch_configure")
 
 
@@ -493,7 +496,7 @@ def ripple_batch_get_stats(ctx):
 def ripple_batch_autotune(ctx, sides, dtype=RIPPLE_F32):
     """Returns (chosen config dict, {(layout, variant): ms per global step})."""
     arr = (ctypes.c_int64 * len(sides))(*[int(x) for x in sides])
-    cfg = ripple_batch_config(RIPPLE_SOA, 0, 16, 1, int(dtype), 4, 0, 0, 0)
+    cfg = ripple_batch_config(RIPPLE_SOA, 0, 16, 1, int(dtype), 4, 0, 0, 0, 1)
     ms = (ctypes.c_double * 12)()
     _check(load().ripple_batch_autotune(ctx, arr, len(sides), int(dtype), ctypes.byref(cfg), ms),
            "ripple_batch_autotune")
@@ -504,4 +507,5 @@ def ripple_batch_autotune(ctx, sides, dtype=RIPPLE_F32):
                 timings[(lay, v, sg)] = ms[(sg * 2 + li) * 3 + v]
     return dict(layout=cfg.layout, tile_variant=cfg.tile_variant, steps_per_sync=cfg.steps_per_sync,
                 use_graphs=cfg.use_graphs, dtype=cfg.dtype, fim_iters_per_step=cfg.fim_iters_per_step,
-                active_cells=cfg.active_cells, staging=cfg.staging, async_queue=bool(cfg.async_queue)), timings
+                active_cells=cfg.active_cells, staging=cfg.staging, async_queue=bool(cfg.async_queue),
+                solo_rounds=bool(cfg.solo_rounds)), timings

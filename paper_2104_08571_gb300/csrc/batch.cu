@@ -170,6 +170,8 @@ struct Inst {
     bool stepped = false;       // taken part in a compute round
     CUtensorMap map[2];         // Euler: TMA maps of buf[0], buf[1] (cached per tile variant and layout)
     int map_key = -1;
+    CUtensorMap solo_map[2][2];  // Euler: staging (kind 0) and store (kind 1) maps of buf[0], buf[1] for the
+    int solo_v = -1;             // field sweep kernel of variant solo_v (solo rounds)
     cudaEvent_t ev = nullptr;
     ripple_status result = RIPPLE_OK;
     double t_submit = 0, t_admit = 0, t_start = 0, t_finish = 0;
@@ -189,7 +191,7 @@ struct BatchRuntime {
     std::deque<Inst*> pending;                      // guarded by mu
     std::unordered_map<uint64_t, Ticket> tickets;   // guarded by mu
     uint64_t next_ticket = 1;                       // guarded by mu
-    ripple_batch_config cfg{RIPPLE_SOA, 0, 16, 1, RIPPLE_F32, 4, 0, 0, 0};
+    ripple_batch_config cfg{RIPPLE_SOA, 0, 16, 1, RIPPLE_F32, 4, 0, 0, 0, 1};
     ripple_batch_stats stats{};                     // guarded by mu
     Clock::time_point epoch = Clock::now();
     // scheduler-thread state
@@ -358,7 +360,8 @@ static ripple_status admit(BatchRuntime* rt, Inst* in)
         in->ntx = (int)((dims[0] + TS - 1) / TS);
         in->nty = (int)((dims[1] + TS - 1) / TS);
         in->ntiles = in->ntx * in->nty;
-        in->scratch_bytes = 64 + (size_t)in->ntiles * 14;
+        // per-tile flags of the batched iterations, or the lists of a solo solve
+        in->scratch_bytes = std::max<size_t>(64 + (size_t)in->ntiles * 14, fim_list_scratch_bytes(in->ntiles));
         in->total_bytes = 2 * ((in->buf_bytes + 255) / 256 * 256) + (in->sbuf_bytes + 255) / 256 * 256 +
                           (in->scratch_bytes + 255) / 256 * 256;
     }
@@ -394,8 +397,12 @@ static ripple_status admit(BatchRuntime* rt, Inst* in)
     RIPPLE_CUDA(cudaMemsetAsync(&rt->slot_status[in->slot], 0, sizeof(unsigned long long), s));
     RIPPLE_CUDA(cudaMemsetAsync(&rt->slot_counters[in->slot * 3], 0, 3 * sizeof(long long), s));
     if (r.kind == RIPPLE_REQ_EULER) {
-        RIPPLE_CUDA(cudaMemsetAsync(in->buf[0], 0, in->buf_bytes, s));
+        // padding beyond the ghost layers reads NaN in both buffers (the field
+        // sweep kernel of solo rounds relies on it; the batched step ignores it)
+        const int pgrid = (int)std::min<long long>((in->g.px * in->g.py + 255) / 256, 4LL * rt->ctx->sm_count);
+        RIPPLE_CUDA(launch_pad_nan(dt, in->buf[0], in->g, pgrid, s));
         RIPPLE_CUDA(launch_interior_copy(dt, in->buf[0], in->g, in->buf[1], LAYOUT_SOA, 0, grid, s));
+        RIPPLE_CUDA(launch_pad_nan(dt, in->buf[1], in->g, pgrid, s));
         const double inv_dx[3] = {1.0 / r.fv.dx[0], 1.0 / r.fv.dx[1], 0.0};
         RIPPLE_CUDA(launch_prep(dt, 2, in->buf[0], &rt->slot_ctl[in->slot], in->g, (int)r.fv.bc, r.fv.gamma, inv_dx,
                                 0, grid, s));
@@ -697,6 +704,153 @@ static ripple_status launch_round_async(BatchRuntime* rt, int K, std::vector<lon
     return RIPPLE_OK;
 }
 
+// Move finished instances (Euler: all steps done; eikonal: a status word
+// set) from the resident set to their downloads.
+static void collect_finished(BatchRuntime* rt)
+{
+    std::vector<Inst*> keep;
+    for (Inst* in : rt->resident) {
+        bool fin = false;
+        if (in->req.kind == RIPPLE_REQ_EULER) fin = in->steps_done >= in->req.nsteps;
+        else fin = rt->h_status[in->slot] != 0ull;
+        if (!fin) {
+            keep.push_back(in);
+            continue;
+        }
+        const ripple_status st = start_download(rt, in);
+        if (st != RIPPLE_OK) {
+            release(rt, in);
+            finish(rt, in, st);
+            delete in;
+            continue;
+        }
+        rt->downloading.push_back(in);
+        rt->dirty = true;
+    }
+    rt->resident.swap(keep);
+}
+
+// Solo rounds: a problem that has the GPU to itself runs on the single-problem
+// kernels, whose per-problem cost is lower than the batched launches' (no
+// work-queue indirection, no launch wide enough for the whole resident set):
+//   * an Euler problem takes up to kSoloSteps steps of the field sweep kernel
+//     (the packed-pair kernel in FP32) on its own buffers and control block; the
+//     step conventions are those of the batched step (buffer parity = step
+//     parity, the 3-slot wave-speed ring indexed by the step), so the problem
+//     continues in batched rounds when others join;
+//   * an eikonal problem that has not iterated yet is solved whole by the
+//     persistent FIM kernel (lists of active tiles), one launch.
+// Requests arriving meanwhile are admitted after the round.
+constexpr long long kSoloSteps = 64;
+
+static ripple_status solo_round(BatchRuntime* rt, bool& handled)
+{
+    handled = false;
+    if (!rt->cfg.solo_rounds || rt->resident.size() != 1 || rt->cfg.async_queue) return RIPPLE_OK;
+    Inst* in = rt->resident[0];
+    const ripple_dtype dt = rt->cfg.dtype;
+    const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
+    cudaStream_t s = rt->compute;
+    FieldCtl* ctl = &rt->slot_ctl[in->slot];
+    if (in->req.kind == RIPPLE_REQ_EIKONAL) {
+        if (in->stepped) return RIPPLE_OK;  // already iterating in batched rounds
+        handled = true;
+        RIPPLE_CUDA(cudaEventRecord(rt->ev_r0, s));
+        const long long max_iters = in->req.eik.max_iters > 0 ? in->req.eik.max_iters : 1000000;
+        ripple_status st =
+            dt == RIPPLE_F32 ? fim_solve_lists<float, 2>(fim_problem<float>(in), in->scratch, ctl, max_iters,
+                                                         rt->ctx->sm_count, s)
+                             : fim_solve_lists<double, 2>(fim_problem<double>(in), in->scratch, ctl, max_iters,
+                                                          rt->ctx->sm_count, s);
+        if (st != RIPPLE_OK) return st;
+        RIPPLE_CUDA(cudaEventRecord(rt->ev_r1, s));
+        RIPPLE_CUDA(cudaMemcpyAsync(&rt->h_ctl[in->slot], ctl, sizeof(FieldCtl), cudaMemcpyDeviceToHost, s));
+        RIPPLE_CUDA(cudaEventSynchronize(rt->ev_r1));
+        RIPPLE_CUDA(cudaStreamSynchronize(s));
+        const FieldCtl& c = rt->h_ctl[in->slot];
+        const bool capped = (c.err & (DEV_ERR_TIMEOUT | DEV_ERR_BARRIER)) != 0u;
+        rt->h_status[in->slot] = ((unsigned long long)c.counters[0] << 2) | (capped ? 2ull : 1ull);
+        // the device words the download reads back
+        RIPPLE_CUDA(cudaMemcpyAsync(&rt->slot_status[in->slot], &rt->h_status[in->slot], sizeof(unsigned long long),
+                                    cudaMemcpyHostToDevice, s));
+        RIPPLE_CUDA(cudaMemcpyAsync(&rt->slot_counters[in->slot * 3], ctl->counters, 3 * sizeof(long long),
+                                    cudaMemcpyDeviceToDevice, s));
+        RIPPLE_CUDA(cudaEventRecord(rt->ev_step, s));
+        RIPPLE_CUDA(cudaEventSynchronize(rt->ev_step));
+    } else {
+        const int scheme = SCHEME_RUSANOV1;
+        int v = dt == RIPPLE_F32 && sweep_smem(dt, 2, layout, scheme, kPairVariant) > 0 ? kPairVariant : -1;
+        for (int c = 0; c < kNumSweepVariants && v < 0; ++c)
+            if (c != kRowVariant && sweep_smem(dt, 2, layout, scheme, c) > 0) v = c;
+        if (v < 0) return RIPPLE_OK;  // no field kernel for this configuration: batched rounds
+        handled = true;
+        const int tx = kSweepVariants[v].tx, ty = kSweepVariants[v].ty;
+        const ripple_layout rl = rt->cfg.layout;
+        if (in->solo_v != v) {
+            for (int b = 0; b < 2; ++b) {
+                ripple_status st = encode_plane_map(in->buf[b], in->g, rl, dt, 0, 1, tx, ty, &in->solo_map[b][0]);
+                if (st == RIPPLE_OK) st = encode_plane_map(in->buf[b], in->g, rl, dt, 1, 1, tx, ty, &in->solo_map[b][1]);
+                if (st != RIPPLE_OK) return st;
+            }
+            in->solo_v = v;
+        }
+        const ripple_request& r = in->req;
+        SweepLaunch L{};
+        L.sg.f = in->g;
+        L.sg.tiles_x = (int)((r.dims[0] + tx - 1) / tx);
+        L.sg.tiles_y = (int)((r.dims[1] + ty - 1) / ty);
+        L.sg.zchunk = 1;
+        L.sg.chunks_z = 1;
+        L.sg.items = L.sg.tiles_x * L.sg.tiles_y;
+        L.grid = std::min(L.sg.items, std::max(1, sweep_occ(dt, 2, layout, scheme, v)) * rt->ctx->sm_count);
+        L.ctl = ctl;
+        L.stream = s;
+        L.prm.gamma = r.fv.gamma;
+        L.prm.cfl = r.fv.cfl;
+        L.prm.inv_dx[0] = 1.0 / r.fv.dx[0];
+        L.prm.inv_dx[1] = 1.0 / r.fv.dx[1];
+        L.prm.inv_dx[2] = 0.0;
+        L.prm.gamma_f = (float)r.fv.gamma;
+        L.prm.gm1_f = (float)(r.fv.gamma - 1.0);
+        for (int d = 0; d < 3; ++d) L.prm.inv_dx_f[d] = (float)L.prm.inv_dx[d];
+        L.prm.bc = (int)r.fv.bc;
+        L.prm.axis = -1;
+        L.prm.last = 1;
+        const long long K = std::min<long long>(kSoloSteps, r.nsteps - in->steps_done);
+        RIPPLE_CUDA(cudaEventRecord(rt->ev_r0, s));
+        for (long long k = 0; k < K; ++k) {
+            const long long step = in->steps_done + k;
+            const int b = (int)(step & 1);
+            L.map_in = &in->solo_map[b][0];
+            L.map_out = &in->solo_map[1 - b][1];
+            L.out = in->buf[1 - b];
+            L.prm.slot_in = (int)(step % 3);
+            L.prm.first = step == 0;
+            RIPPLE_CUDA(sweep_launch(dt, 2, layout, scheme, v, L));
+        }
+        RIPPLE_CUDA(cudaEventRecord(rt->ev_r1, s));
+        RIPPLE_CUDA(cudaEventRecord(rt->ev_step, s));
+        RIPPLE_CUDA(cudaEventSynchronize(rt->ev_step));
+        in->steps_done += K;
+        // the batched step finds a problem's local step as (global step - start_step)
+        in->start_step -= K;
+        in->active = true;
+        rt->dirty = true;
+        std::lock_guard<std::mutex> lk(rt->mu);
+        rt->stats.launches += K;
+    }
+    in->stepped = true;
+    float round_ms = 0.f;
+    RIPPLE_CUDA(cudaEventElapsedTime(&round_ms, rt->ev_r0, rt->ev_r1));
+    {
+        std::lock_guard<std::mutex> lk(rt->mu);
+        rt->stats.device_s += 1e-3 * round_ms;
+        if (in->req.kind == RIPPLE_REQ_EIKONAL) rt->stats.launches += 1;
+    }
+    collect_finished(rt);
+    return RIPPLE_OK;
+}
+
 // One scheduler round of compute: K units over the resident set (K is the
 // configured cap, lowered so that no Euler problem runs past its last step),
 // or one dependency-driven round (up to K steps of every Euler problem).
@@ -776,26 +930,7 @@ static ripple_status compute_round(BatchRuntime* rt)
         rt->stats.fim_iterations = rt->gstep_f;
         rt->stats.device_s += 1e-3 * round_ms;
     }
-    std::vector<Inst*> keep;
-    for (Inst* in : rt->resident) {
-        bool fin = false;
-        if (in->req.kind == RIPPLE_REQ_EULER) fin = in->steps_done >= in->req.nsteps;
-        else fin = rt->h_status[in->slot] != 0ull;
-        if (!fin) {
-            keep.push_back(in);
-            continue;
-        }
-        st = start_download(rt, in);
-        if (st != RIPPLE_OK) {
-            release(rt, in);
-            finish(rt, in, st);
-            delete in;
-            continue;
-        }
-        rt->downloading.push_back(in);
-        rt->dirty = true;
-    }
-    rt->resident.swap(keep);
+    collect_finished(rt);
     return RIPPLE_OK;
 }
 
@@ -872,7 +1007,9 @@ static void scheduler(BatchRuntime* rt)
             continue;
         }
         if (!rt->resident.empty()) {
-            ripple_status st = compute_round(rt);
+            bool solo = false;
+            ripple_status st = solo_round(rt, solo);
+            if (st == RIPPLE_OK && !solo) st = compute_round(rt);
             if (st != RIPPLE_OK) {
                 // a CUDA failure: fail everything resident
                 for (Inst* in : rt->resident) {

@@ -243,10 +243,39 @@ using namespace ripple;
 
 void eik_scratch_free(ripple_field f) { eik_scratch_free_impl(f); }
 
-template <typename T, int DIM>
-static ripple_status run_fim(FimProblem<T>& a, EikArgs& e, ripple_ctx ctx, int ts)
+namespace ripple {
+size_t fim_list_scratch_bytes(int ntiles)
 {
-    cudaStream_t s = ctx->stream;
+    // count[3] + barrier[2] + take[3] u32 (64 bytes), list[3][ntiles] i32,
+    // state[ntiles] u32, mark[ntiles] u32
+    return (size_t)ntiles * 5 * 4 + 64;
+}
+
+template <typename T, int DIM>
+ripple_status fim_solve_lists(FimProblem<T> a, void* scratch, FieldCtl* ctl, long long max_iters, int sm_count,
+                              cudaStream_t s)
+{
+    constexpr int ts = EikTile<DIM>::TS;
+    char* base = static_cast<char*>(scratch);
+    a.count = reinterpret_cast<unsigned*>(base);
+    a.take = reinterpret_cast<unsigned*>(base + 32);
+    a.list = reinterpret_cast<int*>(base + 64);
+    a.state = reinterpret_cast<unsigned*>(base + 64 + (size_t)a.ntiles * 3 * 4);
+    a.mark = reinterpret_cast<unsigned*>(base + 64 + (size_t)a.ntiles * 4 * 4);
+    a.act = nullptr;
+    a.cur = nullptr;
+    EikArgs e{};
+    e.max_iters = max_iters > 0 ? max_iters : 1000000;
+    e.bar = reinterpret_cast<unsigned*>(base + 16);
+    e.spin_limit = kGridSpinLimit;
+    if (const char* lim = std::getenv("RIPPLE_GRID_SPIN_LIMIT")) {
+        char* end = nullptr;
+        const unsigned long v = std::strtoul(lim, &end, 10);
+        if (end != lim && v < kGridSpinLimit) e.spin_limit = (unsigned)v;
+    }
+    e.ctl = ctl;
+    RIPPLE_CUDA(cudaMemsetAsync(scratch, 0, fim_list_scratch_bytes(a.ntiles), s));
+    RIPPLE_CUDA(cudaMemsetAsync(ctl->counters, 0, sizeof(ctl->counters), s));
     auto kern = fim_kernel<T, DIM>;
     int per_sm = 0;
     RIPPLE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, EikTile<DIM>::NT, 0));
@@ -257,15 +286,20 @@ static ripple_status run_fim(FimProblem<T>& a, EikArgs& e, ripple_ctx ctx, int t
     // with four CTAs per SM); 3D solves have thousands of active tiles per
     // iteration and want every resident CTA (192^3: 2.2 ms against 4.2 ms)
     if (DIM == 2) per_sm = std::min(per_sm, kFimCtasPerSm2D);
-    int grid = std::min(per_sm * ctx->sm_count, a.ntiles);
+    int grid = std::min(per_sm * sm_count, a.ntiles);
     grid = std::max(grid, 1);
     const long long total = (long long)a.gT.n[0] * a.gT.n[1] * a.gT.n[2];
-    const int igrid = (int)std::min<long long>((total + 255) / 256, 8LL * ctx->sm_count);
+    const int igrid = (int)std::min<long long>((total + 255) / 256, 8LL * sm_count);
     RIPPLE_CUDA(launch_fim_init<T>(a, ts, igrid, s));
     void* args[] = {&a, &e};
     RIPPLE_CUDA(cudaLaunchCooperativeKernel((const void*)kern, dim3(grid), dim3(EikTile<DIM>::NT), args, 0, s));
     return RIPPLE_OK;
 }
+template ripple_status fim_solve_lists<float, 2>(FimProblem<float>, void*, FieldCtl*, long long, int, cudaStream_t);
+template ripple_status fim_solve_lists<double, 2>(FimProblem<double>, void*, FieldCtl*, long long, int, cudaStream_t);
+template ripple_status fim_solve_lists<float, 3>(FimProblem<float>, void*, FieldCtl*, long long, int, cudaStream_t);
+template ripple_status fim_solve_lists<double, 3>(FimProblem<double>, void*, FieldCtl*, long long, int, cudaStream_t);
+}  // namespace ripple
 
 extern "C" ripple_status ripple_eikonal_solve(ripple_field S, ripple_field Tf, const int64_t* src, int nsrc,
                                               const ripple_eik_params* p, ripple_eik_stats* stats)
@@ -287,9 +321,7 @@ extern "C" ripple_status ripple_eikonal_solve(ripple_field S, ripple_field Tf, c
     ripple_ctx ctx = Tf->ctx;
     st = ensure_second_buffer(Tf);
     if (st != RIPPLE_OK) return st;
-    // scratch: count[3] + barrier[2] + take[3] u32 (64 bytes), list[3][ntiles] i32,
-    // state[ntiles] u32, mark[ntiles] u32
-    const size_t need = (size_t)ntiles * 5 * 4 + 64;
+    const size_t need = fim_list_scratch_bytes(ntiles);
     if (!Tf->eik || Tf->eik->bytes < need) {
         eik_scratch_free(Tf);
         Tf->eik = new EikScratch();
@@ -302,20 +334,8 @@ extern "C" ripple_status ripple_eikonal_solve(ripple_field S, ripple_field Tf, c
         Tf->eik->bytes = need;
         Tf->eik->ntiles = ntiles;
     }
-    char* base = static_cast<char*>(Tf->eik->mem);
-    EikArgs e{};
-    e.max_iters = p->max_iters > 0 ? p->max_iters : 1000000;
-    e.bar = reinterpret_cast<unsigned*>(base + 16);
-    e.spin_limit = kGridSpinLimit;
-    if (const char* lim = std::getenv("RIPPLE_GRID_SPIN_LIMIT")) {
-        char* end = nullptr;
-        const unsigned long v = std::strtoul(lim, &end, 10);
-        if (end != lim && v < kGridSpinLimit) e.spin_limit = (unsigned)v;
-    }
-    e.ctl = Tf->ctl;
     cudaStream_t s = ctx->stream;
-    RIPPLE_CUDA(cudaMemsetAsync(Tf->eik->mem, 0, need, s));
-    RIPPLE_CUDA(cudaMemsetAsync(Tf->ctl->counters, 0, sizeof(Tf->ctl->counters), s));
+    const long long max_iters = p->max_iters > 0 ? p->max_iters : 1000000;
     auto fill = [&](auto& a) {
         using TT = std::remove_pointer_t<decltype(a.slow)>;
         using TV = std::remove_const_t<TT>;
@@ -330,22 +350,18 @@ extern "C" ripple_status ripple_eikonal_solve(ripple_field S, ripple_field Tf, c
             for (int d = 0; d < 3; ++d) a.src[q][d] = srcc[q][d];
         a.h = p->h;
         a.tol = p->tol;
-        a.count = reinterpret_cast<unsigned*>(base);
-        a.take = reinterpret_cast<unsigned*>(base + 32);
-        a.list = reinterpret_cast<int*>(base + 64);
-        a.state = reinterpret_cast<unsigned*>(base + 64 + (size_t)ntiles * 3 * 4);
-        a.mark = reinterpret_cast<unsigned*>(base + 64 + (size_t)ntiles * 4 * 4);
-        a.act = nullptr;
-        a.cur = nullptr;
     };
+    void* mem = Tf->eik->mem;
     if (Tf->dtype == RIPPLE_F32) {
         FimProblem<float> a{};
         fill(a);
-        st = ndim == 2 ? run_fim<float, 2>(a, e, ctx, ts) : run_fim<float, 3>(a, e, ctx, ts);
+        st = ndim == 2 ? fim_solve_lists<float, 2>(a, mem, Tf->ctl, max_iters, ctx->sm_count, s)
+                       : fim_solve_lists<float, 3>(a, mem, Tf->ctl, max_iters, ctx->sm_count, s);
     } else {
         FimProblem<double> a{};
         fill(a);
-        st = ndim == 2 ? run_fim<double, 2>(a, e, ctx, ts) : run_fim<double, 3>(a, e, ctx, ts);
+        st = ndim == 2 ? fim_solve_lists<double, 2>(a, mem, Tf->ctl, max_iters, ctx->sm_count, s)
+                       : fim_solve_lists<double, 3>(a, mem, Tf->ctl, max_iters, ctx->sm_count, s);
     }
     if (st != RIPPLE_OK) return st;
     Tf->cur = 0;

@@ -291,17 +291,17 @@ static int grid_for(ripple_ctx ctx, long long work, int per_block)
 
 // Euler step dispatch -------------------------------------------------------
 
-static cudaError_t sweep_launch(ripple_dtype dt, int dim, int layout, int scheme, int v, const SweepLaunch& L)
+cudaError_t sweep_launch(ripple_dtype dt, int dim, int layout, int scheme, int v, const SweepLaunch& L)
 {
     if (dt == RIPPLE_F32) return dim == 2 ? sweep_launch_f32_2d(layout, scheme, v, L) : sweep_launch_f32_3d(layout, scheme, v, L);
     return dim == 2 ? sweep_launch_f64_2d(layout, scheme, v, L) : sweep_launch_f64_3d(layout, scheme, v, L);
 }
-static int sweep_smem(ripple_dtype dt, int dim, int layout, int scheme, int v)
+int sweep_smem(ripple_dtype dt, int dim, int layout, int scheme, int v)
 {
     if (dt == RIPPLE_F32) return dim == 2 ? sweep_smem_f32_2d(layout, scheme, v) : sweep_smem_f32_3d(layout, scheme, v);
     return dim == 2 ? sweep_smem_f64_2d(layout, scheme, v) : sweep_smem_f64_3d(layout, scheme, v);
 }
-static int sweep_occ(ripple_dtype dt, int dim, int layout, int scheme, int v)
+int sweep_occ(ripple_dtype dt, int dim, int layout, int scheme, int v)
 {
     if (dt == RIPPLE_F32) return dim == 2 ? sweep_occ_f32_2d(layout, scheme, v) : sweep_occ_f32_3d(layout, scheme, v);
     return dim == 2 ? sweep_occ_f64_2d(layout, scheme, v) : sweep_occ_f64_3d(layout, scheme, v);

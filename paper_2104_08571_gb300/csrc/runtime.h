@@ -58,6 +58,23 @@ cudaError_t sweep_launch_f32_2d(int layout, int scheme, int v, const SweepLaunch
 cudaError_t sweep_launch_f32_3d(int layout, int scheme, int v, const SweepLaunch& L);
 cudaError_t sweep_launch_f64_2d(int layout, int scheme, int v, const SweepLaunch& L);
 cudaError_t sweep_launch_f64_3d(int layout, int scheme, int v, const SweepLaunch& L);
+// Dispatch by element type and dimension (runtime.cu).
+cudaError_t sweep_launch(ripple_dtype dt, int dim, int layout, int scheme, int v, const SweepLaunch& L);
+int sweep_smem(ripple_dtype dt, int dim, int layout, int scheme, int v);
+int sweep_occ(ripple_dtype dt, int dim, int layout, int scheme, int v);
+
+// One eikonal solve by the persistent FIM kernel with lists of active tiles
+// (eikonal.cu), queued on s: zeroes `scratch` (fim_list_scratch_bytes bytes)
+// and ctl's solver counters, initialises both T buffers and the first list,
+// launches the cooperative solve; the result is in buf[0], the iterations,
+// tile visits and Godunov updates in ctl->counters[0..2], errors in ctl->err.
+template <typename T>
+struct FimProblem;
+size_t fim_list_scratch_bytes(int ntiles);
+template <typename T, int DIM>
+ripple_status fim_solve_lists(FimProblem<T> a, void* scratch, FieldCtl* ctl, long long max_iters, int sm_count,
+                              cudaStream_t s);
+
 // Dynamic shared memory of a sweep variant (0 if it does not fit).
 int sweep_smem_f32_2d(int layout, int scheme, int v);
 int sweep_smem_f32_3d(int layout, int scheme, int v);

@@ -20,6 +20,9 @@ def ctx():
     import torch
     assert torch.cuda.is_available()
     c = R.ripple_ctx_create(0)
+    # the tests of this file compare batched rounds with one another bit for bit:
+    # a lone problem stays on the batched kernels (solo rounds have their own test)
+    R.ripple_batch_configure(c, solo_rounds=False)
     yield c
     R.ripple_ctx_destroy(c)
 
@@ -33,6 +36,13 @@ def _eik(nx, ny, seed):
     s = inputs.eikonal_slowness((nx, ny), seed=seed).astype(np.float32)
     src = inputs.eikonal_sources((nx, ny), seed=seed)
     return R.eikonal_request(s, src, 1.0 / max(nx, ny))
+
+
+def _again(req):
+    """A fresh request with the same input as req (Euler or eikonal)."""
+    if req["kind"] == R.RIPPLE_REQ_EULER:
+        return R.euler_request(req["input"], req["nsteps"], req["dx"], bc=req.get("bc", R.RIPPLE_BC_PERIODIC))
+    return R.eikonal_request(req["input"], req["sources"], req["h"])
 
 
 def _run(ctx, reqs, timeout_ms=120000):
@@ -66,6 +76,8 @@ def test_batch_eikonal_matches_fmm(ctx):
 
 
 def test_alone_equals_in_mix_bitwise(ctx):
+    # every problem on the batched kernels (a lone problem too): same bits alone and in the mix
+    R.ripple_batch_configure(ctx, solo_rounds=False)
     a = _euler(90, 70, 0.25, 37)
     e = _eik(120, 80, 5)
     _run(ctx, [a])
@@ -79,12 +91,42 @@ def test_alone_equals_in_mix_bitwise(ctx):
     assert np.array_equal(a2["output"], alone_a)
     assert np.array_equal(e2["output"], alone_e)
     # with a small per-step cell budget problems are paused and resumed: same bits
-    R.ripple_batch_configure(ctx, active_cells=5000, steps_per_sync=5)
+    R.ripple_batch_configure(ctx, active_cells=5000, steps_per_sync=5, solo_rounds=False)
     a3 = R.euler_request(a["input"], 37, a["dx"])
     mix = [_euler(64, 64, 0.1, 80), a3, _euler(300, 40, 0.2, 15), _euler(33, 33, 0.3, 50)]
     infos = _run(ctx, mix)
     assert all(i["status"] == R.RIPPLE_OK and i["work"] == r["nsteps"] for i, r in zip(infos, mix))
     assert np.array_equal(a3["output"], alone_a)
+
+
+def test_solo_rounds_alone_and_in_mix(ctx):
+    """A request served alone runs on the single-problem kernels (solo rounds):
+    an Euler problem within FP32 rounding of the same problem in a mix (batched
+    kernel), also when it is joined by other requests part-way (it then
+    continues on the batched kernel from its own step); an eikonal problem with
+    the same bits; both against the oracle."""
+    R.ripple_batch_configure(ctx)  # solo rounds on (the default)
+    a = _euler(150, 130, 0.25, 150)
+    e = _eik(200, 170, 8)
+    _run(ctx, [a])
+    _run(ctx, [e])
+    mix = [_again(a), _euler(64, 64, 0.1, 40), _again(e), _euler(40, 40, 0.2, 20)]
+    infos = _run(ctx, mix)
+    assert all(i["status"] == R.RIPPLE_OK for i in infos)
+    assert rel_l1(mix[0]["output"], a["output"]) <= 1e-6
+    assert np.array_equal(mix[2]["output"], e["output"])
+    assert_parity(a["output"], _oracle_euler(a), 2e-5, LINF_F32)
+    # joined part-way: a long problem alone, a second one submitted while it runs
+    long = _euler(300, 260, 0.2, 400)
+    t1 = R.ripple_batch_submit(ctx, [long])
+    time.sleep(0.002)
+    late = _euler(50, 50, 0.15, 30)
+    t2 = R.ripple_batch_submit(ctx, [late])
+    assert R.ripple_wait(ctx, t1[0], 120000)["status"] == R.RIPPLE_OK
+    assert R.ripple_wait(ctx, t2[0], 120000)["status"] == R.RIPPLE_OK
+    assert_parity(long["output"], _oracle_euler(long), 2e-5, LINF_F32)
+    assert_parity(late["output"], _oracle_euler(late), 2e-5, LINF_F32)
+    R.ripple_batch_configure(ctx, solo_rounds=False)
 
 
 def test_batch_matches_single_field_sweep(ctx):
@@ -101,9 +143,10 @@ def test_batch_matches_single_field_sweep(ctx):
 
 
 def test_graphs_and_sync_interval_do_not_change_results(ctx):
+    R.ripple_batch_configure(ctx, solo_rounds=False)
     reqs1 = [_euler(70, 50, 0.2, 33), _eik(90, 90, 7)]
     _run(ctx, reqs1)
-    R.ripple_batch_configure(ctx, steps_per_sync=3, use_graphs=False, fim_iters_per_step=1)
+    R.ripple_batch_configure(ctx, steps_per_sync=3, use_graphs=False, fim_iters_per_step=1, solo_rounds=False)
     reqs2 = [R.euler_request(reqs1[0]["input"], 33, reqs1[0]["dx"]),
              R.eikonal_request(reqs1[1]["input"], reqs1[1]["sources"], reqs1[1]["h"])]
     _run(ctx, reqs2)
@@ -117,11 +160,11 @@ def test_aos_layout_tile_variants_and_staging(ctx):
     for staging in (0, 1):
         for layout in (R.RIPPLE_SOA, R.RIPPLE_AOS):
             for v in range(3):
-                R.ripple_batch_configure(ctx, layout=layout, tile_variant=v, staging=staging)
+                R.ripple_batch_configure(ctx, layout=layout, tile_variant=v, staging=staging, solo_rounds=False)
                 r = R.euler_request(base["input"], 21, base["dx"])
                 _run(ctx, [r])
                 assert rel_l1(r["output"], base["output"]) <= 1e-6
-    R.ripple_batch_configure(ctx)
+    R.ripple_batch_configure(ctx, solo_rounds=False)
 
 
 def test_budget_admission_waits_for_memory():
@@ -144,7 +187,7 @@ def test_budget_admission_waits_for_memory():
 
 
 def test_requests_arriving_while_others_run(ctx):
-    R.ripple_batch_configure(ctx, steps_per_sync=2)
+    R.ripple_batch_configure(ctx, steps_per_sync=2, solo_rounds=False)
     first = [_euler(256, 256, 0.2, 3000), _eik(300, 300, 8)]
     t_first = R.ripple_batch_submit(ctx, first)
     time.sleep(0.005)

@@ -22,6 +22,9 @@ def ctx():
     import torch
     assert torch.cuda.is_available()
     c = R.ripple_ctx_create(0)
+    # the tests of this file compare batched rounds with one another bit for bit:
+    # a lone problem stays on the batched kernels (solo rounds have their own test)
+    R.ripple_batch_configure(c, solo_rounds=False)
     yield c
     R.ripple_ctx_destroy(c)
 
@@ -53,7 +56,7 @@ def test_async_rounds_equal_per_step_launches_bitwise(ctx):
     infos = _run(ctx, ref)
     assert all(i["status"] == R.RIPPLE_OK for i in infos)
     for sps in (64, 7, 1):
-        R.ripple_batch_configure(ctx, steps_per_sync=sps, async_queue=True)
+        R.ripple_batch_configure(ctx, steps_per_sync=sps, async_queue=True, solo_rounds=False)
         reqs = [_again(r) for r in ref]
         infos = _run(ctx, reqs)
         for r, q, i in zip(ref, reqs, infos):
@@ -62,7 +65,7 @@ def test_async_rounds_equal_per_step_launches_bitwise(ctx):
 
 
 def test_async_rounds_match_oracle(ctx):
-    R.ripple_batch_configure(ctx, steps_per_sync=128, async_queue=True)
+    R.ripple_batch_configure(ctx, steps_per_sync=128, async_queue=True, solo_rounds=False)
     reqs = _mix()
     infos = _run(ctx, reqs)
     for req, info in zip(reqs, infos):
@@ -76,14 +79,14 @@ def test_one_launch_per_round(ctx):
     # uneven step counts: per-step launches shrink a round to the shortest
     # remaining problem; a dependency-driven round runs each to its own end
     reqs = [_euler(64 + 8 * i, 48, 0.1 + 0.01 * i, 5 + 7 * i) for i in range(8)]
-    R.ripple_batch_configure(ctx, steps_per_sync=64, async_queue=True, use_graphs=False)
+    R.ripple_batch_configure(ctx, steps_per_sync=64, async_queue=True, use_graphs=False, solo_rounds=False)
     s0 = R.ripple_batch_get_stats(ctx)
     infos = _run(ctx, reqs)
     s1 = R.ripple_batch_get_stats(ctx)
     assert all(i["status"] == R.RIPPLE_OK for i in infos)
     assert s1["launches"] - s0["launches"] == 1
     assert s1["global_steps"] - s0["global_steps"] == max(r["nsteps"] for r in reqs)
-    R.ripple_batch_configure(ctx, steps_per_sync=64, async_queue=False, use_graphs=False)
+    R.ripple_batch_configure(ctx, steps_per_sync=64, async_queue=False, use_graphs=False, solo_rounds=False)
     again = [_again(r) for r in reqs]
     s2 = R.ripple_batch_get_stats(ctx)
     _run(ctx, again)
@@ -98,17 +101,17 @@ def test_async_layouts_and_tile_shapes(ctx):
     _run(ctx, [base])
     for layout in (R.RIPPLE_SOA, R.RIPPLE_AOS):
         for v in range(3):
-            R.ripple_batch_configure(ctx, layout=layout, tile_variant=v, async_queue=True)
+            R.ripple_batch_configure(ctx, layout=layout, tile_variant=v, async_queue=True, solo_rounds=False)
             r = _again(base)
             other = _euler(150, 40, 0.3, 33)
             infos = _run(ctx, [r, other])
             assert all(i["status"] == R.RIPPLE_OK for i in infos)
             assert rel_l1(r["output"], base["output"]) <= 1e-6
-    R.ripple_batch_configure(ctx)
+    R.ripple_batch_configure(ctx, solo_rounds=False)
 
 
 def test_async_with_eikonal_requests(ctx):
-    R.ripple_batch_configure(ctx, steps_per_sync=16, async_queue=True)
+    R.ripple_batch_configure(ctx, steps_per_sync=16, async_queue=True, solo_rounds=False)
     s = inputs.eikonal_slowness((120, 90), seed=4).astype(np.float32)
     src = inputs.eikonal_sources((120, 90), seed=4)
     e = R.eikonal_request(s, src, 1.0 / 120)
@@ -117,7 +120,7 @@ def test_async_with_eikonal_requests(ctx):
     assert all(i["status"] == R.RIPPLE_OK for i in infos)
     ref = oracle.eikonal_fmm(s.astype(np.float64), 1.0 / 120, src)
     assert_parity(e["output"][None], ref[None], 1e-4, LINF_EIK)
-    R.ripple_batch_configure(ctx)
+    R.ripple_batch_configure(ctx, solo_rounds=False)
     alone = _again(a)
     _run(ctx, [alone])
     assert np.array_equal(alone["output"], a["output"])
@@ -125,13 +128,13 @@ def test_async_with_eikonal_requests(ctx):
 
 def test_async_with_cell_budget_and_late_requests(ctx):
     # a per-round cell budget: problems join the stepped set as others finish
-    R.ripple_batch_configure(ctx, steps_per_sync=8, async_queue=True, active_cells=64 * 64 * 2)
+    R.ripple_batch_configure(ctx, steps_per_sync=8, async_queue=True, active_cells=64 * 64 * 2, solo_rounds=False)
     reqs = [_euler(64, 64, 0.1 + 0.03 * i, 12 + 5 * i) for i in range(5)]
     t1 = R.ripple_batch_submit(ctx, reqs[:3])
     t2 = R.ripple_batch_submit(ctx, reqs[3:])
     infos = [R.ripple_wait(ctx, t, 120000) for t in t1 + t2]
     assert all(i["status"] == R.RIPPLE_OK and i["work"] == r["nsteps"] for i, r in zip(infos, reqs))
-    R.ripple_batch_configure(ctx)
+    R.ripple_batch_configure(ctx, solo_rounds=False)
     for r in reqs:
         b = _again(r)
         _run(ctx, [b])
@@ -139,7 +142,7 @@ def test_async_with_cell_budget_and_late_requests(ctx):
 
 
 def test_async_numeric_error_reported_per_request(ctx):
-    R.ripple_batch_configure(ctx, steps_per_sync=16, async_queue=True)
+    R.ripple_batch_configure(ctx, steps_per_sync=16, async_queue=True, solo_rounds=False)
     bad = _euler(40, 40, 0.2, 5)
     bad["input"][3, 10, 10] = -1.0  # negative energy -> negative pressure
     good = _euler(40, 40, 0.2, 9)
