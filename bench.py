@@ -529,9 +529,10 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
 
 
 def bench_force_split(R, torch, local, par=None, legs=None):
-    """The paper's own Euler solver (dimensionally split x then y sweeps, FORCE
-    face flux): 2D FP32 8192^2 periodic sine density (a Table flux size), and
-    the 2D FP64 128^2 workload.  One step = one sweep per axis."""
+    """The paper's own Euler solver (dimensionally split sweeps, x then y [then
+    z], FORCE face flux), one sweep launch per axis: 2D FP32 8192^2 periodic sine
+    density (a Table flux size), 3D FP32 256^3 blast (the headline state,
+    transmissive), and the 2D FP64 128^2 workload."""
     ctx = R.ripple_ctx_create(local)
     R.use_torch_allocator(ctx, local)
     stream = torch.cuda.Stream(device=local)
@@ -539,12 +540,19 @@ def bench_force_split(R, torch, local, par=None, legs=None):
     out = {}
     try:
         if legs is None:
-            legs = (("fp32_8192", 8192, R.RIPPLE_F32, 20), ("fp64_128", 128, R.RIPPLE_F64, 100))
-        for name, n, dtype, steps in legs:
+            legs = (("fp32_8192", 2, 8192, R.RIPPLE_F32, 20), ("fp32_3d_256", 3, 256, R.RIPPLE_F32, 10),
+                    ("fp64_128", 2, 128, R.RIPPLE_F64, 100))
+        for name, ndim, n, dtype, steps in legs:
             npdt = np.float32 if dtype == R.RIPPLE_F32 else np.float64
-            U0 = inputs.euler2d_sine(n).astype(npdt)
-            f = R.ripple_field_create(ctx, (n, n), 4, R.RIPPLE_SOA, 1, dtype)
-            prm = R.make_fv_params([1.0 / n] * 2, scheme=R.RIPPLE_FORCE_SPLIT)
+            if ndim == 2:
+                U0 = inputs.euler2d_sine(n).astype(npdt)
+                bc = R.RIPPLE_BC_PERIODIC
+            else:
+                U0 = inputs.euler3d_blast(n, seed=1).astype(npdt)
+                bc = R.RIPPLE_BC_TRANSMISSIVE
+            nc = ndim + 2
+            f = R.ripple_field_create(ctx, (n,) * ndim, nc, R.RIPPLE_SOA, 1, dtype)
+            prm = R.make_fv_params([1.0 / n] * ndim, scheme=R.RIPPLE_FORCE_SPLIT, bc=bc)
             R.ripple_field_upload(f, U0)
             R.ripple_fv_step(f, prm, 3)
             torch.cuda.synchronize()
@@ -556,11 +564,12 @@ def bench_force_split(R, torch, local, par=None, legs=None):
                 torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / steps
             R.ripple_fv_step(f, prm, 0)
-            es = 16 if dtype == R.RIPPLE_F32 else 32
-            gbs = 2 * 2 * es * n * n / (ms / 1e3) / 1e9  # two sweeps, each reads and writes the state
-            out[name] = {"cells": n * n, "ms_per_step": ms, "cell_updates_per_s": n * n / (ms / 1e3),
-                         "launches_per_step": 2, "GB_s_algorithmic": gbs, "hbm_frac": gbs / load_peaks()[0],
-                         "clocks": clk_f.summary()}
+            es = nc * (4 if dtype == R.RIPPLE_F32 else 8)
+            cells = n ** ndim
+            gbs = ndim * 2 * es * cells / (ms / 1e3) / 1e9  # each sweep reads and writes the state
+            out[name] = {"cells": cells, "ms_per_step": ms, "cell_updates_per_s": cells / (ms / 1e3),
+                         "launches_per_step": ndim, "algorithmic_bytes_per_cell_update": ndim * 2 * es,
+                         "GB_s_algorithmic": gbs, "hbm_frac": gbs / load_peaks()[0], "clocks": clk_f.summary()}
             if name == "fp32_8192":
                 out[name]["paper_v100_flux_difference_ms_8k"] = {"ripple_s": 3.5533, "ripple_c": 5.5284,
                                                                    "kokkos": 12.919}
@@ -568,6 +577,17 @@ def bench_force_split(R, torch, local, par=None, legs=None):
                 R.ripple_field_upload(f, U0)
                 R.ripple_fv_step(f, prm, 100)
                 par["force_split_fp64_128"] = dict(U0=U0, gpu=R.ripple_field_download(f))
+            R.ripple_field_destroy(f)
+        if par is not None:
+            # the 3D FP32 split step on the walk sweeps: the whole 128^3 blast after
+            # 10 steps, for the oracle's run of the same state
+            n1 = 128
+            U1 = inputs.euler3d_blast(n1, seed=1).astype(np.float32)
+            f = R.ripple_field_create(ctx, (n1,) * 3, 5, R.RIPPLE_SOA, 1, R.RIPPLE_F32)
+            R.ripple_field_upload(f, U1)
+            R.ripple_fv_step(f, R.make_fv_params([1.0 / n1] * 3, scheme=R.RIPPLE_FORCE_SPLIT,
+                                                 bc=R.RIPPLE_BC_TRANSMISSIVE), 10)
+            par["force_split_fp32_3d_128"] = dict(U0=U1, gpu=R.ripple_field_download(f), n=n1)
             R.ripple_field_destroy(f)
     finally:
         R.ripple_ctx_destroy(ctx)
@@ -805,6 +825,24 @@ def oracle_legs(par):
             "elementwise_tolerance": 5e-5, "t_rel_diff": abs(p["t"] - info["t"]) / info["t"],
             "check": f"whole {n1}^3 field after {NSTEPS_SOLVE} steps from the initial blast (SoA, the headline kernel)",
             "oracle_cell_updates_per_s": n1 ** 3 * NSTEPS_SOLVE / t, "oracle_threads": nt, "oracle_seconds": t}
+    if "force_split_fp32_3d_128" in par:
+        p = par["force_split_fp32_3d_128"]
+        nt = oracle.set_threads(os.cpu_count() or 1)
+        try:
+            t0 = time.perf_counter()
+            ref, _ = oracle.euler_run(p["U0"].astype(np.float64), 10, scheme=oracle.FORCE_SPLIT,
+                                      bc=oracle.TRANSMISSIVE)
+            t = time.perf_counter() - t0
+        finally:
+            oracle.set_threads(1)
+        g = np.asarray(p["gpu"], dtype=np.float64).reshape(5, -1)
+        r_ = ref.reshape(5, -1)
+        out["force_split_fp32_3d_128"] = {
+            "rel_l1_vs_oracle": rel_l1(p["gpu"], ref), "tolerance": 2e-5,
+            "max_elementwise_rel": float((np.abs(g - r_).max(1) / np.abs(r_).max(1)).max()),
+            "elementwise_tolerance": 5e-5,
+            "check": "whole 128^3 blast after 10 split FORCE steps (x, y, z walk sweeps)",
+            "oracle_cell_updates_per_s": p["n"] ** 3 * 10 / t, "oracle_threads": nt, "oracle_seconds": t}
     if "force_split_fp64_128" in par:
         p = par["force_split_fp64_128"]
         t0 = time.perf_counter()
@@ -862,8 +900,9 @@ def main():
                     help="time only the SoA sweep (a small case for profiling; not the headline line)")
     ap.add_argument("--sweep-dims", type=int, nargs=3, default=[N3, N3, N3], metavar=("NX", "NY", "NZ"))
     ap.add_argument("--force-only", action="store_true",
-                    help="time only the split FORCE step, 2D FP32 SoA (profiling; not the headline line)")
+                    help="time only the split FORCE step, FP32 SoA (profiling; not the headline line)")
     ap.add_argument("--force-n", type=int, default=8192)
+    ap.add_argument("--force-dim", type=int, default=2, choices=[2, 3])
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 512-instance batched workload (profiling; not the headline line)")
     ap.add_argument("--eikonal-only", action="store_true",
@@ -920,10 +959,12 @@ def main():
         import torch
         import paper_2104_08571_gb300 as R
         torch.cuda.set_device(local)
-        fs = bench_force_split(R, torch, local, legs=(("fp32", args.force_n, R.RIPPLE_F32, args.steps),))
+        fs = bench_force_split(R, torch, local, legs=(("fp32", args.force_dim, args.force_n, R.RIPPLE_F32,
+                                                       args.steps),))
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": fs["fp32"]["cell_updates_per_s"], "unit": METRIC,
-                              "n_gpus": world, "config": {"workload": f"force_split_2d_fp32_{args.force_n}^2_sine"},
+                              "n_gpus": world,
+                              "config": {"workload": f"force_split_{args.force_dim}d_fp32_{args.force_n}^{args.force_dim}"},
                               "force_split": fs}))
         return
     if args.serve_only:

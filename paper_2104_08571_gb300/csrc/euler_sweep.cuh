@@ -55,12 +55,15 @@ struct SweepGeom {
     int items;  // tiles_x * tiles_y * chunks_z
 };
 
-// Strip walks of a one-axis sweep (euler_force_walk.cuh): walk w covers `seg`
-// cells of row w / nseg from x = (w % nseg) * seg (x sweep), or `seg` rows of
-// the 64-column strip w % nstrips from y = (w / nstrips) * seg (y sweep).
+// Strip walks of a one-axis sweep (euler_force_walk.cuh).  x sweep: walk w
+// covers `seg` cells of row w / nseg (rows of all y, then z) from
+// x = (w % nseg) * seg.  y or z sweep: walk w covers `seg` rows along the
+// swept axis of the 64-column strip w % nstrips, on line (w / nstrips) % nlines
+// (the z plane of a y sweep, the y row of a z sweep; 1 line in 2D), from
+// ((w / nstrips) / nlines) * seg.
 struct WalkGeom {
     FieldGeom f;
-    int seg, nseg, nstrips, walks;
+    int seg, nseg, nstrips, nlines, walks;
 };
 constexpr int kWalkWarps = 8;  // walks in flight per CTA (one per warp)
 

@@ -566,30 +566,35 @@ ripple_status ripple_field_set_sweep(ripple_field f, int variant, int zchunk)
     return RIPPLE_OK;
 }
 
-// Walks of a one-axis sweep of a 2D field (euler_force_walk.cuh): about 16 per
-// resident warp, so that the grid-stride walks spread evenly over the SMs, and
-// at least 4 chunks (x) or 16 rows (y) long, so that the first face of a walk
-// (evaluated by the walk before it too) stays a few per cent of the arithmetic.
+// Walks of a one-axis sweep (euler_force_walk.cuh): about 16 per resident
+// warp, so that the grid-stride walks spread evenly over the SMs, and at least
+// 4 chunks (x) or 16 rows (y, z) long, so that the face a walk shares with the
+// walk before it (evaluated by both) stays a small part of the arithmetic.
 static WalkGeom walk_geom(const FieldGeom& g, int axis, long long resident_warps)
 {
     WalkGeom w{};
     w.f = g;
     const long long target = std::max(1LL, 16 * resident_warps);
-    const long long nch = (g.n[0] + 63) / 64, ny = g.n[1];
+    const long long nch = (g.n[0] + 63) / 64;
+    const long long nyz = (long long)g.n[1] * (g.ndim == 3 ? g.n[2] : 1);  // rows of the x sweep
     if (axis == 0) {
-        long long cpw = nch * ny / target;
+        long long cpw = nch * nyz / target;
         cpw = std::max(std::min(cpw, nch), std::min(4LL, nch));
         w.seg = (int)(64 * cpw);
         w.nseg = (int)((nch + cpw - 1) / cpw);
         w.nstrips = 0;
-        w.walks = (int)(w.nseg * ny);
+        w.nlines = 1;
+        w.walks = (int)(w.nseg * nyz);
     } else {
-        long long rows = nch * ny / target;
-        rows = std::max(std::min(rows, ny), std::min(16LL, ny));
+        const long long na = g.n[axis];
+        const long long lines = g.ndim == 3 ? g.n[axis == 1 ? 2 : 1] : 1;
+        long long rows = nch * lines * na / target;
+        rows = std::max(std::min(rows, na), std::min(16LL, na));
         w.seg = (int)rows;
-        w.nseg = (int)((ny + rows - 1) / rows);
+        w.nseg = (int)((na + rows - 1) / rows);
         w.nstrips = (int)nch;
-        w.walks = (int)(w.nseg * nch);
+        w.nlines = (int)lines;
+        w.walks = (int)(w.nseg * nch * lines);
     }
     return w;
 }
@@ -699,12 +704,12 @@ ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t 
     // one launch per step (unsplit), or one sweep per axis (split: x, then y, then z;
     // each sweep writes the ghost images its successor reads; all read the same dt)
     const int sweeps = split ? U->ndim : 1;
-    // the split step of a 2D FP32 field sweeps on strip walks (no tile staging)
-    const bool walk = split && U->ndim == 2 && U->dtype == RIPPLE_F32 && U->variant < 0;
-    WalkLaunch W[2]{};
+    // the split step of an FP32 field sweeps on strip walks (no tile staging)
+    const bool walk = split && U->dtype == RIPPLE_F32 && U->variant < 0;
+    WalkLaunch W[3]{};
     if (walk) {
-        for (int a = 0; a < 2; ++a) {
-            const int wocc = force_walk_occ_f32_2d(layout, a);
+        for (int a = 0; a < U->ndim; ++a) {
+            const int wocc = U->ndim == 2 ? force_walk_occ_f32_2d(layout, a) : force_walk_occ_f32_3d(layout, a);
             if (wocc <= 0) return fail(RIPPLE_ERR_INTERNAL, "walk sweep kernel does not fit");
             W[a].wg = walk_geom(g, a, (long long)wocc * ctx->sm_count * kWalkWarps);
             W[a].grid = (int)std::min<long long>((W[a].wg.walks + kWalkWarps - 1) / kWalkWarps,
@@ -724,7 +729,8 @@ ripple_status ripple_fv_step(ripple_field U, const ripple_fv_params* p, int64_t 
                 W[a].prm.first = n == 0;
                 W[a].prm.axis = a;
                 W[a].prm.last = a == sweeps - 1;
-                RIPPLE_CUDA(force_walk_launch_f32_2d(layout, a, W[a]));
+                RIPPLE_CUDA(U->ndim == 2 ? force_walk_launch_f32_2d(layout, a, W[a])
+                                         : force_walk_launch_f32_3d(layout, a, W[a]));
                 U->cur = outb;
                 continue;
             }

@@ -86,8 +86,9 @@ int sweep_occ_f32_3d(int layout, int scheme, int v);
 int sweep_occ_f64_2d(int layout, int scheme, int v);
 int sweep_occ_f64_3d(int layout, int scheme, int v);
 
-// One sweep of the split FORCE step of a 2D FP32 field on strip walks
-// (euler_force_walk.cuh), along axis 0 or 1; defined with the 2D FP32 sweeps.
+// One sweep of the split FORCE step of an FP32 field on strip walks
+// (euler_force_walk.cuh), along axis 0, 1 (or 2 in 3D); defined with the FP32
+// sweeps of the same dimension.
 struct WalkLaunch {
     const void* in;
     void* out;
@@ -98,8 +99,10 @@ struct WalkLaunch {
     cudaStream_t stream;
 };
 cudaError_t force_walk_launch_f32_2d(int layout, int axis, const WalkLaunch& L);
+cudaError_t force_walk_launch_f32_3d(int layout, int axis, const WalkLaunch& L);
 // Resident CTAs per SM of the walk kernel (0 on error).
 int force_walk_occ_f32_2d(int layout, int axis);
+int force_walk_occ_f32_3d(int layout, int axis);
 
 // Aux kernels (f32/f64 x 2D/3D), defined in aux.cu.
 cudaError_t launch_prep(int dtype, int dim, void* buf, FieldCtl* ctl, const FieldGeom& g, int bc, double gamma,

@@ -81,6 +81,29 @@ def test_force_split_fp32_2d_long_walks(ctx, layout, bc):
     assert st["t"] == pytest.approx(info["t"], rel=1e-5)
 
 
+_LONG_WALK_REF_3D = {}
+
+
+@pytest.mark.parametrize("layout", [R.RIPPLE_SOA, R.RIPPLE_AOS])
+@pytest.mark.parametrize("bc", [R.RIPPLE_BC_PERIODIC, R.RIPPLE_BC_TRANSMISSIVE])
+def test_force_split_fp32_3d_walks(ctx, layout, bc):
+    """3D FP32 split sweeps on strip walks: x walks over every (y, z) row with a
+    ragged last chunk (150 = 64 + 64 + 22), y walks through the strips of every
+    z plane and z walks through those of every y row, cut into several
+    segments with a ragged last one; the whole field against the oracle, and
+    against the tiled pair kernel's split sweeps."""
+    dims = (150, 70, 61)
+    U0 = _random_state(dims, seed=13, amp=0.3).astype(np.float32).astype(np.float64)
+    if bc not in _LONG_WALK_REF_3D:
+        _LONG_WALK_REF_3D[bc] = oracle.euler_run(U0, 4, scheme=oracle.FORCE_SPLIT, bc=bc)
+    ref, info = _LONG_WALK_REF_3D[bc]
+    got, st = gpu_euler(ctx, U0, 4, dtype=R.RIPPLE_F32, layout=layout, scheme=FORCE, bc=bc)
+    assert_parity(got, ref, 2e-5, LINF_F32)
+    assert st["t"] == pytest.approx(info["t"], rel=1e-5)
+    tiled, _ = gpu_euler(ctx, U0, 4, dtype=R.RIPPLE_F32, layout=layout, scheme=FORCE, bc=bc, variant=2)
+    assert_parity(got, tiled.astype(np.float64), 1e-6, 1e-5)
+
+
 @pytest.mark.parametrize("ndim,dims", [(2, (40, 21)), (3, (18, 9, 12))])
 @pytest.mark.parametrize("dtype", [R.RIPPLE_F64, R.RIPPLE_F32])
 def test_force_split_uniform_state_bit_exact(ctx, ndim, dims, dtype):
