@@ -40,10 +40,10 @@ import inputs  # noqa: E402
 N3 = 256
 NSTEPS_SOLVE = 50
 BYTES_PER_CELL_UPDATE = 40  # FP32, 5 components: 20 B read + 20 B written per cell per step
-# DRAM bytes per cell update of the sweep kernel as measured by ncu
+# DRAM bytes per cell update of the sweep kernel (the row kernel, SoA) as measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum of one 256x256x128 launch, divided by its cells);
 # traffic scales with the cells of a launch.  Re-measure whenever the kernel changes.
-DRAM_BYTES_PER_CELL_UPDATE = (215535872 + 142807296) / (256 * 256 * 128)
+DRAM_BYTES_PER_CELL_UPDATE = (216015616 + 136395520) / (256 * 256 * 128)
 METRIC = "cell-updates/s"
 ACTIVE_CELLS = 4 << 20  # serving: per-step cell budget of stepped Euler problems
 
@@ -121,7 +121,7 @@ class ClockSampler:
 # capture of each solve (smsp__inst_executed.sum x 32 / the solve's Godunov
 # updates); the eikonal roofline is issue-bound, so these set its achieved
 # rate.  Re-measure whenever the kernels change.
-FIM_INSTR_PER_UPDATE = {"2d_2048": None, "3d_192": None}
+FIM_INSTR_PER_UPDATE = {"2d_2048": 38.44, "3d_192": 85.87}
 
 
 def eikonal_roofline(name, updates_per_s, clocks, sms):
@@ -232,6 +232,8 @@ def bench_gpu(args, rank, world, local):
 
     # ---- headline: SoA, inputs resident in HBM ----
     f = R.ripple_field_create(ctx, dims, 5, R.RIPPLE_SOA, 2, R.RIPPLE_F32)
+    if args.sweep_only and args.sweep_variant >= 0:
+        R.ripple_field_set_sweep(f, args.sweep_variant, 0)
     R.ripple_field_upload(f, U0_dev, R.RIPPLE_SOA)
     R.ripple_fv_step(f, prm, 1, stats=False)  # first call: second buffer, prep, tensor maps
     torch.cuda.synchronize()
@@ -899,6 +901,8 @@ def main():
     ap.add_argument("--sweep-only", action="store_true",
                     help="time only the SoA sweep (a small case for profiling; not the headline line)")
     ap.add_argument("--sweep-dims", type=int, nargs=3, default=[N3, N3, N3], metavar=("NX", "NY", "NZ"))
+    ap.add_argument("--sweep-variant", type=int, default=-1,
+                    help="sweep kernel of the sweep-only run (ripple_field_set_sweep; -1: the default)")
     ap.add_argument("--force-only", action="store_true",
                     help="time only the split FORCE step, FP32 SoA (profiling; not the headline line)")
     ap.add_argument("--force-n", type=int, default=8192)
