@@ -405,7 +405,17 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
     one batched launch per global step (autotuned layout and tile shape, CUDA
     graphs) against the per-instance launch loop on the same GPU."""
     probs = inputs.batch_problems(count, seed=1)
-    states = [inputs.euler2d_sine(side, amp=amp).astype(np.float32) for side, amp in probs]
+    pageable = [inputs.euler2d_sine(side, amp=amp).astype(np.float32) for side, amp in probs]
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+        t.numpy()[...] = a
+        return t.numpy()
+
+    # requests read and write page-locked host arrays (the end-to-end form);
+    # the pageable form is timed once beside it
+    states = [pinned(a) for a in pageable]
+    outs = [pinned(a) for a in pageable]
     sides = [side for side, _ in probs]
     cells = float(sum(side * side for side in sides))
     ctx = R.ripple_ctx_create(local)
@@ -414,8 +424,10 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
         R.ripple_batch_configure(ctx, layout=cfg["layout"], tile_variant=cfg["tile_variant"],
                                  steps_per_sync=nsteps, use_graphs=True, staging=cfg["staging"])
 
-        def run_batch():
-            reqs = [R.euler_request(U, nsteps, [1.0 / U.shape[2], 1.0 / U.shape[1]]) for U in states]
+        def run_batch(src=None, dst=None):
+            src = states if src is None else src
+            dst = outs if dst is None else dst
+            reqs = [R.euler_request(U, nsteps, [1.0 / U.shape[2], 1.0 / U.shape[1]], out=o) for U, o in zip(src, dst)]
             t0 = time.perf_counter()
             tickets = R.ripple_batch_submit(ctx, reqs)
             infos = [R.ripple_wait(ctx, t, 600000) for t in tickets]
@@ -428,10 +440,15 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
         with ClockSampler(local) as clk_b:
             reqs, infos, t_batch = run_batch()
         st1 = R.ripple_batch_get_stats(ctx)
+        host_ms = {k: 1e3 * (st1[k] - st0[k]) for k in ("host_admit_s", "host_round_s", "host_finish_s")}
+        kept = [np.array(r["output"]) for r in reqs]
+        outs_p = [np.empty_like(a) for a in pageable]
+        run_batch(pageable, outs_p)
+        _, _, t_pageable = run_batch(pageable, outs_p)
         if keep is not None:  # four instances (the smallest, two middle, the largest) for the oracle
             order = np.argsort(sides)
             pick = [int(order[0]), int(order[count // 3]), int(order[2 * count // 3]), int(order[-1])]
-            keep["batched"] = [dict(U0=states[i], gpu=reqs[i]["output"], side=sides[i]) for i in pick]
+            keep["batched"] = [dict(U0=pageable[i], gpu=kept[i], side=sides[i]) for i in pick]
         span = max(i["finish_s"] for i in infos) - min(i["start_s"] for i in infos)
         dev_s = st1["device_s"] - st0["device_s"]
         # dependency-driven rounds: the same batch in ONE persistent launch
@@ -443,7 +460,7 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
             reqs_a, infos_a, t_async = run_batch()
         sa1 = R.ripple_batch_get_stats(ctx)
         span_a = max(i["finish_s"] for i in infos_a) - min(i["start_s"] for i in infos_a)
-        same = all(np.array_equal(x["output"], y["output"]) for x, y in zip(reqs, reqs_a))
+        same = all(np.array_equal(x, y["output"]) for x, y in zip(kept, reqs_a))
         # uneven step counts (uniform in [nsteps/2, 3 nsteps/2], seeded): per-step
         # launches shrink each round to the shortest remaining problem
         steps_u = [int(nsteps // 2 + u * nsteps) for u in inputs.uniform(3, count, stream=6)]
@@ -454,7 +471,8 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
                                      steps_per_sync=max(steps_u), use_graphs=True, staging=cfg["staging"],
                                      async_queue=mode == "dependency_driven")
             for rep_ in range(2):  # warm-up, then timed
-                rq = [R.euler_request(U, k, [1.0 / U.shape[2], 1.0 / U.shape[1]]) for U, k in zip(states, steps_u)]
+                rq = [R.euler_request(U, k, [1.0 / U.shape[2], 1.0 / U.shape[1]], out=o)
+                      for U, k, o in zip(states, steps_u, outs)]
                 s0 = R.ripple_batch_get_stats(ctx)
                 t0 = time.perf_counter()
                 inf = [R.ripple_wait(ctx, t, 600000) for t in R.ripple_batch_submit(ctx, rq)]
@@ -465,7 +483,7 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
             uneven[mode] = {"value": cells_u / dt_u, "value_compute_span": cells_u / sp,
                             "value_device": cells_u / (s1["device_s"] - s0["device_s"]),
                             "launches": s1["launches"] - s0["launches"],
-                            "outputs": [r["output"] for r in rq]}
+                            "outputs": [np.array(r["output"]) for r in rq]}
         uneven_same = all(np.array_equal(x, y) for x, y in zip(uneven["per_step_launches"].pop("outputs"),
                                                                uneven["dependency_driven"].pop("outputs")))
         # per-instance launch loop over device-resident fields (no transfers timed)
@@ -487,9 +505,9 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
             R.ripple_ctx_sync(ctx)
             t_loop = time.perf_counter() - t0
         worst = 0.0
-        for f, req in zip(fields, reqs):
+        for f, out_b in zip(fields, kept):
             loop_out = R.ripple_field_download(f)
-            a = np.abs(req["output"].astype(np.float64) - loop_out).reshape(4, -1).sum(1)
+            a = np.abs(out_b.astype(np.float64) - loop_out).reshape(4, -1).sum(1)
             b = np.abs(loop_out.astype(np.float64)).reshape(4, -1).sum(1)
             worst = max(worst, float((a / b).max()))
             R.ripple_field_destroy(f)
@@ -500,6 +518,9 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
         "instances": count, "total_cells": int(cells), "steps": nsteps,
         "value": cells * nsteps / t_batch, "unit": METRIC,
         "batched_seconds_end_to_end": t_batch,
+        "host_arrays": "page-locked (pinned) inputs and outputs",
+        "value_pageable_host_arrays": cells * nsteps / t_pageable,
+        "scheduler_host_ms": host_ms,
         "clocks": clk_b.summary(), "clocks_dependency_driven": clk_a.summary(), "clocks_loop": clk_l.summary(),
         "batched_compute_span_s": span,
         "batched_value_compute_span": cells * nsteps / span,

@@ -313,6 +313,12 @@ typedef struct {
     int64_t fim_iterations;   /* eikonal iterations issued */
     double device_s;          /* GPU time of the compute rounds (CUDA events around each round's
                                  launches on the compute stream) */
+    double host_admit_s;      /* scheduler-thread time in admissions: allocation, input copies
+                                 (synchronous for pageable host arrays), group launches */
+    double host_round_s;      /* scheduler-thread time preparing and queueing compute rounds
+                                 (tables, launches), without the wait for the GPU */
+    double host_finish_s;     /* scheduler-thread time queueing downloads (output copies are
+                                 synchronous for pageable host arrays) and completing tickets */
 } ripple_batch_stats;
 
 /* Set the batch configuration (defaults: SoA, 32x8, 16 steps per sync, graphs

@@ -103,7 +103,8 @@ class ripple_batch_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("global_steps", ctypes.c_int64), ("launches", ctypes.c_int64),
                 ("graph_replays", ctypes.c_int64), ("now_s", ctypes.c_double), ("fim_iterations", ctypes.c_int64),
-                ("device_s", ctypes.c_double)]
+                ("device_s", ctypes.c_double), ("host_admit_s", ctypes.c_double),
+                ("host_round_s", ctypes.c_double), ("host_finish_s", ctypes.c_double)]
 
 # name -> (argtypes) ; every ABI function returns ripple_status (int)
 _SIGNATURES = {
@@ -436,31 +437,80 @@ def eikonal_request(s, sources, h, tol=1e-6, max_iters=0, out=None):
                 max_iters=max_iters)
 
 
+def _struct_dtype(cls):
+    """numpy dtype with the field offsets of a ctypes Structure (pointers as uint64)."""
+    names, formats, offsets = [], [], []
+    for name, ct in cls._fields_:
+        f = getattr(cls, name)
+        if isinstance(ct, type) and issubclass(ct, ctypes.Structure):
+            fmt = _struct_dtype(ct)
+        elif isinstance(ct, type) and issubclass(ct, ctypes.Array):
+            fmt = (np.dtype(ct._type_), ct._length_)
+        elif ct in (ctypes.c_void_p,) or (isinstance(ct, type) and issubclass(ct, ctypes._Pointer)):
+            fmt = np.uint64
+        else:
+            fmt = np.dtype(ct)
+        names.append(name)
+        formats.append(fmt)
+        offsets.append(f.offset)
+    return np.dtype({"names": names, "formats": formats, "offsets": offsets, "itemsize": ctypes.sizeof(cls)})
+
+
+_REQ_DTYPE = None
+
+
 def ripple_batch_submit(ctx, requests):
     """Queue request dicts (see euler_request / eikonal_request); returns tickets."""
+    global _REQ_DTYPE
+    if _REQ_DTYPE is None:
+        _REQ_DTYPE = _struct_dtype(ripple_request)
     n = len(requests)
     arr = (ripple_request * n)()
     keep = []
+    kind, dims, ptr, fv, fvi, nsteps = [], [], [], [], [], []
     for i, r in enumerate(requests):
         inp, outp = r["input"], r["output"]
-        ny, nx = inp.shape[-2], inp.shape[-1]
-        arr[i].kind = r["kind"]
-        arr[i].dims[0] = nx
-        arr[i].dims[1] = ny
-        arr[i].input = inp.ctypes.data
-        arr[i].output = outp.ctypes.data
+        k = r["kind"]
+        kind.append(k)
+        shp = inp.shape
+        dims.append((shp[-1], shp[-2]))
+        ptr.append((inp.__array_interface__["data"][0], outp.__array_interface__["data"][0]))
         src = None
-        if r["kind"] == RIPPLE_REQ_EULER:
-            arr[i].fv = make_fv_params(r["dx"], gamma=r.get("gamma", 1.4), cfl=r.get("cfl", 0.4),
-                                       scheme=RIPPLE_RUSANOV1, bc=r.get("bc", RIPPLE_BC_PERIODIC))
-            arr[i].nsteps = r["nsteps"]
+        if k == RIPPLE_REQ_EULER:
+            dx = r["dx"]
+            fv.append((r.get("gamma", 1.4), r.get("cfl", 0.4), dx[0], dx[1] if len(dx) > 1 else 1.0,
+                       dx[2] if len(dx) > 2 else 1.0))
+            fvi.append((RIPPLE_RUSANOV1, r.get("bc", RIPPLE_BC_PERIODIC)))
+            nsteps.append(r["nsteps"])
         else:
+            fv.append((0.0, 0.0, 0.0, 0.0, 0.0))
+            fvi.append((0, 0))
+            nsteps.append(0)
             flat = [int(c) for xy in r["sources"] for c in xy]
             src = (ctypes.c_int64 * len(flat))(*flat)
             arr[i].sources = src
             arr[i].nsrc = len(r["sources"])
             arr[i].eik = ripple_eik_params(float(r["h"]), float(r.get("tol", 1e-6)), int(r.get("max_iters", 0)))
         keep.append((inp, outp, src))
+    if n:
+        a = np.frombuffer(arr, dtype=_REQ_DTYPE)
+        kind = np.asarray(kind, np.int32)
+        fv = np.asarray(fv, np.float64)
+        fvi = np.asarray(fvi, np.int32)
+        eu = kind == RIPPLE_REQ_EULER
+        ptr = np.asarray(ptr, np.uint64)
+        a["kind"] = kind
+        a["dims"] = np.asarray(dims, np.int64)
+        a["input"] = ptr[:, 0]
+        a["output"] = ptr[:, 1]
+        f = a["fv"]
+        f["gamma"] = np.where(eu, fv[:, 0], f["gamma"])
+        f["cfl"] = np.where(eu, fv[:, 1], f["cfl"])
+        f["dx"] = np.where(eu[:, None], fv[:, 2:5], f["dx"])
+        f["scheme"] = np.where(eu, fvi[:, 0], f["scheme"])
+        f["bc"] = np.where(eu, fvi[:, 1], f["bc"])
+        a["fv"] = f
+        a["nsteps"] = np.where(eu, np.asarray(nsteps, np.int64), a["nsteps"])
     tickets = (ctypes.c_uint64 * n)()
     _check(load().ripple_batch_submit(ctx, arr, n, tickets), "ripple_batch_submit")
     out = [int(t) for t in tickets]

@@ -73,4 +73,21 @@ cudaError_t launch_interior_copy(int dtype, void* buf, const FieldGeom& g, void*
     return cudaGetLastError();
 }
 
+cudaError_t launch_group(int dtype, int op, const GroupItem* items, int n, long long blocks, cudaStream_t s)
+{
+    if (n <= 0 || blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const unsigned grid = (unsigned)blocks;
+    if (dtype == RIPPLE_F32) {
+        if (op == GROUP_ADMIT_FILL) group_admit_fill_kernel<float><<<grid, 256, 0, s>>>(items, n);
+        else if (op == GROUP_ADMIT_PREP) group_admit_prep_kernel<float><<<grid, 256, 0, s>>>(items, n);
+        else group_pack_kernel<float><<<grid, 256, 0, s>>>(items, n);
+    } else {
+        if (op == GROUP_ADMIT_FILL) group_admit_fill_kernel<double><<<grid, 256, 0, s>>>(items, n);
+        else if (op == GROUP_ADMIT_PREP) group_admit_prep_kernel<double><<<grid, 256, 0, s>>>(items, n);
+        else group_pack_kernel<double><<<grid, 256, 0, s>>>(items, n);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace ripple

@@ -172,9 +172,16 @@ struct Inst {
     int map_key = -1;
     CUtensorMap solo_map[2][2];  // Euler: staging (kind 0) and store (kind 1) maps of buf[0], buf[1] for the
     int solo_v = -1;             // field sweep kernel of variant solo_v (solo rounds)
-    cudaEvent_t ev = nullptr;
+    struct GroupEv* gev = nullptr;  // completion of the instance's admission or download group
     ripple_status result = RIPPLE_OK;
     double t_submit = 0, t_admit = 0, t_start = 0, t_finish = 0;
+};
+
+// An event shared by the instances of one admission or download group,
+// returned to the runtime's pool when the last of them has seen it.
+struct GroupEv {
+    cudaEvent_t ev = nullptr;
+    int refs = 0;
 };
 
 struct Ticket {
@@ -202,6 +209,12 @@ struct BatchRuntime {
     cudaMemPool_t pool = nullptr;
     cudaEvent_t ev_step = nullptr;
     cudaEvent_t ev_r0 = nullptr, ev_r1 = nullptr;  // timing of a compute round (device_s)
+    std::vector<cudaEvent_t> ev_pool;  // events of finished groups, for reuse
+    // descriptors of the current admission or download group: pinned host
+    // array, its device copy (both kSlots long) and the event after the copy
+    GroupItem* h_items = nullptr;
+    GroupItem* d_items = nullptr;
+    cudaEvent_t ev_items = nullptr;
     bool started = false;
     // slot arrays: device, and pinned mirrors of status/counters/ctl
     FieldCtl* slot_ctl = nullptr;
@@ -209,6 +222,10 @@ struct BatchRuntime {
     long long* slot_counters = nullptr;
     FieldCtl* h_ctl = nullptr;
     unsigned long long* h_status = nullptr;
+    // written only by the downloads (copy stream): the slot entries of
+    // finished instances, read when their group's event has completed
+    FieldCtl* out_ctl = nullptr;
+    unsigned long long* out_status = nullptr;
     long long* h_counters = nullptr;
     std::vector<int> free_slots;
     // tables
@@ -269,11 +286,11 @@ static void rt_free(BatchRuntime* rt, void* p, size_t bytes)
 
 static ripple_status rt_start(BatchRuntime* rt);
 
-static void finish(BatchRuntime* rt, Inst* in, ripple_status st)
+// Complete an instance's ticket (rt->mu held).
+static void fill_ticket(BatchRuntime* rt, Inst* in, ripple_status st, double t)
 {
     in->result = st;
-    in->t_finish = rt->now();
-    std::lock_guard<std::mutex> lk(rt->mu);
+    in->t_finish = t;
     Ticket& tk = rt->tickets[in->ticket];
     tk.done = true;
     tk.info.status = st;
@@ -284,7 +301,7 @@ static void finish(BatchRuntime* rt, Inst* in, ripple_status st)
     if (in->slot >= 0) {
         if (in->req.kind == RIPPLE_REQ_EULER) {
             tk.info.work = in->req.nsteps;
-            tk.info.t = rt->h_ctl[in->slot].t;
+            tk.info.t = rt->out_ctl[in->slot].t;
         } else {
             tk.info.work = rt->h_counters[in->slot * 3 + 0];
             tk.info.tile_visits = rt->h_counters[in->slot * 3 + 1];
@@ -293,8 +310,51 @@ static void finish(BatchRuntime* rt, Inst* in, ripple_status st)
     }
     if (st == RIPPLE_OK) rt->stats.completed++;
     else rt->stats.failed++;
+}
+
+static void add_host_time(BatchRuntime* rt, double ripple_batch_stats::*field, double t0)
+{
+    const double dt = rt->now() - t0;
+    std::lock_guard<std::mutex> lk(rt->mu);
+    rt->stats.*field += dt;
+}
+
+static void finish(BatchRuntime* rt, Inst* in, ripple_status st)
+{
+    {
+        std::lock_guard<std::mutex> lk(rt->mu);
+        fill_ticket(rt, in, st, rt->now());
+    }
     rt->cv_done.notify_all();
 }
+
+// A pooled event for a group of n instances.
+static ripple_status group_event(BatchRuntime* rt, int n, GroupEv** out)
+{
+    *out = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (!rt->ev_pool.empty()) {
+        ev = rt->ev_pool.back();
+        rt->ev_pool.pop_back();
+    } else {
+        RIPPLE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    *out = new GroupEv{ev, n};
+    return RIPPLE_OK;
+}
+
+// The instance no longer waits on its group's event.
+static void drop_event(BatchRuntime* rt, Inst* in)
+{
+    GroupEv* g = in->gev;
+    in->gev = nullptr;
+    if (g && --g->refs == 0) {
+        rt->ev_pool.push_back(g->ev);
+        delete g;
+    }
+}
+
+static bool group_done(const Inst* in) { return !in->gev || cudaEventQuery(in->gev->ev) == cudaSuccess; }
 
 // Free everything an instance holds (stream-ordered after its last use).
 static void release(BatchRuntime* rt, Inst* in)
@@ -305,8 +365,7 @@ static void release(BatchRuntime* rt, Inst* in)
     rt_free(rt, in->scratch, in->scratch_bytes);
     in->buf[0] = in->buf[1] = in->sbuf = in->scratch = nullptr;
     if (in->slot >= 0) rt->free_slots.push_back(in->slot);
-    if (in->ev) cudaEventDestroy(in->ev);
-    in->ev = nullptr;
+    drop_event(rt, in);
 }
 
 template <typename T>
@@ -388,60 +447,140 @@ static ripple_status admit(BatchRuntime* rt, Inst* in)
     rt->free_slots.pop_back();
     if (fault_injected("upload")) return fail(RIPPLE_ERR_CUDA, "input upload failed (injected: RIPPLE_FAULT=upload)");
     cudaStream_t s = rt->copy;
-    const long long total = dims[0] * dims[1];
-    const int grid = (int)std::min<long long>((total + 255) / 256, 4LL * rt->ctx->sm_count);
-    RIPPLE_CUDA(cudaEventCreateWithFlags(&in->ev, cudaEventDisableTiming));
     // the second buffer is the dense staging area of the upload
     RIPPLE_CUDA(cudaMemcpyAsync(in->buf[1], r.input, dense, cudaMemcpyHostToDevice, s));
-    RIPPLE_CUDA(cudaMemsetAsync(&rt->slot_ctl[in->slot], 0, sizeof(FieldCtl), s));
-    RIPPLE_CUDA(cudaMemsetAsync(&rt->slot_status[in->slot], 0, sizeof(unsigned long long), s));
-    RIPPLE_CUDA(cudaMemsetAsync(&rt->slot_counters[in->slot * 3], 0, 3 * sizeof(long long), s));
     if (r.kind == RIPPLE_REQ_EULER) {
-        // padding beyond the ghost layers reads NaN in both buffers (the field
-        // sweep kernel of solo rounds relies on it; the batched step ignores it)
-        const int pgrid = (int)std::min<long long>((in->g.px * in->g.py + 255) / 256, 4LL * rt->ctx->sm_count);
-        RIPPLE_CUDA(launch_pad_nan(dt, in->buf[0], in->g, pgrid, s));
-        RIPPLE_CUDA(launch_interior_copy(dt, in->buf[0], in->g, in->buf[1], LAYOUT_SOA, 0, grid, s));
-        RIPPLE_CUDA(launch_pad_nan(dt, in->buf[1], in->g, pgrid, s));
-        const double inv_dx[3] = {1.0 / r.fv.dx[0], 1.0 / r.fv.dx[1], 0.0};
-        RIPPLE_CUDA(launch_prep(dt, 2, in->buf[0], &rt->slot_ctl[in->slot], in->g, (int)r.fv.bc, r.fv.gamma, inv_dx,
-                                0, grid, s));
+        // TMA maps of the batched step, encoded while the copies run (the tile
+        // shape and layout cannot change while a request is in flight)
+        BatchEuler e{};
+        e.buf[0] = in->buf[0];
+        e.buf[1] = in->buf[1];
+        e.g = in->g;
+        ripple_status st = encode_batch_maps(e, rt->cfg.layout, dt, rt->cfg.tile_variant);
+        if (st != RIPPLE_OK) return st;
+        std::memcpy(in->map, e.map, sizeof(in->map));
+        in->map_key = rt->cfg.tile_variant * 2 + (rt->cfg.layout == RIPPLE_SOA ? 1 : 0);
     } else {
+        const long long total = dims[0] * dims[1];
+        const int grid = (int)std::min<long long>((total + 255) / 256, 4LL * rt->ctx->sm_count);
         RIPPLE_CUDA(launch_interior_copy(dt, in->sbuf, in->gs, in->buf[1], LAYOUT_SOA, 0, grid, s));
         RIPPLE_CUDA(cudaMemsetAsync(in->scratch, 0, in->scratch_bytes, s));
         if (dt == RIPPLE_F32) RIPPLE_CUDA(launch_fim_init<float>(fim_problem<float>(in), EikTile<2>::TS, grid, s));
         else RIPPLE_CUDA(launch_fim_init<double>(fim_problem<double>(in), EikTile<2>::TS, grid, s));
     }
-    RIPPLE_CUDA(cudaEventRecord(in->ev, s));
-    in->t_admit = rt->now();
     return RIPPLE_OK;
 }
 
-// Queue the download of a finished instance (after the compute work recorded in ev_step).
-static ripple_status start_download(BatchRuntime* rt, Inst* in)
+// Make the descriptors of a group in the pinned array (after the previous
+// group's copy of it has completed) and copy them to the device.
+static ripple_status put_items(BatchRuntime* rt, int n, cudaStream_t s)
 {
-    const ripple_request& r = in->req;
+    RIPPLE_CUDA(cudaMemcpyAsync(rt->d_items, rt->h_items, (size_t)n * sizeof(GroupItem), cudaMemcpyHostToDevice, s));
+    RIPPLE_CUDA(cudaEventRecord(rt->ev_items, s));
+    return RIPPLE_OK;
+}
+
+// Device-side preparation of every instance admitted in one scheduler pass,
+// after their input copies: two launches over the whole group (Euler: buffer 0
+// filled from the dense input with NaN padding, the slot cleared; then the
+// boundary images, the first wave-speed maximum, the input check and buffer
+// 1's NaN padding; eikonal: the slot cleared), then one event for the group.
+static ripple_status admit_group(BatchRuntime* rt, const std::vector<Inst*>& group)
+{
+    const int n = (int)group.size();
+    if (n == 0) return RIPPLE_OK;
+    cudaStream_t s = rt->copy;
+    RIPPLE_CUDA(cudaEventSynchronize(rt->ev_items));
+    long long b0 = 0, b1 = 0;
+    for (int i = 0; i < n; ++i) {
+        const Inst* in = group[i];
+        GroupItem& d = rt->h_items[i];
+        d = GroupItem{};
+        d.buf = in->buf[0];
+        d.other = in->buf[1];
+        d.ctl = &rt->slot_ctl[in->slot];
+        d.status = &rt->slot_status[in->slot];
+        d.counters = &rt->slot_counters[in->slot * 3];
+        d.g = in->g;
+        d.euler = in->req.kind == RIPPLE_REQ_EULER ? 1 : 0;
+        d.gamma = in->req.fv.gamma;
+        d.inv_dx0 = d.euler ? 1.0 / in->req.fv.dx[0] : 0.0;
+        d.inv_dx1 = d.euler ? 1.0 / in->req.fv.dx[1] : 0.0;
+        d.bc = (int)in->req.fv.bc;
+        d.blk[0] = b0;
+        d.blk[1] = b1;
+        const long long nb =
+            d.euler ? (in->g.px * in->g.py * in->g.pz + kGroupCellsPerBlock - 1) / kGroupCellsPerBlock : 1;
+        b0 += nb;
+        if (d.euler) b1 += nb;
+    }
+    ripple_status st = put_items(rt, n, s);
+    if (st != RIPPLE_OK) return st;
+    RIPPLE_CUDA(launch_group(rt->cfg.dtype, GROUP_ADMIT_FILL, rt->d_items, n, b0, s));
+    RIPPLE_CUDA(launch_group(rt->cfg.dtype, GROUP_ADMIT_PREP, rt->d_items, n, b1, s));
+    GroupEv* ge = nullptr;
+    st = group_event(rt, n, &ge);
+    if (st != RIPPLE_OK) return st;
+    const double t = rt->now();
+    for (Inst* in : group) {
+        in->gev = ge;
+        in->t_admit = t;
+    }
+    RIPPLE_CUDA(cudaEventRecord(ge->ev, s));
+    return RIPPLE_OK;
+}
+
+// Queue the downloads of a group of finished instances (after the compute
+// work recorded in ev_step): one launch gathers every result into its dense
+// stage, then one copy per result into the caller's array and one copy per
+// slot array of the group's slot range into the pinned mirrors.
+static ripple_status start_downloads(BatchRuntime* rt, const std::vector<Inst*>& group)
+{
+    const int n = (int)group.size();
+    if (n == 0) return RIPPLE_OK;
     const ripple_dtype dt = rt->cfg.dtype;
     cudaStream_t s = rt->copy;
     RIPPLE_CUDA(cudaStreamWaitEvent(s, rt->ev_step, 0));
-    const long long total = r.dims[0] * r.dims[1];
-    const int grid = (int)std::min<long long>((total + 255) / 256, 4LL * rt->ctx->sm_count);
-    const size_t dense = (size_t)total * elem_size(dt) * (r.kind == RIPPLE_REQ_EULER ? 4 : 1);
-    void* fin = in->buf[0];
-    void* stage = in->buf[1];
-    if (r.kind == RIPPLE_REQ_EULER && (r.nsteps & 1)) {
-        fin = in->buf[1];
-        stage = in->buf[0];
+    RIPPLE_CUDA(cudaEventSynchronize(rt->ev_items));
+    long long b0 = 0;
+    int lo = kSlots, hi = -1;
+    for (int i = 0; i < n; ++i) {
+        const Inst* in = group[i];
+        const bool odd = in->req.kind == RIPPLE_REQ_EULER && (in->req.nsteps & 1);
+        GroupItem& d = rt->h_items[i];
+        d = GroupItem{};
+        d.buf = in->buf[odd ? 1 : 0];
+        d.other = in->buf[odd ? 0 : 1];
+        d.g = in->g;
+        d.euler = in->req.kind == RIPPLE_REQ_EULER ? 1 : 0;
+        d.blk[0] = b0;
+        b0 += (in->req.dims[0] * in->req.dims[1] + kGroupCellsPerBlock - 1) / kGroupCellsPerBlock;
+        lo = std::min(lo, in->slot);
+        hi = std::max(hi, in->slot);
     }
-    RIPPLE_CUDA(launch_interior_copy(dt, fin, in->g, stage, LAYOUT_SOA, 1, grid, s));
-    RIPPLE_CUDA(cudaMemcpyAsync(r.output, stage, dense, cudaMemcpyDeviceToHost, s));
-    RIPPLE_CUDA(cudaMemcpyAsync(&rt->h_ctl[in->slot], &rt->slot_ctl[in->slot], sizeof(FieldCtl),
+    ripple_status st = put_items(rt, n, s);
+    if (st != RIPPLE_OK) return st;
+    RIPPLE_CUDA(launch_group(dt, GROUP_PACK, rt->d_items, n, b0, s));
+    for (int i = 0; i < n; ++i) {
+        const Inst* in = group[i];
+        const ripple_request& r = in->req;
+        const size_t dense = (size_t)(r.dims[0] * r.dims[1]) * elem_size(dt) * (r.kind == RIPPLE_REQ_EULER ? 4 : 1);
+        RIPPLE_CUDA(cudaMemcpyAsync(r.output, rt->h_items[i].other, dense, cudaMemcpyDeviceToHost, s));
+    }
+    const int ns = hi - lo + 1;
+    RIPPLE_CUDA(cudaMemcpyAsync(&rt->out_ctl[lo], &rt->slot_ctl[lo], ns * sizeof(FieldCtl), cudaMemcpyDeviceToHost, s));
+    RIPPLE_CUDA(cudaMemcpyAsync(&rt->out_status[lo], &rt->slot_status[lo], ns * sizeof(unsigned long long),
                                 cudaMemcpyDeviceToHost, s));
-    RIPPLE_CUDA(cudaMemcpyAsync(&rt->h_status[in->slot], &rt->slot_status[in->slot], sizeof(unsigned long long),
+    RIPPLE_CUDA(cudaMemcpyAsync(&rt->h_counters[lo * 3], &rt->slot_counters[lo * 3], ns * 3 * sizeof(long long),
                                 cudaMemcpyDeviceToHost, s));
-    RIPPLE_CUDA(cudaMemcpyAsync(&rt->h_counters[in->slot * 3], &rt->slot_counters[in->slot * 3], 3 * sizeof(long long),
-                                cudaMemcpyDeviceToHost, s));
-    RIPPLE_CUDA(cudaEventRecord(in->ev, s));
+    GroupEv* ge = nullptr;
+    st = group_event(rt, n, &ge);
+    if (st != RIPPLE_OK) return st;
+    for (Inst* in : group) {
+        drop_event(rt, in);
+        in->gev = ge;
+    }
+    RIPPLE_CUDA(cudaEventRecord(ge->ev, s));
     return RIPPLE_OK;
 }
 
@@ -708,26 +847,28 @@ static ripple_status launch_round_async(BatchRuntime* rt, int K, std::vector<lon
 // set) from the resident set to their downloads.
 static void collect_finished(BatchRuntime* rt)
 {
-    std::vector<Inst*> keep;
+    std::vector<Inst*> keep, done;
     for (Inst* in : rt->resident) {
         bool fin = false;
         if (in->req.kind == RIPPLE_REQ_EULER) fin = in->steps_done >= in->req.nsteps;
         else fin = rt->h_status[in->slot] != 0ull;
-        if (!fin) {
-            keep.push_back(in);
-            continue;
-        }
-        const ripple_status st = start_download(rt, in);
-        if (st != RIPPLE_OK) {
-            release(rt, in);
-            finish(rt, in, st);
-            delete in;
-            continue;
-        }
-        rt->downloading.push_back(in);
-        rt->dirty = true;
+        (fin ? done : keep).push_back(in);
     }
     rt->resident.swap(keep);
+    if (done.empty()) return;
+    const double t0 = rt->now();
+    rt->dirty = true;
+    const ripple_status st = start_downloads(rt, done);
+    for (Inst* in : done) {
+        if (st == RIPPLE_OK) {
+            rt->downloading.push_back(in);
+            continue;
+        }
+        release(rt, in);
+        finish(rt, in, st);
+        delete in;
+    }
+    add_host_time(rt, &ripple_batch_stats::host_finish_s, t0);
 }
 
 // Solo rounds: a problem that has the GPU to itself runs on the single-problem
@@ -856,6 +997,7 @@ static ripple_status solo_round(BatchRuntime* rt, bool& handled)
 // or one dependency-driven round (up to K steps of every Euler problem).
 static ripple_status compute_round(BatchRuntime* rt)
 {
+    const double t_enter = rt->now();
     // Active set: resident Euler problems in order of least remaining work
     // (cells x steps) while their cells fit the per-step budget (at least
     // one); eikonal problems always iterate.  A problem that (re)joins the
@@ -909,6 +1051,7 @@ static ripple_status compute_round(BatchRuntime* rt)
     RIPPLE_CUDA(cudaMemcpyAsync(rt->h_berr, &rt->d_bctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                 rt->compute));
     RIPPLE_CUDA(cudaEventRecord(rt->ev_step, rt->compute));
+    const double host_q = rt->now() - t_enter;
     RIPPLE_CUDA(cudaEventSynchronize(rt->ev_step));
     float round_ms = 0.f;
     RIPPLE_CUDA(cudaEventElapsedTime(&round_ms, rt->ev_r0, rt->ev_r1));
@@ -929,6 +1072,7 @@ static ripple_status compute_round(BatchRuntime* rt)
         rt->stats.global_steps = rt->gstep_e;
         rt->stats.fim_iterations = rt->gstep_f;
         rt->stats.device_s += 1e-3 * round_ms;
+        rt->stats.host_round_s += host_q;
     }
     collect_finished(rt);
     return RIPPLE_OK;
@@ -937,6 +1081,8 @@ static ripple_status compute_round(BatchRuntime* rt)
 static void scheduler(BatchRuntime* rt)
 {
     cudaSetDevice(rt->ctx->device);
+    std::vector<Inst*> group;  // admitted in this pass
+    double t_adm = 0.0;
     for (;;) {
         {
             std::unique_lock<std::mutex> lk(rt->mu);
@@ -944,6 +1090,7 @@ static void scheduler(BatchRuntime* rt)
             if (!busy)
                 rt->cv_work.wait(lk, [&] { return rt->stop || !rt->pending.empty(); });
             if (rt->stop && rt->resident.empty() && rt->uploading.empty() && rt->downloading.empty()) break;
+            t_adm = rt->now();
             // admission: FIFO while memory fits
             while (!rt->pending.empty()) {
                 Inst* in = rt->pending.front();
@@ -976,12 +1123,27 @@ static void scheduler(BatchRuntime* rt)
                 }
                 rt->stats.admitted++;
                 rt->uploading.push_back(in);  // counts as running for the admissions that follow
+                group.push_back(in);
             }
+        }
+        if (!group.empty()) {
+            const ripple_status st = admit_group(rt, group);
+            if (st != RIPPLE_OK) {
+                for (Inst* in : group) {
+                    rt->uploading.erase(std::find(rt->uploading.begin(), rt->uploading.end(), in));
+                    release(rt, in);
+                    finish(rt, in, st);
+                    delete in;
+                }
+            }
+            group.clear();
+            add_host_time(rt, &ripple_batch_stats::host_admit_s, t_adm);
         }
         // uploads that completed join the resident set at the next global step
         for (size_t i = 0; i < rt->uploading.size();) {
             Inst* in = rt->uploading[i];
-            if (cudaEventQuery(in->ev) == cudaSuccess) {
+            if (group_done(in)) {
+                drop_event(rt, in);
                 in->start_step = in->req.kind == RIPPLE_REQ_EULER ? rt->gstep_e : rt->gstep_f;
                 in->steps_done = 0;
                 in->active = false;  // the next round's active-set pass decides
@@ -1021,24 +1183,42 @@ static void scheduler(BatchRuntime* rt)
                 rt->dirty = true;
             }
         }
-        // completions
-        for (size_t i = 0; i < rt->downloading.size();) {
-            Inst* in = rt->downloading[i];
-            if (cudaEventQuery(in->ev) == cudaSuccess) {
-                ripple_status st = RIPPLE_OK;
-                if (in->req.kind == RIPPLE_REQ_EULER) {
-                    const unsigned err = rt->h_ctl[in->slot].err;
-                    if (err & DEV_ERR_NUMERIC) st = RIPPLE_ERR_NUMERIC;
-                    else if (err) st = RIPPLE_ERR_INTERNAL;
-                } else if ((rt->h_status[in->slot] & 3ull) == 2ull) {
-                    st = RIPPLE_ERR_TIMEOUT;
+        // completions: every ticket of the finished downloads first, then
+        // their memory and slots
+        {
+            std::vector<Inst*> done;
+            for (size_t i = 0; i < rt->downloading.size();) {
+                Inst* in = rt->downloading[i];
+                if (group_done(in)) {
+                    done.push_back(in);
+                    rt->downloading.erase(rt->downloading.begin() + i);
+                } else {
+                    ++i;
                 }
-                finish(rt, in, st);
-                release(rt, in);
-                delete in;
-                rt->downloading.erase(rt->downloading.begin() + i);
-            } else {
-                ++i;
+            }
+            if (!done.empty()) {
+                const double t0 = rt->now();
+                {
+                    std::lock_guard<std::mutex> lk(rt->mu);
+                    const double t = rt->now();
+                    for (Inst* in : done) {
+                        ripple_status st = RIPPLE_OK;
+                        if (in->req.kind == RIPPLE_REQ_EULER) {
+                            const unsigned err = rt->out_ctl[in->slot].err;
+                            if (err & DEV_ERR_NUMERIC) st = RIPPLE_ERR_NUMERIC;
+                            else if (err) st = RIPPLE_ERR_INTERNAL;
+                        } else if ((rt->out_status[in->slot] & 3ull) == 2ull) {
+                            st = RIPPLE_ERR_TIMEOUT;
+                        }
+                        fill_ticket(rt, in, st, t);
+                    }
+                }
+                rt->cv_done.notify_all();
+                for (Inst* in : done) {
+                    release(rt, in);
+                    delete in;
+                }
+                add_host_time(rt, &ripple_batch_stats::host_finish_s, t0);
             }
         }
         if (rt->resident.empty() && (!rt->uploading.empty() || !rt->downloading.empty()))
@@ -1063,6 +1243,9 @@ static ripple_status rt_start(BatchRuntime* rt)
         RIPPLE_CUDA(cudaMemPoolSetAttribute(rt->pool, cudaMemPoolAttrReleaseThreshold, &keep));
     }
     RIPPLE_CUDA(cudaEventCreateWithFlags(&rt->ev_step, cudaEventDisableTiming));
+    RIPPLE_CUDA(cudaEventCreateWithFlags(&rt->ev_items, cudaEventDisableTiming));
+    RIPPLE_CUDA(cudaMallocHost(&rt->h_items, kSlots * sizeof(GroupItem)));
+    RIPPLE_CUDA(cudaMalloc(&rt->d_items, kSlots * sizeof(GroupItem)));
     RIPPLE_CUDA(cudaEventCreate(&rt->ev_r0));
     RIPPLE_CUDA(cudaEventCreate(&rt->ev_r1));
     RIPPLE_CUDA(cudaMalloc(&rt->slot_ctl, kSlots * sizeof(FieldCtl)));
@@ -1072,6 +1255,8 @@ static ripple_status rt_start(BatchRuntime* rt)
     RIPPLE_CUDA(cudaMallocHost(&rt->h_ctl, kSlots * sizeof(FieldCtl)));
     RIPPLE_CUDA(cudaMallocHost(&rt->h_status, kSlots * sizeof(unsigned long long)));
     RIPPLE_CUDA(cudaMallocHost(&rt->h_counters, kSlots * 3 * sizeof(long long)));
+    RIPPLE_CUDA(cudaMallocHost(&rt->out_ctl, kSlots * sizeof(FieldCtl)));
+    RIPPLE_CUDA(cudaMallocHost(&rt->out_status, kSlots * sizeof(unsigned long long)));
     RIPPLE_CUDA(cudaMalloc(&rt->d_bctl, sizeof(BatchCtl)));
     RIPPLE_CUDA(cudaMemset(rt->d_bctl, 0, sizeof(BatchCtl)));
     RIPPLE_CUDA(cudaMallocHost(&rt->h_berr, sizeof(unsigned)));
@@ -1249,6 +1434,8 @@ void batch_runtime_destroy(ripple_ctx ctx)
         cudaFreeHost(rt->h_ctl);
         cudaFreeHost(rt->h_status);
         cudaFreeHost(rt->h_counters);
+        cudaFreeHost(rt->out_ctl);
+        cudaFreeHost(rt->out_status);
         cudaFree(rt->d_euler);
         cudaFree(rt->d_fim);
         cudaFree(rt->d_table);
@@ -1263,6 +1450,11 @@ void batch_runtime_destroy(ripple_ctx ctx)
         cudaFreeHost(rt->h_fim);
         cudaFreeHost(rt->h_table);
         cudaEventDestroy(rt->ev_step);
+        cudaEventDestroy(rt->ev_items);
+        for (cudaEvent_t e : rt->ev_pool) cudaEventDestroy(e);
+        rt->ev_pool.clear();
+        cudaFreeHost(rt->h_items);
+        cudaFree(rt->d_items);
         if (rt->pool) cudaMemPoolDestroy(rt->pool);
         cudaEventDestroy(rt->ev_r0);
         cudaEventDestroy(rt->ev_r1);

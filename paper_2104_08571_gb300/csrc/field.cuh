@@ -54,4 +54,24 @@ struct FieldCtl {
     long long counters[8];       // solver counters (eikonal iterations, visits, ...)
 };
 
+
+// One instance of a grouped admission or download of the batch runtime (the
+// kernels are in euler_aux.cuh): every instance of a group owns a contiguous
+// run of blocks of one launch, blk[pass] its first block in launch `pass`
+// (an instance with no blocks in a launch repeats the next one's value).
+constexpr int kGroupCellsPerBlock = 2048;  // 256 threads x 8 cells
+
+struct GroupItem {
+    void* buf;                    // admission: buffer 0; download: the buffer holding the result
+    void* other;                  // admission: buffer 1, dense input on entry; download: the dense stage
+    FieldCtl* ctl;                // the instance's slot entries
+    unsigned long long* status;
+    long long* counters;
+    FieldGeom g;
+    double gamma, inv_dx0, inv_dx1;
+    int bc;
+    int euler;                    // 1: Euler state (fill and prepare), 0: eikonal (slot reset only)
+    long long blk[2];
+};
+
 }  // namespace ripple

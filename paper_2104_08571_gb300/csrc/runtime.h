@@ -120,6 +120,11 @@ cudaError_t launch_totals(int dtype, int ncomp, const void* buf, const FieldGeom
                           FieldCtl* ctl, cudaStream_t s);
 cudaError_t launch_interior_copy(int dtype, void* buf, const FieldGeom& g, void* dense, int dense_layout, int dir,
                                  int grid, cudaStream_t s);
+// Grouped admission (op 0: fill buffer 0 and clear the slot, op 1: boundary
+// images, wave speeds and buffer 1's padding) and download (op 2: pack) of
+// the batch runtime over n device-resident GroupItems (field.cuh).
+enum : int { GROUP_ADMIT_FILL = 0, GROUP_ADMIT_PREP = 1, GROUP_PACK = 2 };
+cudaError_t launch_group(int dtype, int op, const GroupItem* items, int n, long long blocks, cudaStream_t s);
 
 // Tensor-map cache entry.
 struct MapEntry {
