@@ -296,14 +296,14 @@ typedef struct {
                                  is the CFL limit of its whole state), with no barrier between
                                  problems or global steps.  Uses TMA staging whatever `staging`
                                  says.  0 = one launch per global step (default). */
-    int solo_rounds;          /* 1 = a problem that is the only resident one runs on the single-problem
-                                 kernels (Euler: up to 64 steps per round of the field sweep kernel;
-                                 eikonal, before its first batched iteration: one persistent FIM solve),
-                                 lowering the latency of requests served at low load.  Eikonal results
-                                 are bitwise those of batched rounds; Euler results agree to FP32
-                                 rounding (the field kernel orders its arithmetic differently), so
-                                 bitwise equality of a result alone and in a mix holds with 0.
-                                 Default 1. */
+    int solo_rounds;          /* 1 = while at most four problems are resident (none of them an eikonal
+                                 problem already iterating in batched rounds), each round runs the one
+                                 with the least estimated time left alone on the single-problem kernels
+                                 (Euler: one launch of the multi-step solver, up to about a millisecond
+                                 of steps; eikonal: one persistent FIM solve), lowering the latency of
+                                 requests served at low load; more resident problems run in batched
+                                 rounds.  Results are bitwise those of batched rounds (the solvers
+                                 share the per-step arithmetic).  Default 1. */
 } ripple_batch_config;
 
 typedef struct {

@@ -23,6 +23,8 @@
 #include <unordered_map>
 
 #include "batch_kernels.cuh"
+#include "euler_solo2d.cuh"
+#include "grid_sync.cuh"
 #include "runtime.h"
 
 namespace ripple {
@@ -170,8 +172,6 @@ struct Inst {
     bool stepped = false;       // taken part in a compute round
     CUtensorMap map[2];         // Euler: TMA maps of buf[0], buf[1] (cached per tile variant and layout)
     int map_key = -1;
-    CUtensorMap solo_map[2][2];  // Euler: staging (kind 0) and store (kind 1) maps of buf[0], buf[1] for the
-    int solo_v = -1;             // field sweep kernel of variant solo_v (solo rounds)
     struct GroupEv* gev = nullptr;  // completion of the instance's admission or download group
     ripple_status result = RIPPLE_OK;
     double t_submit = 0, t_admit = 0, t_start = 0, t_finish = 0;
@@ -212,6 +212,8 @@ struct BatchRuntime {
     std::vector<cudaEvent_t> ev_pool;  // events of finished groups, for reuse
     // descriptors of the current admission or download group: pinned host
     // array, its device copy (both kSlots long) and the event after the copy
+    unsigned* d_solo_bar = nullptr;  // arrival counter of the multi-step solo launches' grid barrier
+    int solo_occ[2] = {0, 0};        // resident CTAs per SM of the solo kernel (FP32, FP64)
     GroupItem* h_items = nullptr;
     GroupItem* d_items = nullptr;
     cudaEvent_t ev_items = nullptr;
@@ -871,30 +873,52 @@ static void collect_finished(BatchRuntime* rt)
     add_host_time(rt, &ripple_batch_stats::host_finish_s, t0);
 }
 
-// Solo rounds: a problem that has the GPU to itself runs on the single-problem
-// kernels, whose per-problem cost is lower than the batched launches' (no
-// work-queue indirection, no launch wide enough for the whole resident set):
-//   * an Euler problem takes up to kSoloSteps steps of the field sweep kernel
-//     (the packed-pair kernel in FP32) on its own buffers and control block; the
-//     step conventions are those of the batched step (buffer parity = step
-//     parity, the 3-slot wave-speed ring indexed by the step), so the problem
-//     continues in batched rounds when others join;
+// Solo rounds: while few problems are resident (at most kSoloMaxResident, and
+// none of them an eikonal problem already iterating in batched rounds), each
+// round gives the GPU to ONE of them, the one with the least estimated solo
+// time left (shortest remaining time first), on the single-problem kernels,
+// whose cost per problem is lower than the batched launches' (no work-queue
+// indirection, no per-step launch, no lockstep with a larger problem):
+//   * an Euler problem takes up to kSoloMaxSteps steps (about a millisecond of
+//     work at most) in one launch of the multi-step solver (euler_solo2d.cuh)
+//     on its own buffers and control block; its steps are the batched step's
+//     bit for bit (buffer parity = step parity, the 3-slot wave-speed ring
+//     indexed by the step), so the problem continues in batched rounds when
+//     others join;
 //   * an eikonal problem that has not iterated yet is solved whole by the
 //     persistent FIM kernel (lists of active tiles), one launch.
-// Requests arriving meanwhile are admitted after the round.
-constexpr long long kSoloSteps = 64;
+// Requests arriving meanwhile are admitted after the round.  More resident
+// problems than that run in batched rounds, where one launch steps all of them.
+constexpr long long kSoloMaxSteps = 1024;
+constexpr size_t kSoloMaxResident = 4;
+
+// Solo GPU seconds an Euler step of `cells` cells takes (a fit of the
+// multi-step solver on GB300: a fixed barrier and dt cost, then the cells).
+static double solo_step_seconds(double cells) { return 3.3e-6 + 12e-12 * cells; }
+
+// Estimated solo GPU seconds a resident problem still needs.
+static double solo_remaining(const Inst* in)
+{
+    const double cells = (double)in->req.dims[0] * (double)in->req.dims[1];
+    if (in->req.kind == RIPPLE_REQ_EULER) return (double)(in->req.nsteps - in->steps_done) * solo_step_seconds(cells);
+    return 2e-4 + 0.7e-9 * cells;  // one persistent FIM solve
+}
 
 static ripple_status solo_round(BatchRuntime* rt, bool& handled)
 {
     handled = false;
-    if (!rt->cfg.solo_rounds || rt->resident.size() != 1 || rt->cfg.async_queue) return RIPPLE_OK;
-    Inst* in = rt->resident[0];
+    if (!rt->cfg.solo_rounds || rt->cfg.async_queue || rt->resident.empty() ||
+        rt->resident.size() > kSoloMaxResident)
+        return RIPPLE_OK;
+    Inst* in = nullptr;
+    for (Inst* r : rt->resident) {
+        if (r->req.kind == RIPPLE_REQ_EIKONAL && r->stepped) return RIPPLE_OK;  // iterating in batched rounds
+        if (!in || solo_remaining(r) < solo_remaining(in)) in = r;
+    }
     const ripple_dtype dt = rt->cfg.dtype;
-    const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
     cudaStream_t s = rt->compute;
     FieldCtl* ctl = &rt->slot_ctl[in->slot];
     if (in->req.kind == RIPPLE_REQ_EIKONAL) {
-        if (in->stepped) return RIPPLE_OK;  // already iterating in batched rounds
         handled = true;
         RIPPLE_CUDA(cudaEventRecord(rt->ev_r0, s));
         const long long max_iters = in->req.eik.max_iters > 0 ? in->req.eik.max_iters : 1000000;
@@ -919,66 +943,68 @@ static ripple_status solo_round(BatchRuntime* rt, bool& handled)
         RIPPLE_CUDA(cudaEventRecord(rt->ev_step, s));
         RIPPLE_CUDA(cudaEventSynchronize(rt->ev_step));
     } else {
-        const int scheme = SCHEME_RUSANOV1;
-        int v = dt == RIPPLE_F32 && sweep_smem(dt, 2, layout, scheme, kPairVariant) > 0 ? kPairVariant : -1;
-        for (int c = 0; c < kNumSweepVariants && v < 0; ++c)
-            if (c != kRowVariant && sweep_smem(dt, 2, layout, scheme, c) > 0) v = c;
-        if (v < 0) return RIPPLE_OK;  // no field kernel for this configuration: batched rounds
         handled = true;
-        const int tx = kSweepVariants[v].tx, ty = kSweepVariants[v].ty;
-        const ripple_layout rl = rt->cfg.layout;
-        if (in->solo_v != v) {
-            for (int b = 0; b < 2; ++b) {
-                ripple_status st = encode_plane_map(in->buf[b], in->g, rl, dt, 0, 1, tx, ty, &in->solo_map[b][0]);
-                if (st == RIPPLE_OK) st = encode_plane_map(in->buf[b], in->g, rl, dt, 1, 1, tx, ty, &in->solo_map[b][1]);
-                if (st != RIPPLE_OK) return st;
-            }
-            in->solo_v = v;
-        }
         const ripple_request& r = in->req;
-        SweepLaunch L{};
-        L.sg.f = in->g;
-        L.sg.tiles_x = (int)((r.dims[0] + tx - 1) / tx);
-        L.sg.tiles_y = (int)((r.dims[1] + ty - 1) / ty);
-        L.sg.zchunk = 1;
-        L.sg.chunks_z = 1;
-        L.sg.items = L.sg.tiles_x * L.sg.tiles_y;
-        L.grid = std::min(L.sg.items, std::max(1, sweep_occ(dt, 2, layout, scheme, v)) * rt->ctx->sm_count);
-        L.ctl = ctl;
-        L.stream = s;
-        L.prm.gamma = r.fv.gamma;
-        L.prm.cfl = r.fv.cfl;
-        L.prm.inv_dx[0] = 1.0 / r.fv.dx[0];
-        L.prm.inv_dx[1] = 1.0 / r.fv.dx[1];
-        L.prm.inv_dx[2] = 0.0;
-        L.prm.gamma_f = (float)r.fv.gamma;
-        L.prm.gm1_f = (float)(r.fv.gamma - 1.0);
-        for (int d = 0; d < 3; ++d) L.prm.inv_dx_f[d] = (float)L.prm.inv_dx[d];
-        L.prm.bc = (int)r.fv.bc;
-        L.prm.axis = -1;
-        L.prm.last = 1;
-        const long long K = std::min<long long>(kSoloSteps, r.nsteps - in->steps_done);
+        const long long cells = r.dims[0] * r.dims[1];
+        // a launch of about a millisecond at most, so arrivals wait little
+        const double est_step = solo_step_seconds((double)cells);
+        const long long K = std::min<long long>(
+            r.nsteps - in->steps_done, std::max<long long>(8, std::min<long long>(kSoloMaxSteps, (long long)(1e-3 / est_step))));
+        SoloEuler a{};
+        a.buf[0] = in->buf[0];
+        a.buf[1] = in->buf[1];
+        a.ctl = ctl;
+        a.g = in->g;
+        a.bc = (int)r.fv.bc;
+        a.K = (int)K;
+        a.first = in->steps_done;
+        a.cfl = r.fv.cfl;
+        a.gamma = r.fv.gamma;
+        a.gm1 = r.fv.gamma - 1.0;
+        a.inv_dx0 = 1.0 / r.fv.dx[0];
+        a.inv_dx1 = 1.0 / r.fv.dx[1];
+        a.gamma_f = (float)a.gamma;
+        a.gm1_f = (float)a.gm1;
+        a.inv_dx0_f = (float)a.inv_dx0;
+        a.inv_dx1_f = (float)a.inv_dx1;
+        a.bar = rt->d_solo_bar;
+        a.spin_limit = grid_spin_limit();
+        a.err = &rt->d_bctl->err;
+        const int n0 = (int)r.dims[0], n1 = (int)r.dims[1];
+        const int per_sm = dt == RIPPLE_F32 ? rt->solo_occ[0] : rt->solo_occ[1];  // at kSoloThreads
+        const int sms = rt->ctx->sm_count;
+        a.strips = (n0 + kSoloW - 1) / kSoloW;
+        // segments as short as one row while the units fit one full CTA per SM
+        const long long most = (long long)sms * (kSoloThreads / 32);
+        a.rows = (int)std::min<long long>(n1, std::max<long long>(1, ((long long)n1 * a.strips + most - 1) / most));
+        a.segs = (n1 + a.rows - 1) / a.rows;
+        const long long units = (long long)a.strips * a.segs;
+        // CTAs of as few warps as spread the units over every SM (a small
+        // problem's step is then short chains on many SMs, not long ones on few)
+        const int wpc = (int)std::min<long long>(kSoloThreads / 32, std::max<long long>(1, (units + sms - 1) / sms));
+        const int grid = (int)std::max<long long>(
+            1, std::min<long long>((units + wpc - 1) / wpc, (long long)std::max(1, per_sm) * sms));
+        RIPPLE_CUDA(cudaMemsetAsync(rt->d_solo_bar, 0, 2 * sizeof(unsigned), s));
         RIPPLE_CUDA(cudaEventRecord(rt->ev_r0, s));
-        for (long long k = 0; k < K; ++k) {
-            const long long step = in->steps_done + k;
-            const int b = (int)(step & 1);
-            L.map_in = &in->solo_map[b][0];
-            L.map_out = &in->solo_map[1 - b][1];
-            L.out = in->buf[1 - b];
-            L.prm.slot_in = (int)(step % 3);
-            L.prm.first = step == 0;
-            RIPPLE_CUDA(sweep_launch(dt, 2, layout, scheme, v, L));
-        }
+        void* args[] = {&a};
+        const void* kern = dt == RIPPLE_F32 ? (const void*)solo_euler2d_kernel<float>
+                                            : (const void*)solo_euler2d_kernel<double>;
+        RIPPLE_CUDA(cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(32 * wpc), args, 0, s));
         RIPPLE_CUDA(cudaEventRecord(rt->ev_r1, s));
+        RIPPLE_CUDA(cudaMemcpyAsync(rt->h_berr, &rt->d_bctl->err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         RIPPLE_CUDA(cudaEventRecord(rt->ev_step, s));
         RIPPLE_CUDA(cudaEventSynchronize(rt->ev_step));
+        if (*rt->h_berr) {
+            RIPPLE_CUDA(cudaMemsetAsync(&rt->d_bctl->err, 0, sizeof(unsigned), s));
+            return fail(RIPPLE_ERR_TIMEOUT, "a grid barrier wait of a solo round ran out");
+        }
         in->steps_done += K;
         // the batched step finds a problem's local step as (global step - start_step)
         in->start_step -= K;
         in->active = true;
         rt->dirty = true;
         std::lock_guard<std::mutex> lk(rt->mu);
-        rt->stats.launches += K;
+        rt->stats.launches += 1;
     }
     in->stepped = true;
     float round_ms = 0.f;
@@ -1245,6 +1271,11 @@ static ripple_status rt_start(BatchRuntime* rt)
     RIPPLE_CUDA(cudaEventCreateWithFlags(&rt->ev_step, cudaEventDisableTiming));
     RIPPLE_CUDA(cudaEventCreateWithFlags(&rt->ev_items, cudaEventDisableTiming));
     RIPPLE_CUDA(cudaMallocHost(&rt->h_items, kSlots * sizeof(GroupItem)));
+    RIPPLE_CUDA(cudaMalloc(&rt->d_solo_bar, 2 * sizeof(unsigned)));
+    RIPPLE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rt->solo_occ[0], solo_euler2d_kernel<float>,
+                                                              kSoloThreads, 0));
+    RIPPLE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rt->solo_occ[1], solo_euler2d_kernel<double>,
+                                                              kSoloThreads, 0));
     RIPPLE_CUDA(cudaMalloc(&rt->d_items, kSlots * sizeof(GroupItem)));
     RIPPLE_CUDA(cudaEventCreate(&rt->ev_r0));
     RIPPLE_CUDA(cudaEventCreate(&rt->ev_r1));
@@ -1454,6 +1485,7 @@ void batch_runtime_destroy(ripple_ctx ctx)
         for (cudaEvent_t e : rt->ev_pool) cudaEventDestroy(e);
         rt->ev_pool.clear();
         cudaFreeHost(rt->h_items);
+        cudaFree(rt->d_solo_bar);
         cudaFree(rt->d_items);
         if (rt->pool) cudaMemPoolDestroy(rt->pool);
         cudaEventDestroy(rt->ev_r0);

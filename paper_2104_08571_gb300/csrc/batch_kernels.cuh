@@ -420,11 +420,10 @@ __global__ void __launch_bounds__(288) batch_euler_kernel(const BatchEuler* __re
             const int o = PV::idx(lx, ly, 0);
             T qn[NC];
 #pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                T acc = (FX[m * NFX + ly * (TX + 1) + lx + 1] - FX[m * NFX + ly * (TX + 1) + lx]) * inv_dx[0];
-                acc += (FY[m * NFY + (ly + 1) * TX + lx] - FY[m * NFY + ly * TX + lx]) * inv_dx[1];
-                qn[m] = S[o + m * SM] - dtT * acc;
-            }
+            for (int m = 0; m < NC; ++m)
+                qn[m] = cell_update2(S[o + m * SM], FX[m * NFX + ly * (TX + 1) + lx], FX[m * NFX + ly * (TX + 1) + lx + 1],
+                                     FY[m * NFY + ly * TX + lx], FY[m * NFY + (ly + 1) * TX + lx], inv_dx[0], inv_dx[1],
+                                     dtT);
             const long long base = geom_cell(g, gx, gy, 0) * g.cell_stride;
 #pragma unroll
             for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = qn[m];
@@ -613,11 +612,9 @@ __global__ void __launch_bounds__(256) batch_euler_direct_kernel(const BatchEule
         if ((gx < g.n[0]) & (gy < g.n[1])) {
             T qn[NC];
 #pragma unroll
-            for (int m = 0; m < NC; ++m) {
-                T acc = (FX[m][ly * (TX + 1) + lx + 1] - FX[m][ly * (TX + 1) + lx]) * inv_dx[0];
-                acc += (FY[m][(ly + 1) * TX + lx] - FY[m][ly * TX + lx]) * inv_dx[1];
-                qn[m] = S[m][ly + 1][lx + 1] - dtT * acc;
-            }
+            for (int m = 0; m < NC; ++m)
+                qn[m] = cell_update2(S[m][ly + 1][lx + 1], FX[m][ly * (TX + 1) + lx], FX[m][ly * (TX + 1) + lx + 1],
+                                     FY[m][ly * TX + lx], FY[m][(ly + 1) * TX + lx], inv_dx[0], inv_dx[1], dtT);
             const long long base = geom_cell(g, gx, gy, 0) * g.cell_stride;
 #pragma unroll
             for (int m = 0; m < NC; ++m) out[base + (long long)m * g.comp_stride] = qn[m];

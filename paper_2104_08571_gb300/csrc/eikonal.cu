@@ -29,13 +29,11 @@
 #include <vector>
 
 #include "fim_tile.cuh"
+#include "grid_sync.cuh"
 #include "runtime.h"
 
 namespace ripple {
 
-// Default bound on the polls of a grid-barrier wait (several seconds).  The
-// host may lower it (RIPPLE_GRID_SPIN_LIMIT) to exercise the timeout path.
-constexpr uint32_t kGridSpinLimit = 1u << 26;
 constexpr int kFimCtasPerSm2D = 1;
 
 // Arguments of the persistent single-problem solve beyond the problem itself.
@@ -51,34 +49,6 @@ struct EikScratch {
     void* mem = nullptr;
     int ntiles = 0;
 };
-
-// Bounded sense-reversal grid barrier.  Returns false if the wait ran out.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned spin_limit, int* sflag)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
-        const unsigned g0 = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) == nblocks - 1) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
-        } else {
-            uint32_t i = 0;
-            while (*gen == g0) {
-                if (i++ >= spin_limit) {
-                    sflag[0] = 1;
-                    break;
-                }
-                __nanosleep(32);
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-    return sflag[0] == 0;
-}
 
 template <typename T, int DIM>
 __global__ void __launch_bounds__(EikTile<DIM>::NT) fim_kernel(const FimProblem<T> a, const EikArgs e)
@@ -267,12 +237,7 @@ ripple_status fim_solve_lists(FimProblem<T> a, void* scratch, FieldCtl* ctl, lon
     EikArgs e{};
     e.max_iters = max_iters > 0 ? max_iters : 1000000;
     e.bar = reinterpret_cast<unsigned*>(base + 16);
-    e.spin_limit = kGridSpinLimit;
-    if (const char* lim = std::getenv("RIPPLE_GRID_SPIN_LIMIT")) {
-        char* end = nullptr;
-        const unsigned long v = std::strtoul(lim, &end, 10);
-        if (end != lim && v < kGridSpinLimit) e.spin_limit = (unsigned)v;
-    }
+    e.spin_limit = grid_spin_limit();
     e.ctl = ctl;
     RIPPLE_CUDA(cudaMemsetAsync(scratch, 0, fim_list_scratch_bytes(a.ntiles), s));
     RIPPLE_CUDA(cudaMemsetAsync(ctl->counters, 0, sizeof(ctl->counters), s));

@@ -1,0 +1,232 @@
+// Multi-step solver of ONE 2D Euler problem (first-order Rusanov), the
+// single-problem kernel of the batch runtime's solo rounds.
+//
+// One cooperative launch advances the problem K steps; a bounded grid barrier
+// separates the steps.  Per launched step the field and batched step kernels
+// pay a launch, a pipeline fill and a grid drain (about 8 us at 64^2, so small
+// problems were bound by that floor); here a step costs its arithmetic and one
+// barrier, and the state of the served sizes (up to 1024^2, 16 MB per buffer)
+// stays in L2 between steps.  The step's FP64 work (dt = cfl / smax) is one
+// division per CTA, broadcast through shared memory: FP64 issues at 1/64 of
+// the FP32 rate on GB300, and a division in every thread cost about 4 us per
+// step.  The barrier is one monotonic arrival counter (a release add per CTA,
+// acquire polls for the step's target count), with at most one CTA per SM
+// arriving.
+//
+// Work: warps walk units of (strip of 30 columns) x (segment of R rows).  The
+// 32 lanes of a warp hold the columns x0 - 1 .. x0 + 30 of the current row:
+// lane l evaluates the x face between its left neighbour (shuffled from lane
+// l - 1) and itself, the right face of a cell is its right neighbour's left
+// face (shuffled back), so lanes 1..30 update their cells with every x face
+// evaluated once; along y each lane carries the face below its cell from the
+// previous row and prefetches the row two ahead.
+//
+// The step is the batched step's, term for term: dt = cfl / smax of the input
+// state (FP64, from the instance's 3-slot ring), the same Rusanov faces of the
+// same left/right states (a face's value depends only on its two states), the
+// same cell update (cell_update2), ghost images and wave-speed maximum.  A
+// problem's state is therefore bitwise the same whichever kernel advanced
+// which of its steps.
+#pragma once
+#include <cstdint>
+
+#include "batch_kernels.cuh"
+
+namespace ripple {
+
+constexpr int kSoloW = 30;           // cells a warp updates per row
+constexpr int kSoloThreads = 1024;   // 32 warps per CTA, one CTA per SM
+
+struct SoloEuler {
+    void* buf[2];
+    FieldCtl* ctl;
+    FieldGeom g;
+    int bc;
+    int K;                    // steps of this launch
+    long long first;          // local step index of the first of them
+    int strips, segs, rows;   // units: strips x segs, segment height `rows`
+    double cfl, gamma, gm1, inv_dx0, inv_dx1;
+    float gamma_f, gm1_f, inv_dx0_f, inv_dx1_f;
+    unsigned* bar;            // grid barrier: arrivals of this launch (zero at launch)
+    unsigned spin_limit;      // polls of a barrier wait before it gives up
+    unsigned* err;            // DEV_ERR_TIMEOUT when a barrier wait ran out
+};
+
+template <typename T>
+__device__ __forceinline__ void solo_load(const T* __restrict__ in, const FieldGeom& g, int x, int y, T (&q)[4])
+{
+    const long long base = geom_cell(g, x, y, 0) * g.cell_stride;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) q[m] = ldcg_t(in + base + (long long)m * g.comp_stride);
+}
+
+// Arrive at barrier number b (1, 2, ...) of the launch and wait until every
+// CTA has arrived.  Returns false if the wait ran out (bounded polls).  Thread
+// 0 arrives after its own earlier writes (release) and the other threads'
+// writes (the CTA barrier before it).
+__device__ __forceinline__ bool solo_barrier(unsigned* count, unsigned b, unsigned spin_limit, int* sflag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        const unsigned target = b * gridDim.x;
+        uint32_t i = 0;
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+            if (v >= target) break;
+            if (++i > spin_limit) {
+                sflag[0] = 1;
+                break;
+            }
+        }
+    }
+    __syncthreads();
+    return sflag[0] == 0;
+}
+
+// Registers of a warp's current unit: the rows below, at, above and two above
+// the current row, the face below the current row, the admissibility trackers.
+template <typename T>
+struct SoloUnit {
+    int strip, x, xl, y0, y1;
+    bool upd, xface;
+    T chk;
+    bool bad;
+    T qc[4], qa[4], qf[4], Fb[4];
+};
+
+// Start unit u: its first rows and the face below its first row (none of it
+// depends on dt, so the first unit of a step starts before dt is known).
+template <typename T>
+__device__ __forceinline__ void solo_unit_begin(const SoloEuler& a, const T* __restrict__ in, int u, int lane,
+                                                T gamma, T gm1, SoloUnit<T>& w)
+{
+    const FieldGeom& g = a.g;
+    w.strip = u % a.strips;
+    const int seg = u / a.strips;
+    w.x = w.strip * kSoloW - 1 + lane;
+    w.xl = min(w.x, g.n[0]);  // columns past the ghost column load the ghost (unused)
+    w.upd = lane >= 1 && lane <= kSoloW && w.x < g.n[0];
+    w.xface = lane >= 1 && w.x <= g.n[0];
+    w.y0 = seg * a.rows;
+    w.y1 = min(g.n[1], w.y0 + a.rows);
+    w.chk = T(1);
+    w.bad = false;
+    T qd[4];
+    solo_load(in, g, w.xl, w.y0 - 1, qd);
+    solo_load(in, g, w.xl, w.y0, w.qc);
+    solo_load(in, g, w.xl, w.y0 + 1, w.qa);  // y0 + 1 <= n[1]: at most the ghost row
+    if (w.y0 + 2 <= g.n[1]) solo_load(in, g, w.xl, w.y0 + 2, w.qf);
+    rusanov<T, 2, 1>(qd, w.qc, gamma, gm1, w.Fb, w.chk, w.upd);
+}
+
+// Walk the started unit's rows: faces, update, stores, ghost images.
+template <typename T>
+__device__ __forceinline__ void solo_unit_walk(const SoloEuler& a, const T* __restrict__ in, T* __restrict__ out,
+                                               T gamma, T gm1, const T (&inv_dx)[3], T dtT, SoloUnit<T>& w,
+                                               T& smax)
+{
+    const FieldGeom& g = a.g;
+    for (int y = w.y0; y < w.y1; ++y) {
+        // rows y + 1 (qa) and y + 2 (qf) are loaded; fetch row y + 3
+        T qg[4];
+        if (y + 3 <= g.n[1]) solo_load(in, g, w.xl, y + 3, qg);
+        T Fa[4], Fl[4], Fr[4], left[4];
+        rusanov<T, 2, 1>(w.qc, w.qa, gamma, gm1, Fa, w.chk, w.upd);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) left[m] = __shfl_up_sync(0xffffffffu, w.qc[m], 1);
+        rusanov<T, 2, 0>(left, w.qc, gamma, gm1, Fl, w.chk, w.xface);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) Fr[m] = __shfl_down_sync(0xffffffffu, Fl[m], 1);
+        if (w.upd) {
+            T qn[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                qn[m] = cell_update2(w.qc[m], Fl[m], Fr[m], w.Fb[m], Fa[m], inv_dx[0], inv_dx[1], dtT);
+            const long long base = geom_cell(g, w.x, y, 0) * g.cell_stride;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) out[base + (long long)m * g.comp_stride] = qn[m];
+            bool ok;
+            smax = max(smax, wave_sum<T, 2>(qn, gamma, gm1, inv_dx, ok));
+            w.bad |= !ok;
+            if (w.x < g.h || w.x >= g.n[0] - g.h || y < g.h || y >= g.n[1] - g.h)
+                write_ghost_images<T, 2>(out, g, a.bc, w.x, y, 0, qn);
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            w.Fb[m] = Fa[m];
+            w.qc[m] = w.qa[m];
+            w.qa[m] = w.qf[m];
+            w.qf[m] = qg[m];
+        }
+    }
+}
+
+// Launched with blockDim.x a multiple of 32, at most kSoloThreads: the host
+// sizes CTAs so that the units spread over as many SMs as possible.
+template <typename T>
+__global__ void __launch_bounds__(kSoloThreads) solo_euler2d_kernel(const SoloEuler a)
+{
+    __shared__ int sflag[1];
+    __shared__ T s_dt[1];
+    __shared__ T s_max[kSoloThreads / 32];
+    if (threadIdx.x == 0) sflag[0] = 0;
+    FieldCtl* ctl = a.ctl;
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+    const int warp = blockIdx.x * wpc + wib;
+    const int nwarps = gridDim.x * wpc;
+    const int units = a.strips * a.segs;
+    const T gamma = field_const<T>(a.gamma, a.gamma_f), gm1 = field_const<T>(a.gm1, a.gm1_f);
+    const T inv_dx[3] = {field_const<T>(a.inv_dx0, a.inv_dx0_f), field_const<T>(a.inv_dx1, a.inv_dx1_f), T(0)};
+    for (int k = 0; k < a.K; ++k) {
+        const long long local = a.first + k;
+        const int rs = (int)(local % 3);
+        const T* __restrict__ in = static_cast<const T*>(a.buf[local & 1]);
+        T* __restrict__ out = static_cast<T*>(a.buf[(local & 1) ^ 1]);
+        if (threadIdx.x == 0) {
+            const double dt = a.cfl / __longlong_as_double((long long)__ldcg(&ctl->smax[rs]));
+            s_dt[0] = (T)dt;
+            if (blockIdx.x == 0) {
+                ctl->t = local == 0 ? dt : ctl->t + dt;
+                ctl->dt_last = dt;
+                ctl->smax[(rs + 2) % 3] = 0ull;
+            }
+        }
+        SoloUnit<T> w;
+        int u = warp;
+        if (u < units) solo_unit_begin(a, in, u, lane, gamma, gm1, w);
+        __syncthreads();  // s_dt
+        const T dtT = s_dt[0];
+        T smax = T(0);
+        while (u < units) {
+            solo_unit_walk(a, in, out, gamma, gm1, inv_dx, dtT, w, smax);
+            // a non-admissible face or new state: the unit's first cell and row
+            if (__any_sync(0xffffffffu, w.bad || !(w.chk > T(0))) && lane == 0) {
+                record_bad(ctl, BAD_STATE, w.strip * kSoloW, w.y0, 0);
+                atomicOr(&ctl->err, DEV_ERR_NUMERIC);
+            }
+            u += nwarps;
+            if (u < units) solo_unit_begin(a, in, u, lane, gamma, gm1, w);
+        }
+        // CTA maximum of the new wave-speed sums -> the next ring slot (one
+        // atomic per CTA, before the CTA's arrival at the barrier)
+        T v = smax;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) s_max[wib] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            T m = s_max[0];
+            for (int i = 1; i < wpc; ++i) m = max(m, s_max[i]);
+            atomic_max_pos_double(&ctl->smax[(rs + 1) % 3], (double)m);
+        }
+        if (k + 1 < a.K && !solo_barrier(a.bar, (unsigned)(k + 1), a.spin_limit, sflag)) {
+            if (threadIdx.x == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
+            return;
+        }
+    }
+}
+
+}  // namespace ripple

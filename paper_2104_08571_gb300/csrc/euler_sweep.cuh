@@ -178,6 +178,18 @@ __device__ __forceinline__ void rusanov(const T (&a)[DIM + 2], const T (&b)[DIM 
     for (int m = 0; m < DIM + 2; ++m) F[m] = T(0.5) * (Fa[m] + Fb[m]) - T(0.5) * s * (b[m] - a[m]);
 }
 
+// First-order conservative update of one component of a 2D cell from its
+// four face fluxes (x: left, right; y: below, above).  The batched step and
+// the multi-step solo solver share this arithmetic, so a problem's state does
+// not depend on which of them advanced it.
+template <typename T>
+__device__ __forceinline__ T cell_update2(T q, T fxl, T fxr, T fyd, T fyu, T inv_dx0, T inv_dx1, T dt)
+{
+    T acc = (fxr - fxl) * inv_dx0;
+    acc += (fyu - fyd) * inv_dx1;
+    return q - dt * acc;
+}
+
 // Rusanov face flux from states whose 1/rho and sound speed were formed once
 // per cell beforehand (the FP64 path, where division and square root are
 // the costly operations): the same flux as rusanov().

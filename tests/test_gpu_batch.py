@@ -101,10 +101,10 @@ def test_alone_equals_in_mix_bitwise(ctx):
 
 def test_solo_rounds_alone_and_in_mix(ctx):
     """A request served alone runs on the single-problem kernels (solo rounds):
-    an Euler problem within FP32 rounding of the same problem in a mix (batched
-    kernel), also when it is joined by other requests part-way (it then
-    continues on the batched kernel from its own step); an eikonal problem with
-    the same bits; both against the oracle."""
+    an Euler problem on the multi-step solver, bit for bit the batched step,
+    also when it is joined by other requests part-way (it then continues on
+    the batched kernel from its own step); an eikonal problem with the same
+    bits; both against the oracle."""
     R.ripple_batch_configure(ctx)  # solo rounds on (the default)
     a = _euler(150, 130, 0.25, 150)
     e = _eik(200, 170, 8)
@@ -113,7 +113,7 @@ def test_solo_rounds_alone_and_in_mix(ctx):
     mix = [_again(a), _euler(64, 64, 0.1, 40), _again(e), _euler(40, 40, 0.2, 20)]
     infos = _run(ctx, mix)
     assert all(i["status"] == R.RIPPLE_OK for i in infos)
-    assert rel_l1(mix[0]["output"], a["output"]) <= 1e-6
+    assert np.array_equal(mix[0]["output"], a["output"])
     assert np.array_equal(mix[2]["output"], e["output"])
     assert_parity(a["output"], _oracle_euler(a), 2e-5, LINF_F32)
     # joined part-way: a long problem alone, a second one submitted while it runs
@@ -126,6 +126,53 @@ def test_solo_rounds_alone_and_in_mix(ctx):
     assert R.ripple_wait(ctx, t2[0], 120000)["status"] == R.RIPPLE_OK
     assert_parity(long["output"], _oracle_euler(long), 2e-5, LINF_F32)
     assert_parity(late["output"], _oracle_euler(late), 2e-5, LINF_F32)
+    R.ripple_batch_configure(ctx, solo_rounds=False)
+    batched = [_again(long), _again(late)]
+    _run(ctx, batched)
+    assert np.array_equal(batched[0]["output"], long["output"])
+    assert np.array_equal(batched[1]["output"], late["output"])
+
+
+@pytest.mark.parametrize("layout", [R.RIPPLE_SOA, R.RIPPLE_AOS])
+@pytest.mark.parametrize("dtype", [R.RIPPLE_F32, R.RIPPLE_F64])
+def test_solo_solver_equals_batched_step_bitwise(ctx, layout, dtype):
+    """The multi-step solo solver against the batched step, bit for bit, on
+    grids that leave ragged strips (widths not multiples of 30) and segments,
+    one-cell-wide and one-row grids, both boundary conditions."""
+    npdt = np.float32 if dtype == R.RIPPLE_F32 else np.float64
+    shapes = [(64, 64, 0.2, 120, R.RIPPLE_BC_PERIODIC), (31, 47, 0.3, 77, R.RIPPLE_BC_TRANSMISSIVE),
+              (1, 40, 0.1, 20, R.RIPPLE_BC_PERIODIC), (45, 1, 0.1, 20, R.RIPPLE_BC_TRANSMISSIVE),
+              (2, 2, 0.2, 9, R.RIPPLE_BC_PERIODIC), (611, 333, 0.15, 60, R.RIPPLE_BC_PERIODIC),
+              (1000, 700, 0.2, 330, R.RIPPLE_BC_TRANSMISSIVE)]  # the last takes several solo launches
+    out = {}
+    for solo in (True, False):
+        R.ripple_batch_configure(ctx, layout=layout, dtype=dtype, solo_rounds=solo)
+        res = []
+        for nx, ny, amp, nsteps, bc in shapes:
+            U = inputs.euler2d_sine(nx, amp=amp, ny=ny).astype(npdt)
+            req = R.euler_request(U, nsteps, [1.0 / nx, 1.0 / ny], bc=bc)
+            info = _run(ctx, [req])[0]
+            assert info["status"] == R.RIPPLE_OK and info["work"] == nsteps
+            res.append((req["output"], info["t"]))
+        out[solo] = res
+    R.ripple_batch_configure(ctx, solo_rounds=False)
+    for (a, ta), (b, tb), shp in zip(out[True], out[False], shapes):
+        assert np.array_equal(a, b), shp
+        assert ta == tb, shp
+
+
+def test_solo_barrier_timeout_reports(ctx, monkeypatch):
+    """A grid-barrier wait of the solo solver that runs out (the wait bound
+    forced to zero polls) fails the request with RIPPLE_ERR_TIMEOUT; the
+    runtime keeps serving."""
+    monkeypatch.setenv("RIPPLE_GRID_SPIN_LIMIT", "0")
+    R.ripple_batch_configure(ctx)
+    info = _run(ctx, [_euler(300, 300, 0.2, 50)])[0]
+    monkeypatch.delenv("RIPPLE_GRID_SPIN_LIMIT")
+    assert info["status"] == R.RIPPLE_ERR_TIMEOUT
+    req = _euler(60, 60, 0.2, 30)
+    assert _run(ctx, [req])[0]["status"] == R.RIPPLE_OK
+    assert_parity(req["output"], _oracle_euler(req), 2e-5, LINF_F32)
     R.ripple_batch_configure(ctx, solo_rounds=False)
 
 
