@@ -296,14 +296,13 @@ typedef struct {
                                  is the CFL limit of its whole state), with no barrier between
                                  problems or global steps.  Uses TMA staging whatever `staging`
                                  says.  0 = one launch per global step (default). */
-    int solo_rounds;          /* 1 = while at most four problems are resident (none of them an eikonal
-                                 problem already iterating in batched rounds), each round runs the one
+    int solo_rounds;          /* n > 0 = while at most n problems are resident, each round runs the one
                                  with the least estimated time left alone on the single-problem kernels
                                  (Euler: one launch of the multi-step solver, up to about a millisecond
                                  of steps; eikonal: one persistent FIM solve), lowering the latency of
                                  requests served at low load; more resident problems run in batched
                                  rounds.  Results are bitwise those of batched rounds (the solvers
-                                 share the per-step arithmetic).  Default 1. */
+                                 share the per-step arithmetic).  0 = off; 0..4096, default 4. */
 } ripple_batch_config;
 
 typedef struct {
@@ -323,7 +322,7 @@ typedef struct {
 
 /* Set the batch configuration (defaults: SoA, 32x8, 16 steps per sync, graphs
  * on, F32, 4 FIM iterations per step, no cell budget, TMA staging, one launch
- * per global step, solo rounds on).  Only while no request is in flight. */
+ * per global step, solo rounds up to 4 resident problems).  Only while no request is in flight. */
 RIPPLE_API ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* cfg);
 
 /* Queue n requests; tickets_out[i] identifies request i.  Validates every

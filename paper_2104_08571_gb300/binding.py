@@ -412,12 +412,16 @@ def _info_dict(info):
                 cell_updates=info.cell_updates, t=info.t)
 
 
+SOLO_ROUNDS_DEFAULT = 4  # resident problems up to which solo rounds run (the C default)
+
+
 def ripple_batch_configure(ctx, layout=RIPPLE_SOA, tile_variant=0, steps_per_sync=16, use_graphs=True,
                            dtype=RIPPLE_F32, fim_iters_per_step=4, active_cells=0, staging=0, async_queue=False,
                            solo_rounds=True):
+    """solo_rounds: True (at most SOLO_ROUNDS_DEFAULT resident problems), False (off) or that bound."""
+    solo = SOLO_ROUNDS_DEFAULT if solo_rounds is True else int(solo_rounds)
     cfg = ripple_batch_config(int(layout), int(tile_variant), int(steps_per_sync), int(bool(use_graphs)), int(dtype),
-                              int(fim_iters_per_step), int(active_cells), int(staging), int(bool(async_queue)),
-                              int(bool(solo_rounds)))
+                              int(fim_iters_per_step), int(active_cells), int(staging), int(bool(async_queue)), solo)
     _check(load().ripple_batch_configure(ctx, ctypes.byref(cfg)), "ripple_batch_configure")
 
 
@@ -546,7 +550,7 @@ def ripple_batch_get_stats(ctx):
 def ripple_batch_autotune(ctx, sides, dtype=RIPPLE_F32):
     """Returns (chosen config dict, {(layout, variant): ms per global step})."""
     arr = (ctypes.c_int64 * len(sides))(*[int(x) for x in sides])
-    cfg = ripple_batch_config(RIPPLE_SOA, 0, 16, 1, int(dtype), 4, 0, 0, 0, 1)
+    cfg = ripple_batch_config(RIPPLE_SOA, 0, 16, 1, int(dtype), 4, 0, 0, 0, SOLO_ROUNDS_DEFAULT)
     ms = (ctypes.c_double * 12)()
     _check(load().ripple_batch_autotune(ctx, arr, len(sides), int(dtype), ctypes.byref(cfg), ms),
            "ripple_batch_autotune")
@@ -558,4 +562,4 @@ def ripple_batch_autotune(ctx, sides, dtype=RIPPLE_F32):
     return dict(layout=cfg.layout, tile_variant=cfg.tile_variant, steps_per_sync=cfg.steps_per_sync,
                 use_graphs=cfg.use_graphs, dtype=cfg.dtype, fim_iters_per_step=cfg.fim_iters_per_step,
                 active_cells=cfg.active_cells, staging=cfg.staging, async_queue=bool(cfg.async_queue),
-                solo_rounds=bool(cfg.solo_rounds)), timings
+                solo_rounds=int(cfg.solo_rounds)), timings

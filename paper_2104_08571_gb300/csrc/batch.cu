@@ -198,7 +198,7 @@ struct BatchRuntime {
     std::deque<Inst*> pending;                      // guarded by mu
     std::unordered_map<uint64_t, Ticket> tickets;   // guarded by mu
     uint64_t next_ticket = 1;                       // guarded by mu
-    ripple_batch_config cfg{RIPPLE_SOA, 0, 16, 1, RIPPLE_F32, 4, 0, 0, 0, 1};
+    ripple_batch_config cfg{RIPPLE_SOA, 0, 16, 1, RIPPLE_F32, 4, 0, 0, 0, 4};
     ripple_batch_stats stats{};                     // guarded by mu
     Clock::time_point epoch = Clock::now();
     // scheduler-thread state
@@ -873,8 +873,7 @@ static void collect_finished(BatchRuntime* rt)
     add_host_time(rt, &ripple_batch_stats::host_finish_s, t0);
 }
 
-// Solo rounds: while few problems are resident (at most kSoloMaxResident, and
-// none of them an eikonal problem already iterating in batched rounds), each
+// Solo rounds: while few problems are resident (at most cfg.solo_rounds), each
 // round gives the GPU to ONE of them, the one with the least estimated solo
 // time left (shortest remaining time first), on the single-problem kernels,
 // whose cost per problem is lower than the batched launches' (no work-queue
@@ -885,12 +884,13 @@ static void collect_finished(BatchRuntime* rt)
 //     bit for bit (buffer parity = step parity, the 3-slot wave-speed ring
 //     indexed by the step), so the problem continues in batched rounds when
 //     others join;
-//   * an eikonal problem that has not iterated yet is solved whole by the
-//     persistent FIM kernel (lists of active tiles), one launch.
+//   * an eikonal problem is solved whole by the persistent FIM kernel (lists of
+//     active tiles), one launch, from its initial state (iterations it ran in
+//     batched rounds are discarded: the solve's result does not depend on how
+//     its iterations were scheduled, so the bits are the same).
 // Requests arriving meanwhile are admitted after the round.  More resident
 // problems than that run in batched rounds, where one launch steps all of them.
 constexpr long long kSoloMaxSteps = 1024;
-constexpr size_t kSoloMaxResident = 4;
 
 // Solo GPU seconds an Euler step of `cells` cells takes (a fit of the
 // multi-step solver on GB300: a fixed barrier and dt cost, then the cells).
@@ -907,14 +907,12 @@ static double solo_remaining(const Inst* in)
 static ripple_status solo_round(BatchRuntime* rt, bool& handled)
 {
     handled = false;
-    if (!rt->cfg.solo_rounds || rt->cfg.async_queue || rt->resident.empty() ||
-        rt->resident.size() > kSoloMaxResident)
+    if (rt->cfg.solo_rounds <= 0 || rt->cfg.async_queue || rt->resident.empty() ||
+        rt->resident.size() > (size_t)rt->cfg.solo_rounds)
         return RIPPLE_OK;
     Inst* in = nullptr;
-    for (Inst* r : rt->resident) {
-        if (r->req.kind == RIPPLE_REQ_EIKONAL && r->stepped) return RIPPLE_OK;  // iterating in batched rounds
+    for (Inst* r : rt->resident)
         if (!in || solo_remaining(r) < solo_remaining(in)) in = r;
-    }
     const ripple_dtype dt = rt->cfg.dtype;
     cudaStream_t s = rt->compute;
     FieldCtl* ctl = &rt->slot_ctl[in->slot];
@@ -1511,6 +1509,7 @@ ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* 
     if (cfg->fim_iters_per_step < 1 || cfg->fim_iters_per_step > 64)
         return fail(RIPPLE_ERR_INVALID, "fim_iters_per_step must be 1..64");
     if (cfg->dtype != RIPPLE_F32 && cfg->dtype != RIPPLE_F64) return fail(RIPPLE_ERR_INVALID, "bad dtype");
+    if (cfg->solo_rounds < 0 || cfg->solo_rounds > kSlots) return fail(RIPPLE_ERR_INVALID, "solo_rounds must be 0..4096");
     BatchRuntime* rt = runtime_of(ctx, true);
     std::lock_guard<std::mutex> lk(rt->mu);
     if (rt->started) {

@@ -133,6 +133,29 @@ def test_solo_rounds_alone_and_in_mix(ctx):
     assert np.array_equal(batched[1]["output"], late["output"])
 
 
+def test_solo_rounds_over_a_batched_start_bitwise(ctx):
+    """More resident problems than the solo bound start in batched rounds; as
+    they finish, the rest continue in solo rounds (an eikonal problem already
+    iterating in batched rounds is solved again whole): every result is the
+    same bits as the problem alone in batched rounds."""
+    reqs = [_euler(40 + 7 * i, 36 + 5 * i, 0.1 + 0.02 * i, 15 + 9 * i) for i in range(5)]
+    reqs += [_eik(150, 120, 11), _eik(90, 200, 12)]
+    R.ripple_batch_configure(ctx, solo_rounds=False)
+    alone = []
+    for r in reqs:
+        a = _again(r)
+        assert _run(ctx, [a])[0]["status"] == R.RIPPLE_OK
+        alone.append(a["output"])
+    for bound in (2, 4):
+        R.ripple_batch_configure(ctx, solo_rounds=bound)
+        mix = [_again(r) for r in reqs]
+        infos = _run(ctx, mix)
+        assert all(i["status"] == R.RIPPLE_OK for i in infos)
+        for m, a in zip(mix, alone):
+            assert np.array_equal(m["output"], a)
+    R.ripple_batch_configure(ctx, solo_rounds=False)
+
+
 @pytest.mark.parametrize("layout", [R.RIPPLE_SOA, R.RIPPLE_AOS])
 @pytest.mark.parametrize("dtype", [R.RIPPLE_F32, R.RIPPLE_F64])
 def test_solo_solver_equals_batched_step_bitwise(ctx, layout, dtype):
