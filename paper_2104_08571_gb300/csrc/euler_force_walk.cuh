@@ -100,29 +100,36 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
     // padded cell rb into slot s.  Slot layout: SoA component m at [64 m, 64 m
     // + 64); AoS cell i at [NC i, NC i + NC).  A whole chunk moves as 16-byte
     // copies coalesced across the warp (SoA: 16 per component row; AoS: the
-    // chunk's contiguous bytes, or in 2D the lane's own two cells); a chunk
-    // past the last cell copies each lane's two cells with the index clamped
-    // to the ghost cell x = nx (never stored).
+    // chunk's contiguous bytes, or in 2D the lane's own two cells); the lane's
+    // pieces (slot offset, source offset from the chunk's first cell) are
+    // formed once here.  A chunk past the last cell copies each lane's two
+    // cells with the index clamped to the ghost cell x = nx (never stored).
+    constexpr int NPIECE = kOwnCells ? 64 : 16 * NC;  // 16-byte pieces of a full chunk
+    constexpr int PPL = (NPIECE + 31) / 32;           // per lane
+    int pdst[PPL];
+    long long psrc[PPL];
+#pragma unroll
+    for (int t = 0; t < PPL; ++t) {
+        const int i = kOwnCells ? 2 * lane + t : lane + 32 * t;
+        if constexpr (kOwnCells) {
+            pdst[t] = 4 * i;
+            psrc[t] = (long long)i * NC;
+        } else if constexpr (LAYOUT == LAYOUT_SOA) {
+            const int m = i >> 4, part = i & 15;
+            pdst[t] = 64 * m + 4 * part;
+            psrc[t] = (long long)m * cs + 4 * part;
+        } else {
+            pdst[t] = 4 * i;
+            psrc[t] = 4LL * i;
+        }
+        if (i >= NPIECE) pdst[t] = -1;
+    }
     auto stage = [&](float* s, long long rb, int x0) {
         if (x0 + 64 <= nx) {
-            if constexpr (kOwnCells) {
-                const long long c = rb + x0 + 2 * lane;
-                cp_async16(s + 8 * lane, in + c * NC);
-                cp_async16(s + 8 * lane + 4, in + (c + 1) * NC);
-            } else {
-                constexpr int NPIECE = 16 * NC;
+            const float* src = LAYOUT == LAYOUT_SOA ? in + rb + x0 : in + (rb + x0) * NC;
 #pragma unroll
-                for (int t = 0; t < (NPIECE + 31) / 32; ++t) {
-                    const int i = lane + 32 * t;
-                    if (i >= NPIECE) break;
-                    if constexpr (LAYOUT == LAYOUT_SOA) {
-                        const int m = i >> 4, part = i & 15;
-                        cp_async16(s + 64 * m + 4 * part, in + rb + x0 + 4 * part + m * cs);
-                    } else {
-                        cp_async16(s + 4 * i, in + (rb + x0) * NC + 4 * i);
-                    }
-                }
-            }
+            for (int t = 0; t < PPL; ++t)
+                if (t * 32 + 31 < NPIECE || pdst[t] >= 0) cp_async16(s + pdst[t], src + psrc[t]);
         } else {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -195,11 +202,15 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
         const f2 sw = wave_sum2<DIM>(qn, gamma, gm1, ivx, ok0, ok1);
         smax_local = fmaxf(smax_local, fmaxf(v0 ? sw.x : 0.f, v1 ? sw.y : 0.f));
         const bool b0 = v0 && !ok0, b1 = v1 && !ok1;
-        if (b0 || b1) {
-            bad = true;
-            record_bad(ctl, BAD_CELL, b0 ? x : x + 1, y, z);
+        // warp-uniform branches around the rare paths (a non-admissible cell, a
+        // ragged last chunk), so the common path has no divergent region
+        if (__any_sync(0xffffffffu, b0 || b1)) {
+            if (b0 || b1) {
+                bad = true;
+                record_bad(ctl, BAD_CELL, b0 ? x : x + 1, y, z);
+            }
         }
-        if (v0 && v1) {
+        if (__all_sync(0xffffffffu, v0 && v1) || (v0 && v1)) {
             if constexpr (LAYOUT == LAYOUT_SOA) {
 #pragma unroll
                 for (int m = 0; m < NC; ++m)
@@ -234,7 +245,16 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
         return ((long long)(DIM == 3 ? g.h + z : 0) * g.py + (g.h + y)) * g.px + g.lead + g.h;
     };
 
-    for (int w = blockIdx.x * kWalkWarps + warp; w < wg.walks; w += gridDim.x * kWalkWarps) {
+    // x sweep: the face xs - 1/2 that starts each walk, for 32 of the warp's
+    // walks at a time (lane j: the warp's walk jb + j), in the packed
+    // arithmetic of the walk before, which gives the same bits: the two walks
+    // agree on their common face exactly.  One evaluation per 32 walks instead
+    // of one per walk (a 256-cell row is a walk of only four chunks).
+    const int wstride = gridDim.x * kWalkWarps;
+    float bface[NC];
+    float bchk = 1.f;
+    int jw = 0;  // walks of this warp so far
+    for (int w = blockIdx.x * kWalkWarps + warp; w < wg.walks; w += wstride, ++jw) {
         float chk = 1.f;
         int wx, wy, wz = 0;  // first cell of the walk (reported with a non-admissible face state)
         ring_sync();  // the previous walk's reads of the ring come before its refill
@@ -257,24 +277,29 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
                 }
                 cp_async_commit();
             }
-            // face xs - 1/2, the left face of lane 0's first chunk (every lane the
-            // same), in the packed arithmetic of the walk before, which gives the
-            // same bits: the two walks agree on their common face exactly
-            float carry[NC];
-            {
+            // face xs - 1/2, the left face of lane 0's first chunk
+            if ((jw & 31) == 0) {
+                const int wl = w + lane * wstride;  // this lane's walk of the batch
+                const int rl = min(wl, wg.walks - 1) / wg.nseg, xl = (min(wl, wg.walks - 1) % wg.nseg) * wg.seg;
+                const long long rbl = row_base(rl % g.n[1], rl / g.n[1]);
                 float l[NC], r[NC];
-                load_cell(rb + xs - 1, l);
-                load_cell(rb + xs, r);
+                load_cell(rbl + xl - 1, l);
+                load_cell(rbl + xl, r);
                 f2 a[NC], b[NC], F[NC];
 #pragma unroll
                 for (int m = 0; m < NC; ++m) {
                     a[m] = splat<f2>(l[m]);
                     b[m] = splat<f2>(r[m]);
                 }
-                force<f2, DIM, 0>(a, b, gm1, hdt, hidt, F, chk);
+                bchk = 1.f;
+                force<f2, DIM, 0>(a, b, gm1, hdt, hidt, F, bchk);
 #pragma unroll
-                for (int m = 0; m < NC; ++m) carry[m] = F[m].x;
+                for (int m = 0; m < NC; ++m) bface[m] = F[m].x;
             }
+            float carry[NC];
+#pragma unroll
+            for (int m = 0; m < NC; ++m) carry[m] = __shfl_sync(0xffffffffu, bface[m], jw & 31);
+            chk = __shfl_sync(0xffffffffu, bchk, jw & 31);
             int slot = 0;  // slot of chunk k
 #pragma unroll 1
             for (int k = 0; k < nch; ++k) {
@@ -350,15 +375,17 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
                 force<f2, DIM, AXIS>(up, q0, gm1, hdt, hidt, Fl, chk);
             }
             int slot = 1;  // slot of row r
+            long long rb_next = base + (long long)(ys + NS - 2) * stride;  // row ys - 1 + (i + NS - 2)
+            long long c_row = base + (long long)ys * stride + x;            // the lane's first cell of row r
 #pragma unroll 1
-            for (int r = ys; r < ye; ++r) {
+            for (int r = ys; r < ye; ++r, rb_next += stride, c_row += stride) {
                 const int i = r - ys + 1;
                 {
                     // refill the slot of row i - 2 (read in the previous iteration) with row i + NS - 2
                     const int ir = i + NS - 2;
                     const int sr = slot >= 2 ? slot - 2 : slot + NS - 2;
                     ring_sync();
-                    if (ir < nrows) stage(ring + sr * SLOT, base + (long long)(ys - 1 + ir) * stride, x0);
+                    if (ir < nrows) stage(ring + sr * SLOT, rb_next, x0);
                     cp_async_commit();
                 }
                 cp_async_wait<NS - 3>();  // rows r and r + 1
@@ -375,7 +402,7 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
                 }
                 int y, z;
                 coords(r, y, z);
-                finish(qn, base + (long long)r * stride + x, x, y, z, v0, v1, col_near || r < g.h || r >= na - g.h);
+                finish(qn, c_row, x, y, z, v0, v1, col_near || r < g.h || r >= na - g.h);
                 slot = sn;
             }
         }
