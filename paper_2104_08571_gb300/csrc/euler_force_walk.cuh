@@ -198,9 +198,15 @@ __global__ void __launch_bounds__(kWalkWarps * 32, 2)
     };
     // updated pair of cells (x, x + 1) of row (y, z): checks, CFL maximum, store, ghost images
     auto finish = [&](const f2 (&qn)[NC], long long c, int x, int y, int z, bool v0, bool v1, bool near) {
-        bool ok0, ok1;
-        const f2 sw = wave_sum2<DIM>(qn, gamma, gm1, ivx, ok0, ok1);
-        smax_local = fmaxf(smax_local, fmaxf(v0 ? sw.x : 0.f, v1 ? sw.y : 0.f));
+        // the wave speeds (and the admissibility of the new state) in the last
+        // sweep of a step only: the step's CFL maximum is that of its result,
+        // and an intermediate state reaches the next sweep's faces, whose
+        // states are checked there
+        bool ok0 = true, ok1 = true;
+        if (prm.last) {
+            const f2 sw = wave_sum2<DIM>(qn, gamma, gm1, ivx, ok0, ok1);
+            smax_local = fmaxf(smax_local, fmaxf(v0 ? sw.x : 0.f, v1 ? sw.y : 0.f));
+        }
         const bool b0 = v0 && !ok0, b1 = v1 && !ok1;
         // warp-uniform branches around the rare paths (a non-admissible cell, a
         // ragged last chunk), so the common path has no divergent region
