@@ -342,12 +342,13 @@ def bench_gpu(args, rank, world, local):
     R.ripple_ctx_destroy(ctx)
     batched = None if args.skip_batched else bench_batched(R, torch, local, keep=par if "headline" in par else None)
     serve = None if args.skip_serve else bench_serving(R, torch, local, count=args.serve_requests)
+    solo = bench_solo(R, torch, local)
     layout = None if args.skip_layout else bench_layout(R, torch, local)
     force = bench_force_split(R, torch, local, par=par if "headline" in par else None)
     value = world * args.steps * ncell / (ms_max / 1e3)
     return dict(value=value, ms_per_step=ms_max / args.steps, clocks=clocks, ms_aos=ms_aos / args.steps,
                 e2e_value=e2e_value, e2e_s=e2e_s, e2e_solves=e2e_solves, ms2=ms2, eik=eik,
-                achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result, batched=batched,
+                achieved=achieved, hbm_peak=hbm_peak, peak_kind=peak_kind, extra=result, batched=batched, solo=solo,
                 serve=serve, layout=layout, force=force, parity_data=par)
 
 
@@ -397,6 +398,53 @@ def bench_eikonal(R, torch, local, keep=None, ctx=None, stream=None, steps=5):
         if own:
             R.ripple_ctx_destroy(ctx)
     return eik
+
+
+def bench_solo(R, torch, local, sides=(64, 256, 1024), nsteps=400):
+    """One 2D Euler request (sine density, FP32, periodic Rusanov, 400 steps)
+    served alone, per side: on the multi-step solo solver (solo rounds), on the
+    batched step launched once per step (solo rounds off; the results must be
+    the same bits), and through the single-field API's per-step launch loop
+    on a device-resident field."""
+    out = {}
+    ctx = R.ripple_ctx_create(local)
+    clk = ClockSampler(local).__enter__()
+    try:
+        for side in sides:
+            U = inputs.euler2d_sine(side).astype(np.float32)
+            row, res = {}, {}
+            for mode, solo in (("solo_rounds", True), ("batched_per_step", False)):
+                R.ripple_batch_configure(ctx, steps_per_sync=16, use_graphs=True, solo_rounds=solo)
+                for _ in range(3):  # warm-up twice, then timed
+                    req = R.euler_request(U, nsteps, [1.0 / side] * 2)
+                    s0 = R.ripple_batch_get_stats(ctx)
+                    info = R.ripple_wait(ctx, R.ripple_batch_submit(ctx, [req])[0], 600000)
+                    s1 = R.ripple_batch_get_stats(ctx)
+                assert info["status"] == R.RIPPLE_OK, "solo leg failed"
+                row[mode] = {"us_per_step_device": (s1["device_s"] - s0["device_s"]) * 1e6 / nsteps,
+                             "latency_ms": (info["finish_s"] - info["submit_s"]) * 1e3,
+                             "launches": s1["launches"] - s0["launches"]}
+                res[mode] = req["output"]
+            row["bitwise_equal"] = bool(np.array_equal(res["solo_rounds"], res["batched_per_step"]))
+            f = R.ripple_field_create(ctx, (side, side), 4, R.RIPPLE_SOA, 1, R.RIPPLE_F32)
+            try:
+                R.ripple_field_upload(f, U)
+                prm = R.make_fv_params([1.0 / side] * 2)
+                R.ripple_fv_step(f, prm, 10, stats=False)
+                R.ripple_ctx_sync(ctx)
+                t0 = time.perf_counter()
+                R.ripple_fv_step(f, prm, nsteps, stats=False)
+                R.ripple_ctx_sync(ctx)
+                row["field_api_per_step_launches"] = {"us_per_step": (time.perf_counter() - t0) * 1e6 / nsteps}
+            finally:
+                R.ripple_field_destroy(f)
+            out[str(side)] = row
+    finally:
+        clk.__exit__(None, None, None)
+        R.ripple_ctx_destroy(ctx)
+    out["steps"] = nsteps
+    out["clocks"] = clk.summary()
+    return out
 
 
 def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
@@ -928,6 +976,8 @@ def main():
                     help="time only the split FORCE step, FP32 SoA (profiling; not the headline line)")
     ap.add_argument("--force-n", type=int, default=8192)
     ap.add_argument("--force-dim", type=int, default=2, choices=[2, 3])
+    ap.add_argument("--solo-only", action="store_true",
+                    help="run only the single-request solo solver leg (profiling; not the headline line)")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the 512-instance batched workload (profiling; not the headline line)")
     ap.add_argument("--eikonal-only", action="store_true",
@@ -1012,6 +1062,17 @@ def main():
                               "n_gpus": world, "config": {"workload": "FIM eikonal 2048^2 and 192^3"},
                               "eikonal": ek}))
         return
+    if args.solo_only:
+        import torch
+        import paper_2104_08571_gb300 as R
+        torch.cuda.set_device(local)
+        so = bench_solo(R, torch, local)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": 1024 * 1024 / (so["1024"]["solo_rounds"]["us_per_step_device"] * 1e-6),
+                              "unit": METRIC, "n_gpus": world,
+                              "config": {"workload": "one 2D Euler request served alone, sides 64/256/1024"},
+                              "solo": so}))
+        return
     if args.batched_only:
         import torch
         import paper_2104_08571_gb300 as R
@@ -1077,6 +1138,7 @@ def main():
         "eikonal": r["eik"],
         "batched": r["batched"],
         "serve": r["serve"],
+        "solo": r["solo"],
         "layout_microbench": r["layout"],
         "force_split": r["force"],
     }
