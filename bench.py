@@ -65,14 +65,15 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, period_ms: int = 200):
         self.device = device
+        self.period_ms = period_ms
         self.proc = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -739,6 +740,10 @@ def _make_req(R, r, data, src):
 
 
 SERVE_RATES = (50, 100, 200, 500, 1000, 2000)
+# The served runs are timed in real time; an nvidia-smi query of the clocks
+# and throttle reasons stalls the runtime's CUDA calls while it runs, so the
+# serving legs sample every 2 s (the kernel legs every 200 ms)
+SERVE_CLOCK_PERIOD_MS = 2000
 
 
 def bench_serving(R, torch, local, rates=SERVE_RATES, count=400):
@@ -755,6 +760,8 @@ def bench_serving(R, torch, local, rates=SERVE_RATES, count=400):
               "policy": f"least remaining work first, {ACTIVE_CELLS} active cells per step, 4 FIM iterations per step",
               "euler_cell_updates": int(work_euler), "eikonal_cells": int(cells_eik), "rates": {}}
     # sequential baseline: service time of every request alone, through fields
+    # (under the clock sampler, as the served runs)
+    clk_seq = ClockSampler(local, SERVE_CLOCK_PERIOD_MS).__enter__()
     ctx = R.ripple_ctx_create(local)
     R.use_torch_allocator(ctx, local)  # cached allocations: no cudaMalloc per request
     service = []
@@ -779,6 +786,8 @@ def bench_serving(R, torch, local, rates=SERVE_RATES, count=400):
             service.append(time.perf_counter() - t0)
     finally:
         R.ripple_ctx_destroy(ctx)
+        clk_seq.__exit__(None, None, None)
+    result["baseline_clocks"] = clk_seq.summary()
     ctx = R.ripple_ctx_create(local, 40 << 30)
     try:
         for mode in ("per_step_launches", "dependency_driven"):
@@ -789,7 +798,7 @@ def bench_serving(R, torch, local, rates=SERVE_RATES, count=400):
                 R.ripple_wait(ctx, t, 600000)
             dest = result["rates"] if mode == "per_step_launches" else result.setdefault("rates_dependency_driven", {})
             for rate in rates:
-                with ClockSampler(local) as clk_s:
+                with ClockSampler(local, SERVE_CLOCK_PERIOD_MS) as clk_s:
                     arrivals = [r["t"] for r in inputs.serve_stream(rate, count, seed=1)]
                     reqs = [_make_req(R, r, d, s) for (r, d, s) in prepared]
                     tickets = []

@@ -296,8 +296,8 @@ typedef struct {
                                  is the CFL limit of its whole state), with no barrier between
                                  problems or global steps.  Uses TMA staging whatever `staging`
                                  says.  0 = one launch per global step (default). */
-    int solo_rounds;          /* n > 0 = while at most n problems are resident, each round runs the one
-                                 with the least estimated time left alone on the single-problem kernels
+    int solo_rounds;          /* n > 0 = while at most n problems are resident, each round runs the
+                                 oldest of them alone on the single-problem kernels
                                  (Euler: one launch of the multi-step solver, up to about a millisecond
                                  of steps; eikonal: one persistent FIM solve), lowering the latency of
                                  requests served at low load; more resident problems run in batched

@@ -357,6 +357,10 @@ static void drop_event(BatchRuntime* rt, Inst* in)
 }
 
 static bool group_done(const Inst* in) { return !in->gev || cudaEventQuery(in->gev->ev) == cudaSuccess; }
+static void wait_group(const Inst* in)
+{
+    if (in->gev) cudaEventSynchronize(in->gev->ev);
+}
 
 // Free everything an instance holds (stream-ordered after its last use).
 static void release(BatchRuntime* rt, Inst* in)
@@ -597,6 +601,10 @@ static void fill_fim_desc(BatchRuntime* rt, Inst* in, void* h_fim, int idx)
     f->status = &rt->slot_status[in->slot];
     f->counters = &rt->slot_counters[in->slot * 3];
 }
+
+constexpr int kInitDescriptors = 1024;  // Euler and eikonal descriptors allocated at start
+constexpr int kInitTiles = 1 << 18;     // tile-table entries allocated at start (1 MB)
+constexpr int kInitEvents = 32;         // pooled group events created at start
 
 static ripple_status grow(BatchRuntime* rt, int ne, int nf, int nt)
 {
@@ -874,10 +882,10 @@ static void collect_finished(BatchRuntime* rt)
 }
 
 // Solo rounds: while few problems are resident (at most cfg.solo_rounds), each
-// round gives the GPU to ONE of them, the one with the least estimated solo
-// time left (shortest remaining time first), on the single-problem kernels,
-// whose cost per problem is lower than the batched launches' (no work-queue
-// indirection, no per-step launch, no lockstep with a larger problem):
+// round gives the GPU to ONE of them, the oldest (arrival order), on the
+// single-problem kernels, whose cost per problem is lower than the batched
+// launches' (no work-queue indirection, no per-step launch, no lockstep with a
+// larger problem):
 //   * an Euler problem takes up to kSoloMaxSteps steps (about a millisecond of
 //     work at most) in one launch of the multi-step solver (euler_solo2d.cuh)
 //     on its own buffers and control block; its steps are the batched step's
@@ -896,23 +904,18 @@ constexpr long long kSoloMaxSteps = 1024;
 // multi-step solver on GB300: a fixed barrier and dt cost, then the cells).
 static double solo_step_seconds(double cells) { return 3.3e-6 + 12e-12 * cells; }
 
-// Estimated solo GPU seconds a resident problem still needs.
-static double solo_remaining(const Inst* in)
-{
-    const double cells = (double)in->req.dims[0] * (double)in->req.dims[1];
-    if (in->req.kind == RIPPLE_REQ_EULER) return (double)(in->req.nsteps - in->steps_done) * solo_step_seconds(cells);
-    return 2e-4 + 0.7e-9 * cells;  // one persistent FIM solve
-}
-
 static ripple_status solo_round(BatchRuntime* rt, bool& handled)
 {
     handled = false;
     if (rt->cfg.solo_rounds <= 0 || rt->cfg.async_queue || rt->resident.empty() ||
         rt->resident.size() > (size_t)rt->cfg.solo_rounds)
         return RIPPLE_OK;
+    // the oldest resident problem (arrival order: shortest-remaining-time-first
+    // gave a lower p50 but a higher p99, its largest requests being preempted
+    // by every smaller arrival)
     Inst* in = nullptr;
     for (Inst* r : rt->resident)
-        if (!in || solo_remaining(r) < solo_remaining(in)) in = r;
+        if (!in || r->t_submit < in->t_submit) in = r;
     const ripple_dtype dt = rt->cfg.dtype;
     cudaStream_t s = rt->compute;
     FieldCtl* ctl = &rt->slot_ctl[in->slot];
@@ -1189,7 +1192,7 @@ static void scheduler(BatchRuntime* rt)
             joined = std::min(joined, in->t_start);
         }
         if (fresh && !rt->uploading.empty() && rt->now() - joined < 1.0) {
-            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            wait_group(rt->uploading.front());
             continue;
         }
         if (!rt->resident.empty()) {
@@ -1245,8 +1248,13 @@ static void scheduler(BatchRuntime* rt)
                 add_host_time(rt, &ripple_batch_stats::host_finish_s, t0);
             }
         }
-        if (rt->resident.empty() && (!rt->uploading.empty() || !rt->downloading.empty()))
-            std::this_thread::sleep_for(std::chrono::microseconds(50));
+        // nothing to compute: block until the oldest copy group completes (a
+        // blocking wait wakes as the copies land; a sleep-and-poll loop's
+        // wake-ups depend on the host's load)
+        if (rt->resident.empty()) {
+            if (!rt->downloading.empty()) wait_group(rt->downloading.front());
+            else if (!rt->uploading.empty()) wait_group(rt->uploading.front());
+        }
     }
 }
 
@@ -1300,6 +1308,17 @@ static ripple_status rt_start(BatchRuntime* rt)
         std::max(1, batch_occupancy(rt->cfg.dtype, layout, rt->cfg.tile_variant, kBatchStagingTma)) * rt->ctx->sm_count;
     rt->gstep_e = 0;
     rt->gstep_f = 0;
+    // descriptor tables and group events sized up front: growing them while
+    // serving (cudaFree, cudaMallocHost) stalls the scheduler for milliseconds
+    {
+        const ripple_status st = grow(rt, kInitDescriptors, kInitDescriptors, kInitTiles);
+        if (st != RIPPLE_OK) return st;
+        for (int i = 0; i < kInitEvents; ++i) {
+            cudaEvent_t e = nullptr;
+            RIPPLE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            rt->ev_pool.push_back(e);
+        }
+    }
     rt->started = true;
     rt->th = std::thread(scheduler, rt);
     return RIPPLE_OK;
