@@ -155,6 +155,73 @@ using Clock = std::chrono::steady_clock;
 constexpr int kSlots = 4096;  // concurrent problems (admitted, resident or completing)
 constexpr int kMaxRoundSteps = 4096;  // steps of one dependency-driven round
 
+// A page-locked host arena for request data.  The submitting thread copies a
+// pageable request's input into it and the thread that retrieves the ticket
+// copies the result out of it, so the scheduler thread's copies to and from
+// the device are asynchronous (a copy from or to pageable memory holds the
+// calling thread until it is done, and the scheduler thread is the one that
+// keeps the GPU busy).  First fit over free blocks, coalesced on release.
+struct PinnedArena {
+    std::mutex mu;
+    char* base = nullptr;
+    size_t size = 0;
+    bool tried = false;
+    std::map<size_t, size_t> free_blocks;  // offset -> bytes
+
+    char* alloc(size_t bytes)
+    {
+        bytes = (bytes + 255) / 256 * 256;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!tried) {
+            tried = true;
+            if (cudaMallocHost(reinterpret_cast<void**>(&base), kArenaBytes) == cudaSuccess) {
+                size = kArenaBytes;
+                free_blocks[0] = size;
+            } else {
+                base = nullptr;
+                cudaGetLastError();
+            }
+        }
+        for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
+            if (it->second < bytes) continue;
+            const size_t off = it->first, rest = it->second - bytes;
+            free_blocks.erase(it);
+            if (rest) free_blocks[off + bytes] = rest;
+            return base + off;
+        }
+        return nullptr;
+    }
+    void release(char* p, size_t bytes)
+    {
+        if (!p) return;
+        bytes = (bytes + 255) / 256 * 256;
+        std::lock_guard<std::mutex> lk(mu);
+        size_t off = (size_t)(p - base);
+        auto next = free_blocks.lower_bound(off);
+        if (next != free_blocks.end() && next->first == off + bytes) {
+            bytes += next->second;
+            free_blocks.erase(next);
+        }
+        auto it = free_blocks.lower_bound(off);
+        if (it != free_blocks.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == off) {
+                prev->second += bytes;
+                return;
+            }
+        }
+        free_blocks[off] = bytes;
+    }
+    void destroy()
+    {
+        if (base) cudaFreeHost(base);
+        base = nullptr;
+        size = 0;
+        free_blocks.clear();
+    }
+    static constexpr size_t kArenaBytes = size_t(512) << 20;
+};
+
 struct Inst {
     uint64_t ticket = 0;
     ripple_request req{};
@@ -173,6 +240,9 @@ struct Inst {
     CUtensorMap map[2];         // Euler: TMA maps of buf[0], buf[1] (cached per tile variant and layout)
     int map_key = -1;
     struct GroupEv* gev = nullptr;  // completion of the instance's admission or download group
+    char* h_in = nullptr;           // page-locked copy of the input (arena), or null: copied from req.input
+    char* h_out = nullptr;          // page-locked stage of the result (arena), or null: copied to req.output
+    size_t dense = 0;               // bytes of the input and of the result
     ripple_status result = RIPPLE_OK;
     double t_submit = 0, t_admit = 0, t_start = 0, t_finish = 0;
 };
@@ -187,6 +257,9 @@ struct GroupEv {
 struct Ticket {
     bool done = false;
     ripple_ticket_info info{};
+    char* stage = nullptr;  // result in the arena, copied to `out` by the thread that retrieves the ticket
+    void* out = nullptr;
+    size_t bytes = 0;
 };
 
 struct BatchRuntime {
@@ -214,6 +287,7 @@ struct BatchRuntime {
     // array, its device copy (both kSlots long) and the event after the copy
     unsigned* d_solo_bar = nullptr;  // arrival counter of the multi-step solo launches' grid barrier
     int solo_occ[2] = {0, 0};        // resident CTAs per SM of the solo kernel (FP32, FP64)
+    PinnedArena arena;  // request data staged in page-locked memory
     GroupItem* h_items = nullptr;
     GroupItem* d_items = nullptr;
     cudaEvent_t ev_items = nullptr;
@@ -249,6 +323,7 @@ struct BatchRuntime {
     int* h_cum = nullptr;           // pinned, [kMaxRoundSteps + 1]
     std::vector<Inst*> euler_order;  // Euler instances in table order (set by rebuild_tables)
     bool dirty = true;
+    bool small_only = false;  // batched rounds over the small Euler problems only (solo_round decides)
     bool has_e = false, has_f = false;  // resident kinds (set by rebuild_tables)
     long long gstep_e = 0;  // Euler steps issued (== device counter once they completed)
     long long gstep_f = 0;  // FIM iterations issued
@@ -372,6 +447,9 @@ static void release(BatchRuntime* rt, Inst* in)
     in->buf[0] = in->buf[1] = in->sbuf = in->scratch = nullptr;
     if (in->slot >= 0) rt->free_slots.push_back(in->slot);
     drop_event(rt, in);
+    rt->arena.release(in->h_in, in->dense);
+    rt->arena.release(in->h_out, in->dense);
+    in->h_in = in->h_out = nullptr;
 }
 
 template <typename T>
@@ -431,6 +509,12 @@ static ripple_status admit(BatchRuntime* rt, Inst* in)
                           (in->scratch_bytes + 255) / 256 * 256;
     }
     if (dense > in->buf_bytes) return fail(RIPPLE_ERR_INTERNAL, "staging buffer too small");
+    if (in->dense != dense) {  // the precision changed after submission: copy directly
+        rt->arena.release(in->h_in, in->dense);
+        rt->arena.release(in->h_out, in->dense);
+        in->h_in = in->h_out = nullptr;
+        in->dense = dense;
+    }
     if (fault_injected("admit")) return fail(RIPPLE_ERR_OOM, "admission failed (injected: RIPPLE_FAULT=admit)");
     if (rt->free_slots.empty()) return RIPPLE_ERR_BUDGET;
     if (rt->ctx->budget && in->total_bytes > rt->ctx->budget)
@@ -454,7 +538,8 @@ static ripple_status admit(BatchRuntime* rt, Inst* in)
     if (fault_injected("upload")) return fail(RIPPLE_ERR_CUDA, "input upload failed (injected: RIPPLE_FAULT=upload)");
     cudaStream_t s = rt->copy;
     // the second buffer is the dense staging area of the upload
-    RIPPLE_CUDA(cudaMemcpyAsync(in->buf[1], r.input, dense, cudaMemcpyHostToDevice, s));
+    RIPPLE_CUDA(cudaMemcpyAsync(in->buf[1], in->h_in ? static_cast<const void*>(in->h_in) : r.input, dense,
+                                cudaMemcpyHostToDevice, s));
     if (r.kind == RIPPLE_REQ_EULER) {
         // TMA maps of the batched step, encoded while the copies run (the tile
         // shape and layout cannot change while a request is in flight)
@@ -571,7 +656,8 @@ static ripple_status start_downloads(BatchRuntime* rt, const std::vector<Inst*>&
         const Inst* in = group[i];
         const ripple_request& r = in->req;
         const size_t dense = (size_t)(r.dims[0] * r.dims[1]) * elem_size(dt) * (r.kind == RIPPLE_REQ_EULER ? 4 : 1);
-        RIPPLE_CUDA(cudaMemcpyAsync(r.output, rt->h_items[i].other, dense, cudaMemcpyDeviceToHost, s));
+        RIPPLE_CUDA(cudaMemcpyAsync(in->h_out ? static_cast<void*>(in->h_out) : r.output, rt->h_items[i].other, dense,
+                                    cudaMemcpyDeviceToHost, s));
     }
     const int ns = hi - lo + 1;
     RIPPLE_CUDA(cudaMemcpyAsync(&rt->out_ctl[lo], &rt->slot_ctl[lo], ns * sizeof(FieldCtl), cudaMemcpyDeviceToHost, s));
@@ -638,6 +724,7 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
     int ne = 0, nf = 0, nt = 0;
     for (Inst* in : rt->resident) {
         if (in->req.kind == RIPPLE_REQ_EULER && !in->active) continue;
+        if (in->req.kind != RIPPLE_REQ_EULER && rt->small_only) continue;
         if (in->req.kind == RIPPLE_REQ_EULER) ++ne;
         else ++nf;
         nt += in->ntiles;
@@ -662,7 +749,7 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
     }
     rt->euler_order = order;
     for (Inst* in : rt->resident)
-        if (in->req.kind != RIPPLE_REQ_EULER) order.push_back(in);
+        if (in->req.kind != RIPPLE_REQ_EULER && !rt->small_only) order.push_back(in);
     int nt_e = 0;
     for (Inst* in : order) {
         if (in->req.kind == RIPPLE_REQ_EULER) {
@@ -899,6 +986,10 @@ static void collect_finished(BatchRuntime* rt)
 // Requests arriving meanwhile are admitted after the round.  More resident
 // problems than that run in batched rounds, where one launch steps all of them.
 constexpr long long kSoloMaxSteps = 1024;
+// Euler problems of at least this many cells (512^2) run alone when they are
+// the oldest: alone a 1024^2 step takes 15 us, in a batched round with others
+// 33 us; smaller ones gain from sharing a batched launch
+constexpr long long kSoloBigCells = 1LL << 18;
 
 // Solo GPU seconds an Euler step of `cells` cells takes (a fit of the
 // multi-step solver on GB300: a fixed barrier and dt cost, then the cells).
@@ -907,15 +998,26 @@ static double solo_step_seconds(double cells) { return 3.3e-6 + 12e-12 * cells; 
 static ripple_status solo_round(BatchRuntime* rt, bool& handled)
 {
     handled = false;
-    if (rt->cfg.solo_rounds <= 0 || rt->cfg.async_queue || rt->resident.empty() ||
-        rt->resident.size() > (size_t)rt->cfg.solo_rounds)
-        return RIPPLE_OK;
-    // the oldest resident problem (arrival order: shortest-remaining-time-first
-    // gave a lower p50 but a higher p99, its largest requests being preempted
-    // by every smaller arrival)
+    bool small_only = false;
     Inst* in = nullptr;
-    for (Inst* r : rt->resident)
-        if (!in || r->t_submit < in->t_submit) in = r;
+    if (rt->cfg.solo_rounds > 0 && !rt->cfg.async_queue && !rt->resident.empty()) {
+        // the oldest resident problem (arrival order: shortest-remaining-time-
+        // first gave a lower p50 but a higher p99, its largest requests being
+        // preempted by every smaller arrival)
+        for (Inst* r : rt->resident)
+            if (!in || r->t_submit < in->t_submit) in = r;
+        // it runs alone while few problems are resident, and always when it is
+        // an eikonal problem or a large Euler one (large ones advance faster
+        // alone than in lockstep with others); otherwise the small Euler
+        // problems share batched rounds
+        const bool large = in->req.kind == RIPPLE_REQ_EIKONAL || in->req.dims[0] * in->req.dims[1] >= kSoloBigCells;
+        small_only = rt->resident.size() > (size_t)rt->cfg.solo_rounds && !large;
+    }
+    if (small_only != rt->small_only) {
+        rt->small_only = small_only;
+        rt->dirty = true;
+    }
+    if (!in || small_only) return RIPPLE_OK;
     const ripple_dtype dt = rt->cfg.dtype;
     cudaStream_t s = rt->compute;
     FieldCtl* ctl = &rt->slot_ctl[in->slot];
@@ -1042,7 +1144,8 @@ static ripple_status compute_round(BatchRuntime* rt)
         int64_t cells = 0;
         for (Inst* in : eu) {
             const int64_t c = in->req.dims[0] * in->req.dims[1];
-            const bool take = budget <= 0 || cells == 0 || cells + c <= budget;
+            const bool take = !(rt->small_only && c >= kSoloBigCells) &&
+                              (budget <= 0 || cells == 0 || cells + c <= budget);
             if (take) cells += c;
             if (take != in->active) {
                 in->active = take;
@@ -1171,6 +1274,13 @@ static void scheduler(BatchRuntime* rt)
             Inst* in = rt->uploading[i];
             if (group_done(in)) {
                 drop_event(rt, in);
+                // the host mirror of the slot's status word may still hold the
+                // previous occupant's (a round that iterates no eikonal problem
+                // does not refresh it); the device word was cleared by the
+                // admission group, which has completed
+                rt->h_status[in->slot] = 0ull;
+                rt->arena.release(in->h_in, in->dense);  // the upload has read it
+                in->h_in = nullptr;
                 in->start_step = in->req.kind == RIPPLE_REQ_EULER ? rt->gstep_e : rt->gstep_f;
                 in->steps_done = 0;
                 in->active = false;  // the next round's active-set pass decides
@@ -1238,6 +1348,13 @@ static void scheduler(BatchRuntime* rt)
                             st = RIPPLE_ERR_TIMEOUT;
                         }
                         fill_ticket(rt, in, st, t);
+                        if (in->h_out) {  // the result waits in the arena for the ticket's retrieval
+                            Ticket& tk = rt->tickets[in->ticket];
+                            tk.stage = in->h_out;
+                            tk.out = in->req.output;
+                            tk.bytes = in->dense;
+                            in->h_out = nullptr;
+                        }
                     }
                 }
                 rt->cv_done.notify_all();
@@ -1503,6 +1620,7 @@ void batch_runtime_destroy(ripple_ctx ctx)
         rt->ev_pool.clear();
         cudaFreeHost(rt->h_items);
         cudaFree(rt->d_solo_bar);
+        rt->arena.destroy();
         cudaFree(rt->d_items);
         if (rt->pool) cudaMemPoolDestroy(rt->pool);
         cudaEventDestroy(rt->ev_r0);
@@ -1582,16 +1700,50 @@ ripple_status ripple_batch_submit(ripple_ctx ctx, const ripple_request* reqs, in
         }
     }
     BatchRuntime* rt = runtime_of(ctx, true);
+    const double t_in = rt->now();  // latency counts from here, the staging copies included
+    ripple_dtype dt;
     {
         std::lock_guard<std::mutex> lk(rt->mu);
         if (!rt->started) {
             ripple_status st = rt_start(rt);
             if (st != RIPPLE_OK) return st;
         }
-        const double now = rt->now();
+        dt = rt->cfg.dtype;
+    }
+    // pageable request data goes through the arena (on this thread); page-locked
+    // or registered arrays, or data the arena has no room for, are copied directly
+    std::vector<char*> st_in(n, nullptr), st_out(n, nullptr);
+    std::vector<size_t> st_bytes(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const ripple_request& r = reqs[i];
+        const size_t dense =
+            (size_t)(r.dims[0] * r.dims[1]) * elem_size(dt) * (r.kind == RIPPLE_REQ_EULER ? 4 : 1);
+        st_bytes[i] = dense;
+        cudaPointerAttributes ai{}, ao{};
+        const bool pin_in = cudaPointerGetAttributes(&ai, r.input) == cudaSuccess && ai.type == cudaMemoryTypeHost;
+        const bool pin_out = cudaPointerGetAttributes(&ao, r.output) == cudaSuccess && ao.type == cudaMemoryTypeHost;
+        cudaGetLastError();
+        if (pin_in && pin_out) continue;
+        char* a = pin_in ? nullptr : rt->arena.alloc(dense);
+        char* b = pin_out ? nullptr : rt->arena.alloc(dense);
+        if ((!pin_in && !a) || (!pin_out && !b)) {
+            rt->arena.release(a, dense);
+            rt->arena.release(b, dense);
+            continue;
+        }
+        if (a) std::memcpy(a, r.input, dense);
+        st_in[i] = a;
+        st_out[i] = b;
+    }
+    {
+        std::lock_guard<std::mutex> lk(rt->mu);
+        const double now = t_in;
         for (int i = 0; i < n; ++i) {
             Inst* in = new Inst();
             in->req = reqs[i];
+            in->h_in = st_in[i];
+            in->h_out = st_out[i];
+            in->dense = st_bytes[i];
             if (reqs[i].kind == RIPPLE_REQ_EIKONAL) {
                 in->src.assign(reqs[i].sources, reqs[i].sources + 2 * reqs[i].nsrc);
                 in->req.sources = nullptr;
@@ -1608,17 +1760,29 @@ ripple_status ripple_batch_submit(ripple_ctx ctx, const ripple_request* reqs, in
     return RIPPLE_OK;
 }
 
+// A retrieved ticket's result, if it waits in the arena: into the caller's
+// array (on the retrieving thread), and the arena block back.
+static void deliver(BatchRuntime* rt, const Ticket& tk)
+{
+    if (!tk.stage) return;
+    std::memcpy(tk.out, tk.stage, tk.bytes);
+    rt->arena.release(tk.stage, tk.bytes);
+}
+
 ripple_status ripple_poll(ripple_ctx ctx, uint64_t ticket, ripple_ticket_info* info)
 {
     if (!ctx) return fail(RIPPLE_ERR_INVALID, "ctx is NULL");
     BatchRuntime* rt = runtime_of(ctx, false);
     if (!rt) return fail(RIPPLE_ERR_INVALID, "unknown ticket");
-    std::lock_guard<std::mutex> lk(rt->mu);
+    std::unique_lock<std::mutex> lk(rt->mu);
     auto it = rt->tickets.find(ticket);
     if (it == rt->tickets.end()) return fail(RIPPLE_ERR_INVALID, "unknown ticket");
     if (!it->second.done) return RIPPLE_ERR_NOT_READY;
     if (info) *info = it->second.info;
+    const Ticket tk = it->second;
     rt->tickets.erase(it);
+    lk.unlock();
+    deliver(rt, tk);
     return RIPPLE_OK;
 }
 
@@ -1640,7 +1804,10 @@ ripple_status ripple_wait(ripple_ctx ctx, uint64_t ticket, int64_t timeout_ms, r
         }
     }
     if (info) *info = rt->tickets[ticket].info;
+    const Ticket tk = rt->tickets[ticket];
     rt->tickets.erase(ticket);
+    lk.unlock();
+    deliver(rt, tk);
     return RIPPLE_OK;
 }
 

@@ -199,6 +199,30 @@ def test_solo_barrier_timeout_reports(ctx, monkeypatch):
     R.ripple_batch_configure(ctx, solo_rounds=False)
 
 
+def test_pageable_and_page_locked_requests(ctx):
+    """Pageable request arrays go through the runtime's page-locked arena (the
+    result is copied out when the ticket is retrieved, by wait or by poll);
+    page-locked arrays are copied directly: the same bits either way."""
+    import torch
+    R.ripple_batch_configure(ctx, solo_rounds=False)
+    base = _euler(120, 90, 0.2, 25)
+    pin_in = torch.from_numpy(base["input"]).pin_memory().numpy()
+    pin_out = torch.empty(base["input"].shape, dtype=torch.float32, pin_memory=True).numpy()
+    pinned = R.euler_request(pin_in, 25, base["dx"], out=pin_out)
+    polled = _again(base)
+    infos = _run(ctx, [base, pinned])
+    assert all(i["status"] == R.RIPPLE_OK for i in infos)
+    assert np.array_equal(base["output"], pinned["output"])
+    t = R.ripple_batch_submit(ctx, [polled])[0]
+    deadline = time.time() + 60
+    info = None
+    while info is None and time.time() < deadline:
+        info = R.ripple_poll(ctx, t)
+        time.sleep(0.001)
+    assert info is not None and info["status"] == R.RIPPLE_OK
+    assert np.array_equal(polled["output"], base["output"])
+
+
 def test_batch_matches_single_field_sweep(ctx):
     req = _euler(96, 80, 0.2, 30)
     _run(ctx, [req])
