@@ -259,8 +259,9 @@ typedef struct {
     int64_t dims[2];          /* 2D grid (nx, ny) */
     const void* input;        /* HOST: Euler conserved state (4 components, SoA, dtype of the batch) or
                                  eikonal slowness (1 component); read until the request is admitted */
-    void* output;             /* HOST: final Euler state / eikonal travel times, same shape; written
-                                 before the ticket completes */
+    void* output;             /* HOST: final Euler state / eikonal travel times, same shape; holds the
+                                 result when ripple_poll / ripple_wait retire the ticket (a pageable
+                                 array is written by that call, from the runtime's page-locked stage) */
     ripple_fv_params fv;      /* Euler: gamma, cfl, dx, bc; scheme must be RIPPLE_RUSANOV1 */
     int64_t nsteps;           /* Euler: steps to run (>= 1) */
     ripple_eik_params eik;    /* eikonal: h, tol, max_iters */
@@ -326,17 +327,24 @@ typedef struct {
 RIPPLE_API ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* cfg);
 
 /* Queue n requests; tickets_out[i] identifies request i.  Validates every
- * request first (RIPPLE_ERR_INVALID queues nothing).  Never blocks on the GPU. */
+ * request first (RIPPLE_ERR_INVALID queues nothing).  Never blocks on the GPU.
+ * Pageable input arrays are copied here into the runtime's page-locked arena
+ * (512 MB per context) when they fit and the call carries at most 64 MB, so
+ * the runtime's own copies are asynchronous; page-locked or registered
+ * arrays, and the rest, are read by the runtime directly (an input is then
+ * read until its request is admitted). */
 RIPPLE_API ripple_status ripple_batch_submit(ripple_ctx ctx, const ripple_request* reqs, int n,
                                              uint64_t* tickets_out);
 
 /* RIPPLE_OK and *info filled (ticket retired) once the request finished,
  * RIPPLE_ERR_NOT_READY while it runs, RIPPLE_ERR_INVALID for an unknown ticket.
- * The request's own outcome is info->status. */
+ * The request's own outcome is info->status.  A result staged in the arena is
+ * copied into the request's output array by this call. */
 RIPPLE_API ripple_status ripple_poll(ripple_ctx ctx, uint64_t ticket, ripple_ticket_info* info);
 
 /* Block until the request finished (RIPPLE_OK, *info filled, ticket retired) or
- * timeout_ms passed (RIPPLE_ERR_TIMEOUT; timeout_ms < 0 waits forever). */
+ * timeout_ms passed (RIPPLE_ERR_TIMEOUT; timeout_ms < 0 waits forever).  A
+ * result staged in the arena is copied into the output array by this call. */
 RIPPLE_API ripple_status ripple_wait(ripple_ctx ctx, uint64_t ticket, int64_t timeout_ms, ripple_ticket_info* info);
 
 RIPPLE_API ripple_status ripple_batch_get_stats(ripple_ctx ctx, ripple_batch_stats* out);

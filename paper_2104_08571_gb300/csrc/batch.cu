@@ -1675,6 +1675,8 @@ ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* 
     return RIPPLE_OK;
 }
 
+constexpr size_t kStageCallBytes = size_t(64) << 20;
+
 ripple_status ripple_batch_submit(ripple_ctx ctx, const ripple_request* reqs, int n, uint64_t* tickets)
 {
     if (!ctx || (!reqs && n > 0) || (!tickets && n > 0) || n < 0) return fail(RIPPLE_ERR_INVALID, "bad arguments");
@@ -1711,14 +1713,20 @@ ripple_status ripple_batch_submit(ripple_ctx ctx, const ripple_request* reqs, in
         dt = rt->cfg.dtype;
     }
     // pageable request data goes through the arena (on this thread); page-locked
-    // or registered arrays, or data the arena has no room for, are copied directly
+    // or registered arrays, data the arena has no room for, and bulk submissions
+    // (more than kStageCallBytes: they are admitted together, and a one-thread
+    // host copy is slower than the direct pageable copy) are copied directly
     std::vector<char*> st_in(n, nullptr), st_out(n, nullptr);
     std::vector<size_t> st_bytes(n, 0);
+    size_t call_bytes = 0;
     for (int i = 0; i < n; ++i) {
         const ripple_request& r = reqs[i];
-        const size_t dense =
-            (size_t)(r.dims[0] * r.dims[1]) * elem_size(dt) * (r.kind == RIPPLE_REQ_EULER ? 4 : 1);
-        st_bytes[i] = dense;
+        st_bytes[i] = (size_t)(r.dims[0] * r.dims[1]) * elem_size(dt) * (r.kind == RIPPLE_REQ_EULER ? 4 : 1);
+        call_bytes += st_bytes[i];
+    }
+    for (int i = 0; i < n && call_bytes <= kStageCallBytes; ++i) {
+        const ripple_request& r = reqs[i];
+        const size_t dense = st_bytes[i];
         cudaPointerAttributes ai{}, ao{};
         const bool pin_in = cudaPointerGetAttributes(&ai, r.input) == cudaSuccess && ai.type == cudaMemoryTypeHost;
         const bool pin_out = cudaPointerGetAttributes(&ao, r.output) == cudaSuccess && ao.type == cudaMemoryTypeHost;
