@@ -10,7 +10,7 @@ import pytest
 import inputs
 import oracle
 import paper_2104_08571_gb300 as R
-from tests.gpu_util import LINF_EIK, LINF_F32, LINF_F64, assert_parity, rel_l1
+from tests.gpu_util import LINF_EIK, LINF_F32, LINF_F64, assert_parity, max_rel, rel_l1
 
 pytestmark = pytest.mark.gpu
 
@@ -234,6 +234,7 @@ def test_batch_matches_single_field_sweep(ctx):
     finally:
         R.ripple_field_destroy(f)
     assert rel_l1(req["output"], single) <= 1e-6
+    assert max_rel(req["output"], single) <= 1e-5  # another kernel: FP32 rounding of its own order
 
 
 def test_graphs_and_sync_interval_do_not_change_results(ctx):
@@ -257,7 +258,8 @@ def test_aos_layout_tile_variants_and_staging(ctx):
                 R.ripple_batch_configure(ctx, layout=layout, tile_variant=v, staging=staging, solo_rounds=False)
                 r = R.euler_request(base["input"], 21, base["dx"])
                 _run(ctx, [r])
-                assert rel_l1(r["output"], base["output"]) <= 1e-6
+                # tile shape, layout and halo staging change no arithmetic
+                assert np.array_equal(r["output"], base["output"]), (staging, layout, v)
     R.ripple_batch_configure(ctx, solo_rounds=False)
 
 
@@ -305,6 +307,7 @@ def test_requests_arriving_while_others_run(ctx):
     finally:
         R.ripple_field_destroy(f)
     assert rel_l1(first[0]["output"], single) <= 1e-5
+    assert max_rel(first[0]["output"], single) <= 1e-4  # 3000 steps of another kernel's rounding
     stats = R.ripple_batch_get_stats(ctx)
     assert stats["completed"] == 4 and stats["failed"] == 0
 
