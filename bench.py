@@ -593,9 +593,9 @@ def bench_batched(R, torch, local, nsteps=100, count=512, keep=None):
         "max_rel_l1_vs_loop": worst,
         "autotune": {"layout": "SoA" if cfg["layout"] == R.RIPPLE_SOA else "AoS",
                      "tile": ["32x8", "8x32", "16x16"][cfg["tile_variant"]],
-                     "staging": ["tma", "direct"][cfg["staging"]],
+                     "staging": ["tma", "direct", "walk"][cfg["staging"]],
                      "ms_per_global_step": {
-                         f"{['tma', 'direct'][k[2]]}/{'SoA' if k[0] == R.RIPPLE_SOA else 'AoS'}/"
+                         f"{['tma', 'direct', 'walk'][k[2]]}/{'SoA' if k[0] == R.RIPPLE_SOA else 'AoS'}/"
                          f"{['32x8', '8x32', '16x16'][k[1]]}": v for k, v in timings.items()}},
     }
 

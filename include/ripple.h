@@ -288,7 +288,9 @@ typedef struct {
     int64_t active_cells;     /* per-step cell budget of stepped Euler problems, chosen by least
                                  remaining work (0 = step every resident problem) */
     int staging;              /* halo staging of the Euler step: 0 = TMA tile loads by a producer warp
-                                 into a shared-memory ring; 1 = direct loads by every thread */
+                                 into a shared-memory ring; 1 = direct loads by every thread; 2 = no
+                                 tiles: warps walk rows of 30-column units (x faces by shuffles, the
+                                 y face carried); the results are the same bits either way */
     int async_queue;          /* 1 = dependency-driven rounds: ONE persistent launch runs up to
                                  steps_per_sync steps of every stepped Euler problem (each runs
                                  min(steps_per_sync, its remaining steps), so a round does not
@@ -350,10 +352,11 @@ RIPPLE_API ripple_status ripple_wait(ripple_ctx ctx, uint64_t ticket, int64_t ti
 RIPPLE_API ripple_status ripple_batch_get_stats(ripple_ctx ctx, ripple_batch_stats* out);
 
 /*
- * Autotuner: time the batched step for each halo staging (TMA, direct), layout
- * (SoA, AoS) and tile shape on n sample Euler problems of the given square
- * sides (dtype `dtype`), and return the fastest in *chosen (other fields of
- * *chosen are kept).  ms_per_step (nullable) receives 2 x 2 x 3 timings,
+ * Autotuner: time the batched step for each halo staging (TMA, direct, walk),
+ * layout (SoA, AoS) and tile shape on n sample Euler problems of the given
+ * square sides (dtype `dtype`), and return the fastest in *chosen (other fields
+ * of *chosen are kept).  ms_per_step (nullable) receives 3 x 2 x 3 timings (the
+ * walk staging has no tile shape: its three entries per layout are equal),
  * index (staging * 2 + layout_index) * 3 + tile_variant, SoA = layout index 0.
  * Does not change the context's configuration (pass *chosen to
  * ripple_batch_configure).

@@ -551,11 +551,11 @@ def ripple_batch_autotune(ctx, sides, dtype=RIPPLE_F32):
     """Returns (chosen config dict, {(layout, variant): ms per global step})."""
     arr = (ctypes.c_int64 * len(sides))(*[int(x) for x in sides])
     cfg = ripple_batch_config(RIPPLE_SOA, 0, 16, 1, int(dtype), 4, 0, 0, 0, SOLO_ROUNDS_DEFAULT)
-    ms = (ctypes.c_double * 12)()
+    ms = (ctypes.c_double * 18)()
     _check(load().ripple_batch_autotune(ctx, arr, len(sides), int(dtype), ctypes.byref(cfg), ms),
            "ripple_batch_autotune")
     timings = {}
-    for sg in range(2):
+    for sg in range(3):
         for li, lay in enumerate((RIPPLE_SOA, RIPPLE_AOS)):
             for v in range(3):
                 timings[(lay, v, sg)] = ms[(sg * 2 + li) * 3 + v]

@@ -44,6 +44,8 @@ constexpr BatchTileShape kBatchVariants[kNumBatchVariants] = {{32, 8}, {8, 32}, 
 // Halo staging of the batched Euler step (an autotuner dimension).
 constexpr int kBatchStagingTma = 0;     // producer warp + TMA ring (batch_euler_kernel)
 constexpr int kBatchStagingDirect = 1;  // every thread loads from global memory (batch_euler_direct_kernel)
+constexpr int kBatchStagingWalk = 2;    // warps walk rows of units, no tile staging (batch_euler_walk_kernel)
+constexpr int kNumBatchStagings = 3;
 
 template <typename T, int LAYOUT, int V>
 static cudaError_t step_v(int staging, int grid, cudaStream_t s, const BatchEuler* e, const void* f,
@@ -57,6 +59,8 @@ static cudaError_t step_v(int staging, int grid, cudaStream_t s, const BatchEule
         batch_euler_kernel<T, LAYOUT, TX, TY, true><<<grid, BC::NTHREADS, BC::SMEM, s>>>(e, table, c, q);
     else if (staging == kBatchStagingDirect)
         batch_euler_direct_kernel<T, LAYOUT, TX, TY><<<grid, 256, 0, s>>>(e, table, c);
+    else if (staging == kBatchStagingWalk)
+        batch_euler_walk_kernel<T><<<grid, 256, 0, s>>>(e, table, c);
     else
         batch_euler_kernel<T, LAYOUT, TX, TY><<<grid, BC::NTHREADS, BC::SMEM, s>>>(e, table, c);
     return cudaGetLastError();
@@ -70,6 +74,10 @@ static int occ_v(int staging)
     int n = 0;
     if (staging == kBatchStagingDirect) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_euler_direct_kernel<T, LAYOUT, TX, TY>, 256, 0);
+        return n;
+    }
+    if (staging == kBatchStagingWalk) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_euler_walk_kernel<T>, 256, 0);
         return n;
     }
     using BC = BatchEulerCfg<T, LAYOUT, TX, TY>;
@@ -719,6 +727,16 @@ static ripple_status grow(BatchRuntime* rt, int ne, int nf, int nt)
 }
 
 // Rebuild the descriptor arrays and the tile table of the resident set.
+// Table entries of an instance: its tiles, or with walk staging (per-step
+// rounds) its walk units of kSoloW columns x kBatchWalkRows rows.
+static bool walk_units(const BatchRuntime* rt) { return rt->cfg.staging == kBatchStagingWalk && !rt->cfg.async_queue; }
+static int walk_strips(const Inst* in) { return (int)((in->req.dims[0] + kSoloW - 1) / kSoloW); }
+static int table_entries(const BatchRuntime* rt, const Inst* in)
+{
+    if (in->req.kind != RIPPLE_REQ_EULER || !walk_units(rt)) return in->ntiles;
+    return walk_strips(in) * (int)((in->req.dims[1] + kBatchWalkRows - 1) / kBatchWalkRows);
+}
+
 static ripple_status rebuild_tables(BatchRuntime* rt)
 {
     int ne = 0, nf = 0, nt = 0;
@@ -727,7 +745,7 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
         if (in->req.kind != RIPPLE_REQ_EULER && rt->small_only) continue;
         if (in->req.kind == RIPPLE_REQ_EULER) ++ne;
         else ++nf;
-        nt += in->ntiles;
+        nt += table_entries(rt, in);
     }
     ripple_status st = grow(rt, std::max(ne, 1), std::max(nf, 1), std::max(nt, 1));
     if (st != RIPPLE_OK) return st;
@@ -753,15 +771,15 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
     int nt_e = 0;
     for (Inst* in : order) {
         if (in->req.kind == RIPPLE_REQ_EULER) {
-            nt_e += in->ntiles;
+            nt_e += table_entries(rt, in);
             BatchEuler& e = rt->h_euler[ie];
             e.buf[0] = in->buf[0];
             e.buf[1] = in->buf[1];
             e.ctl = &rt->slot_ctl[in->slot];
             e.g = in->g;
-            e.tiles_x = in->tiles_x;
+            e.tiles_x = walk_units(rt) ? walk_strips(in) : in->tiles_x;
             e.tile_begin = t;
-            e.ntiles = in->ntiles;
+            e.ntiles = table_entries(rt, in);
             e.bc = (int)in->req.fv.bc;
             e.start_step = in->start_step;
             e.nsteps = in->req.nsteps;
@@ -783,7 +801,7 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
             } else {
                 std::memcpy(e.map, in->map, sizeof(e.map));
             }
-            for (int k = 0; k < in->ntiles; ++k) rt->h_table[t + k] = (ie << 1) | 0;
+            for (int k = 0; k < e.ntiles; ++k) rt->h_table[t + k] = (ie << 1) | 0;
             ++ie;
         } else {
             if (rt->cfg.dtype == RIPPLE_F32) fill_fim_desc<float>(rt, in, rt->h_fim, jf);
@@ -793,7 +811,7 @@ static ripple_status rebuild_tables(BatchRuntime* rt)
             for (int k = 0; k < in->ntiles; ++k) rt->h_table[t + k] = (jf << 1) | 1;
             ++jf;
         }
-        t += in->ntiles;
+        t += table_entries(rt, in);
     }
     cudaStream_t s = rt->compute;
     if (ne) RIPPLE_CUDA(cudaMemcpyAsync(rt->d_euler, rt->h_euler, ne * sizeof(BatchEuler), cudaMemcpyHostToDevice, s));
@@ -1464,10 +1482,15 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
     RIPPLE_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     double best_ms = 1e300;
     ripple_status status = RIPPLE_OK;
-    for (int sg = 0; sg < 2 && status == RIPPLE_OK; ++sg)
+    for (int sg = 0; sg < kNumBatchStagings && status == RIPPLE_OK; ++sg)
     for (int li = 0; li < 2 && status == RIPPLE_OK; ++li) {
         const ripple_layout lay = li == 0 ? RIPPLE_SOA : RIPPLE_AOS;
         for (int v = 0; v < kNumBatchVariants && status == RIPPLE_OK; ++v) {
+            const bool walk = sg == kBatchStagingWalk;  // walk units: the tile shape does not apply
+            if (walk && v > 0) {
+                if (ms) ms[(sg * 2 + li) * kNumBatchVariants + v] = ms[(sg * 2 + li) * kNumBatchVariants];
+                continue;
+            }
             std::vector<void*> bufs;
             std::vector<size_t> sizes;
             std::vector<BatchEuler> h(n);
@@ -1505,7 +1528,7 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
                 h[i].buf[1] = b[1];
                 h[i].ctl = ctl + i;
                 h[i].g = g;
-                h[i].tiles_x = (int)((sides[i] + tx - 1) / tx);
+                h[i].tiles_x = walk ? (int)((sides[i] + kSoloW - 1) / kSoloW) : (int)((sides[i] + tx - 1) / tx);
                 h[i].tile_begin = (int)table.size();
                 h[i].bc = RIPPLE_BC_PERIODIC;
                 h[i].start_step = 0;
@@ -1518,7 +1541,8 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
                 h[i].gm1_f = (float)h[i].gm1;
                 h[i].inv_dx0_f = h[i].inv_dx1_f = (float)h[i].inv_dx0;
                 if (status == RIPPLE_OK) status = encode_batch_maps(h[i], lay, dt, v);
-                const int nt = h[i].tiles_x * (int)((sides[i] + ty - 1) / ty);
+                const int nt = walk ? h[i].tiles_x * (int)((sides[i] + kBatchWalkRows - 1) / kBatchWalkRows)
+                                    : h[i].tiles_x * (int)((sides[i] + ty - 1) / ty);
                 for (int k = 0; k < nt; ++k) table.push_back(i << 1);
             }
             if (status != RIPPLE_OK) { cleanup(); break; }
@@ -1639,8 +1663,7 @@ ripple_status ripple_batch_configure(ripple_ctx ctx, const ripple_batch_config* 
     if (!ctx || !cfg) return fail(RIPPLE_ERR_INVALID, "NULL argument");
     if (cfg->layout != RIPPLE_AOS && cfg->layout != RIPPLE_SOA) return fail(RIPPLE_ERR_INVALID, "bad layout");
     if (cfg->tile_variant < 0 || cfg->tile_variant >= kNumBatchVariants) return fail(RIPPLE_ERR_INVALID, "bad tile variant");
-    if (cfg->staging != kBatchStagingTma && cfg->staging != kBatchStagingDirect)
-        return fail(RIPPLE_ERR_INVALID, "bad halo staging");
+    if (cfg->staging < 0 || cfg->staging >= kNumBatchStagings) return fail(RIPPLE_ERR_INVALID, "bad halo staging");
     if (cfg->steps_per_sync < 1) return fail(RIPPLE_ERR_INVALID, "steps_per_sync must be >= 1");
     if (cfg->async_queue != 0 && cfg->async_queue != 1) return fail(RIPPLE_ERR_INVALID, "async_queue must be 0 or 1");
     if (cfg->fim_iters_per_step < 1 || cfg->fim_iters_per_step > 64)

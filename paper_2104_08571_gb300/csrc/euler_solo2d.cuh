@@ -99,18 +99,17 @@ struct SoloUnit {
 // Start unit u: its first rows and the face below its first row (none of it
 // depends on dt, so the first unit of a step starts before dt is known).
 template <typename T>
-__device__ __forceinline__ void solo_unit_begin(const SoloEuler& a, const T* __restrict__ in, int u, int lane,
-                                                T gamma, T gm1, SoloUnit<T>& w)
+__device__ __forceinline__ void solo_unit_begin(const FieldGeom& g, int strips, int rows, const T* __restrict__ in,
+                                                int u, int lane, T gamma, T gm1, SoloUnit<T>& w)
 {
-    const FieldGeom& g = a.g;
-    w.strip = u % a.strips;
-    const int seg = u / a.strips;
+    w.strip = u % strips;
+    const int seg = u / strips;
     w.x = w.strip * kSoloW - 1 + lane;
     w.xl = min(w.x, g.n[0]);  // columns past the ghost column load the ghost (unused)
     w.upd = lane >= 1 && lane <= kSoloW && w.x < g.n[0];
     w.xface = lane >= 1 && w.x <= g.n[0];
-    w.y0 = seg * a.rows;
-    w.y1 = min(g.n[1], w.y0 + a.rows);
+    w.y0 = seg * rows;
+    w.y1 = min(g.n[1], w.y0 + rows);
     w.chk = T(1);
     w.bad = false;
     T qd[4];
@@ -123,11 +122,10 @@ __device__ __forceinline__ void solo_unit_begin(const SoloEuler& a, const T* __r
 
 // Walk the started unit's rows: faces, update, stores, ghost images.
 template <typename T>
-__device__ __forceinline__ void solo_unit_walk(const SoloEuler& a, const T* __restrict__ in, T* __restrict__ out,
-                                               T gamma, T gm1, const T (&inv_dx)[3], T dtT, SoloUnit<T>& w,
-                                               T& smax)
+__device__ __forceinline__ void solo_unit_walk(const FieldGeom& g, int bc, const T* __restrict__ in,
+                                               T* __restrict__ out, T gamma, T gm1, const T (&inv_dx)[3], T dtT,
+                                               SoloUnit<T>& w, T& smax)
 {
-    const FieldGeom& g = a.g;
     for (int y = w.y0; y < w.y1; ++y) {
         // rows y + 1 (qa) and y + 2 (qf) are loaded; fetch row y + 3
         T qg[4];
@@ -151,7 +149,7 @@ __device__ __forceinline__ void solo_unit_walk(const SoloEuler& a, const T* __re
             smax = max(smax, wave_sum<T, 2>(qn, gamma, gm1, inv_dx, ok));
             w.bad |= !ok;
             if (w.x < g.h || w.x >= g.n[0] - g.h || y < g.h || y >= g.n[1] - g.h)
-                write_ghost_images<T, 2>(out, g, a.bc, w.x, y, 0, qn);
+                write_ghost_images<T, 2>(out, g, bc, w.x, y, 0, qn);
         }
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
@@ -196,19 +194,19 @@ __global__ void __launch_bounds__(kSoloThreads) solo_euler2d_kernel(const SoloEu
         }
         SoloUnit<T> w;
         int u = warp;
-        if (u < units) solo_unit_begin(a, in, u, lane, gamma, gm1, w);
+        if (u < units) solo_unit_begin(a.g, a.strips, a.rows, in, u, lane, gamma, gm1, w);
         __syncthreads();  // s_dt
         const T dtT = s_dt[0];
         T smax = T(0);
         while (u < units) {
-            solo_unit_walk(a, in, out, gamma, gm1, inv_dx, dtT, w, smax);
+            solo_unit_walk(a.g, a.bc, in, out, gamma, gm1, inv_dx, dtT, w, smax);
             // a non-admissible face or new state: the unit's first cell and row
             if (__any_sync(0xffffffffu, w.bad || !(w.chk > T(0))) && lane == 0) {
                 record_bad(ctl, BAD_STATE, w.strip * kSoloW, w.y0, 0);
                 atomicOr(&ctl->err, DEV_ERR_NUMERIC);
             }
             u += nwarps;
-            if (u < units) solo_unit_begin(a, in, u, lane, gamma, gm1, w);
+            if (u < units) solo_unit_begin(a.g, a.strips, a.rows, in, u, lane, gamma, gm1, w);
         }
         // CTA maximum of the new wave-speed sums -> the next ring slot (one
         // atomic per CTA, before the CTA's arrival at the barrier)
@@ -227,6 +225,70 @@ __global__ void __launch_bounds__(kSoloThreads) solo_euler2d_kernel(const SoloEu
             return;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// The same row walks as the batched step (one launch per global step over
+// every active Euler problem): table entries [0, ntiles_e) of the batch are
+// walk units instead of tiles, instance-major (BatchEuler::tile_begin is the
+// instance's first unit, tiles_x its strips of kSoloW columns, units of
+// kBatchWalkRows rows).  A warp takes one unit at a time: the instance's local
+// step, its dt (lane 0, FP64, broadcast), the walk, its wave-speed maximum;
+// unit 0 of an instance advances t and clears the ring slot after next, as
+// tile 0 does in the tiled step.  Results are those of the tiled step bit for
+// bit (same faces, same update).
+// ---------------------------------------------------------------------------
+constexpr int kBatchWalkRows = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) batch_euler_walk_kernel(const BatchEuler* __restrict__ euler,
+                                                               const int* __restrict__ table,
+                                                               BatchCtl* __restrict__ bctl)
+{
+    const unsigned long long gstep = __ldcg(&bctl->gstep[0]);
+    const int end = __ldcg(&bctl->ntiles_e);
+    const int lane = threadIdx.x & 31;
+    const int wpc = blockDim.x >> 5;
+    const int nwarps = gridDim.x * wpc;
+    for (int u = blockIdx.x * wpc + (threadIdx.x >> 5); u < end; u += nwarps) {
+        const int inst = __ldg(&table[u]) >> 1;
+        const BatchEuler& d = euler[inst];
+        const long long local = (long long)gstep - d.start_step;
+        if (local < 0 || local >= d.nsteps) continue;
+        const int lu = u - d.tile_begin;
+        const int rs = (int)(local % 3);
+        FieldCtl* ctl = d.ctl;
+        double dt = 0.0;
+        if (lane == 0) dt = d.cfl / __longlong_as_double((long long)__ldcg(&ctl->smax[rs]));
+        dt = __shfl_sync(0xffffffffu, dt, 0);
+        if (lu == 0 && lane == 0) {
+            ctl->t = local == 0 ? dt : ctl->t + dt;
+            ctl->dt_last = dt;
+            ctl->smax[(rs + 2) % 3] = 0ull;
+        }
+        const T dtT = (T)dt;
+        const T gamma = field_const<T>(d.gamma, d.gamma_f), gm1 = field_const<T>(d.gm1, d.gm1_f);
+        const T inv_dx[3] = {field_const<T>(d.inv_dx0, d.inv_dx0_f), field_const<T>(d.inv_dx1, d.inv_dx1_f), T(0)};
+        const T* in = static_cast<const T*>(d.buf[local & 1]);
+        T* out = static_cast<T*>(d.buf[(local & 1) ^ 1]);
+        SoloUnit<T> w;
+        solo_unit_begin(d.g, d.tiles_x, kBatchWalkRows, in, lu, lane, gamma, gm1, w);
+        T smax = T(0);
+        solo_unit_walk(d.g, d.bc, in, out, gamma, gm1, inv_dx, dtT, w, smax);
+        T v = smax;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+        const bool wbad = __any_sync(0xffffffffu, w.bad || !(w.chk > T(0)));
+        if (lane == 0) {
+            atomic_max_pos_double(&ctl->smax[(rs + 1) % 3], (double)v);
+            if (wbad) {
+                record_bad(ctl, BAD_STATE, w.strip * kSoloW, w.y0, 0);
+                atomicOr(&ctl->err, DEV_ERR_NUMERIC);
+            }
+        }
+    }
+    __syncwarp();
+    batch_finish_launch(bctl, 0);
 }
 
 }  // namespace ripple

@@ -252,7 +252,7 @@ def test_graphs_and_sync_interval_do_not_change_results(ctx):
 def test_aos_layout_tile_variants_and_staging(ctx):
     base = _euler(77, 61, 0.2, 21)
     _run(ctx, [base])
-    for staging in (0, 1):
+    for staging in (0, 1, 2):
         for layout in (R.RIPPLE_SOA, R.RIPPLE_AOS):
             for v in range(3):
                 R.ripple_batch_configure(ctx, layout=layout, tile_variant=v, staging=staging, solo_rounds=False)
@@ -336,6 +336,6 @@ def test_autotune_picks_a_candidate(ctx):
     sides = [s for s, _ in inputs.batch_problems(32, seed=2)]
     cfg, timings = R.ripple_batch_autotune(ctx, sides)
     assert cfg["layout"] in (R.RIPPLE_SOA, R.RIPPLE_AOS) and 0 <= cfg["tile_variant"] < 3
-    assert cfg["staging"] in (0, 1)
-    assert len(timings) == 12 and all(v > 0 for v in timings.values())
+    assert cfg["staging"] in (0, 1, 2)
+    assert len(timings) == 18 and all(v > 0 for v in timings.values())
     assert timings[(cfg["layout"], cfg["tile_variant"], cfg["staging"])] == min(timings.values())
