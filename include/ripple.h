@@ -289,7 +289,7 @@ typedef struct {
                                  remaining work (0 = step every resident problem) */
     int staging;              /* halo staging of the Euler step: 0 = TMA tile loads by a producer warp
                                  into a shared-memory ring; 1 = direct loads by every thread; 2 = no
-                                 tiles: warps walk rows of 30-column units (x faces by shuffles, the
+                                 tiles: warps walk 30-column x 16-row units (x faces by shuffles, the
                                  y face carried); the results are the same bits either way */
     int async_queue;          /* 1 = dependency-driven rounds: ONE persistent launch runs up to
                                  steps_per_sync steps of every stepped Euler problem (each runs

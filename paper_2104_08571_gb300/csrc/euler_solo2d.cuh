@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kSoloThreads) solo_euler2d_kernel(const SoloEu
 // tile 0 does in the tiled step.  Results are those of the tiled step bit for
 // bit (same faces, same update).
 // ---------------------------------------------------------------------------
-constexpr int kBatchWalkRows = 8;
+constexpr int kBatchWalkRows = 16;
 
 template <typename T>
 __global__ void __launch_bounds__(256) batch_euler_walk_kernel(const BatchEuler* __restrict__ euler,
