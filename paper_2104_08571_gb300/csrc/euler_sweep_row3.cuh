@@ -34,11 +34,20 @@
 //     wherever it is needed (interior lanes, tile-edge work of the halo
 //     warps, the neighbouring tile), so a face shared by two tiles has the
 //     same bits in both, the update telescopes and a uniform state stays
-//     bit-exact.
+//     bit-exact.  The y predicted states of all 16 warps' rows and the y
+//     faces of warps 1 .. 15 run through one copy of that code in the plane
+//     loop: the loop body's size sets how often warps stall on instruction
+//     fetch (a two-plane unrolled body ran 45 % slower);
+//   * faces are kept as twice the Rusanov flux and the update scales flux
+//     differences by 0.5/dx: both scalings are exact (short of subnormal
+//     fluxes), so the result has the bits of the halved flux times 1/dx,
+//     one multiplication per face component cheaper.
 //
-// Every wait is bounded.  A wait that runs out sets the CTA's abort flag;
-// later waits then return at once, so the CTA finishes its loop (stores stay
-// inside the field) and reports DEV_ERR_TIMEOUT.
+// Every wait is bounded.  A wait first tests its phase without blocking (the
+// common case: the data is there); otherwise it polls with a suspend hint.  A
+// wait that runs out sets the CTA's abort flag; later waits then return at
+// once, so the CTA finishes its loop (stores stay inside the field) and
+// reports DEV_ERR_TIMEOUT.
 #pragma once
 #include <cuda.h>
 #include <cstdint>
@@ -148,17 +157,25 @@ __global__ void __launch_bounds__(512, 1)
     __syncthreads();
     const f2 gamma = splat<f2>(prm.gamma_f), gm1 = splat<f2>(prm.gm1_f);
     const f2 mdt = splat<f2>(-sdt[0]);
-    f2 inv_dx[3], half_dtdx[3];
+    // faces are twice the Rusanov flux (rus<..., false>); the update scales
+    // flux differences by 0.5/dx (upd_dx), which gives the bits of the other
+    // sweep kernels' halved flux times 1/dx
+    f2 inv_dx[3], half_dtdx[3], upd_dx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         inv_dx[d] = splat<f2>(prm.inv_dx_f[d]);
         half_dtdx[d] = splat<f2>(sdt[1 + d]);
+        upd_dx[d] = splat<f2>(0.5f * prm.inv_dx_f[d]);
     }
+    constexpr bool kHalved = false;
 
     // ---- bounded waits; after the first that runs out, none waits any more ----
-    // (each poll may suspend the warp for up to 20 us; 2^16 polls bound a wait
-    // to about a second of polling after the first that suspends)
+    // (a non-blocking test first: most waits find their phase complete, and
+    // then cost neither the abort flag's shared-memory load nor a suspend;
+    // each later poll may suspend the warp for up to 20 us, and 2^16 polls
+    // bound a wait to about a second of polling after the first that suspends)
     auto wait_bar = [&](int b, unsigned parity) {
+        if (mbar_test_wait(&bars[b], parity & 1u)) return;
         if (flags[0]) return;
         for (uint32_t i = 0; i < (1u << 16); ++i)
             if (mbar_try_wait_hint(&bars[b], parity & 1u, 20000u)) return;
@@ -255,7 +272,7 @@ __global__ void __launch_bounds__(512, 1)
             load_pair(plane(seq_base + 3), my_off, q3);
             muscl<f2, 3, 2>(q0, q1, q2, gm1, half_dtdx[2], L1, R1, chk);
             muscl<f2, 3, 2>(q1, q2, q3, gm1, half_dtdx[2], L2, zR, chk);
-            rus<f2, 3, 2>(R1, L2, gamma, gm1, Fzm, chk);
+            rus<f2, 3, 2, kHalved>(R1, L2, gamma, gm1, Fzm, chk);
         }
         release(seq_base + 0);
         release(seq_base + 1);
@@ -278,7 +295,7 @@ __global__ void __launch_bounds__(512, 1)
             wait_full(roww ? sz + 2 : sz);
 
             if (warp == 0) {
-                // ---- halo row below: tile-edge x work of every row, its own high y state ----
+                // ---- halo row below: tile-edge x work of every row ----
                 {
                     // cells (x0-1, x0) of row erow0 as a pair, stencil x0-2 .. x0+1: face x0 - 1/2
                     const int o = K::idx(-1, erow0, 0);
@@ -298,7 +315,7 @@ __global__ void __launch_bounds__(512, 1)
                         a[m] = f2{Rh[m].x, Rh[m].x};
                         b[m] = f2{L[m].y, L[m].y};
                     }
-                    rus<f2, 3, 0>(a, b, gamma, gm1, F, chk);
+                    rus<f2, 3, 0, kHalved>(a, b, gamma, gm1, F, chk);
                     if (lane < TY) {
 #pragma unroll
                         for (int m = 0; m < NC; ++m) eb[K::E_FL + lane * NC + m] = F[m].x;
@@ -323,79 +340,59 @@ __global__ void __launch_bounds__(512, 1)
                         }
                     }
                 }
-                {
-                    f2 qm[NC], qc[NC], qp[NC], L[NC], Rh[NC];
-                    load_pair(S0, my_off - SY, qm);
-                    load_pair(S0, my_off, qc);
-                    load_pair(S0, my_off + SY, qp);
-                    muscl<f2, 3, 1>(qm, qc, qp, gm1, half_dtdx[1], L, Rh, chk);
+            }
+            // ---- every warp: the y predicted states of its row (warp 0: the
+            // row below the tile; warp NW - 1: the row above it) ----
+            f2 qc[NC], Ly[NC];
+            {
+                f2 qm[NC], qp[NC], Rh[NC];
+                load_pair(S0, my_off - SY, qm);
+                load_pair(S0, my_off, qc);
+                load_pair(S0, my_off + SY, qp);
+                muscl<f2, 3, 1>(qm, qc, qp, gm1, half_dtdx[1], Ly, Rh, chk);
+                if (warp < NW - 1) {
+                    // the high state goes to the row above: warp 0's buffer
+                    // of this plane (with its tile-edge data), or this row's
+                    // exchange row
+                    float* dst = warp == 0 ? eb + K::E_RY : Ry + jrow * ROW;
 #pragma unroll
-                    for (int m = 0; m < NC; ++m) st2(eb + K::E_RY + m * TX + lx, Rh[m]);
+                    for (int m = 0; m < NC; ++m) st2(dst + m * TX + lx, Rh[m]);
+                    mbar_arrive(&bars[warp == 0 ? K::BAR_EB + (int)kb : K::BAR_RB + warp]);
                 }
-                mbar_arrive(&bars[K::BAR_EB + kb]);
-            } else if (warp == NW - 1) {
-                // ---- halo row above: its low y state; the face above the tile's last row ----
-                f2 Ly[NC];
-                {
-                    f2 qm[NC], qc[NC], qp[NC], Rh[NC];
-                    load_pair(S0, my_off - SY, qm);
-                    load_pair(S0, my_off, qc);
-                    load_pair(S0, my_off + SY, qp);
-                    muscl<f2, 3, 1>(qm, qc, qp, gm1, half_dtdx[1], Ly, Rh, chk);
+            }
+            f2 Fzp[NC];
+            if (roww) {
+                // z: predicted states of plane z+1, the face z+1/2
+                f2 q1[NC], q2[NC], L[NC], Rn[NC];
+                load_pair(plane(sz + 1), my_off, q1);
+                load_pair(plane(sz + 2), my_off, q2);
+                muscl<f2, 3, 2>(qc, q1, q2, gm1, half_dtdx[2], L, Rn, chk);
+                rus<f2, 3, 2, kHalved>(zR, L, gamma, gm1, Fzp, chk);
+#pragma unroll
+                for (int m = 0; m < NC; ++m) zR[m] = Rn[m];
+            }
+            f2 Fyl[NC];
+            if (warp > 0) {
+                // the y face below this row, from the high state of the row below
+                // (row -1: warp 0's buffer of this plane; warp NW - 1: the
+                // face above the tile's last row)
+                const float* below;
+                if (warp == 1) {
+                    wait_bar(K::BAR_EB + (int)kb, it / K::NE);
+                    below = eb + K::E_RY;
+                } else {
+                    wait_bar(K::BAR_RB + warp - 1, it);
+                    below = Ry + (jrow - 1) * ROW;
                 }
-                wait_bar(K::BAR_RB + TY, it);
-                f2 a[NC], F[NC];
+                f2 a[NC];
 #pragma unroll
-                for (int m = 0; m < NC; ++m) a[m] = ld2(Ry + (TY - 1) * ROW + m * TX + lx);
-                rus<f2, 3, 1>(a, Ly, gamma, gm1, F, chk);
+                for (int m = 0; m < NC; ++m) a[m] = ld2(below + m * TX + lx);
+                rus<f2, 3, 1, kHalved>(a, Ly, gamma, gm1, Fyl, chk);
 #pragma unroll
-                for (int m = 0; m < NC; ++m) st2(Fy + TY * ROW + m * TX + lx, F[m]);
-                mbar_arrive(&bars[K::BAR_FB + NW - 1]);
-            } else {
-                // ---- row warp ----
-                f2 qc[NC], Ly[NC];
-                {
-                    // y predicted states of plane z; the high one goes to the warp above
-                    f2 qm[NC], qp[NC], Rh[NC];
-                    load_pair(S0, my_off - SY, qm);
-                    load_pair(S0, my_off, qc);
-                    load_pair(S0, my_off + SY, qp);
-                    muscl<f2, 3, 1>(qm, qc, qp, gm1, half_dtdx[1], Ly, Rh, chk);
-#pragma unroll
-                    for (int m = 0; m < NC; ++m) st2(Ry + jrow * ROW + m * TX + lx, Rh[m]);
-                    mbar_arrive(&bars[K::BAR_RB + warp]);
-                }
-                f2 Fzp[NC];
-                {
-                    // z: predicted states of plane z+1, the face z+1/2
-                    f2 q1[NC], q2[NC], L[NC], Rn[NC];
-                    load_pair(plane(sz + 1), my_off, q1);
-                    load_pair(plane(sz + 2), my_off, q2);
-                    muscl<f2, 3, 2>(qc, q1, q2, gm1, half_dtdx[2], L, Rn, chk);
-                    rus<f2, 3, 2>(zR, L, gamma, gm1, Fzp, chk);
-#pragma unroll
-                    for (int m = 0; m < NC; ++m) zR[m] = Rn[m];
-                }
-                f2 Fyl[NC];
-                {
-                    // the y face below this row, from the high state of the row below
-                    // (row -1: warp 0's buffer of this plane)
-                    const float* below;
-                    if (warp == 1) {
-                        wait_bar(K::BAR_EB + (int)kb, it / K::NE);
-                        below = eb + K::E_RY;
-                    } else {
-                        wait_bar(K::BAR_RB + warp - 1, it);
-                        below = Ry + (jrow - 1) * ROW;
-                    }
-                    f2 a[NC];
-#pragma unroll
-                    for (int m = 0; m < NC; ++m) a[m] = ld2(below + m * TX + lx);
-                    rus<f2, 3, 1>(a, Ly, gamma, gm1, Fyl, chk);
-#pragma unroll
-                    for (int m = 0; m < NC; ++m) st2(Fy + jrow * ROW + m * TX + lx, Fyl[m]);
-                    mbar_arrive(&bars[K::BAR_FB + warp]);
-                }
+                for (int m = 0; m < NC; ++m) st2(Fy + jrow * ROW + m * TX + lx, Fyl[m]);
+                mbar_arrive(&bars[K::BAR_FB + warp]);
+            }
+            if (roww) {
                 f2 dFx[NC];
                 {
                     // x: predicted states of the pair, faces lx+1/2 and lx+3/2
@@ -416,7 +413,7 @@ __global__ void __launch_bounds__(512, 1)
                         if (lane == 31) nx = eL[m];
                         b[m] = f2{L[m].y, nx};
                     }
-                    rus<f2, 3, 0>(Rh, b, gamma, gm1, F, chk);
+                    rus<f2, 3, 0, kHalved>(Rh, b, gamma, gm1, F, chk);
                     const float* eF = eb + K::E_FL + jrow * NC;
 #pragma unroll
                     for (int m = 0; m < NC; ++m) {
@@ -432,9 +429,9 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
                 for (int m = 0; m < NC; ++m) {
                     const f2 fyu = ld2(Fy + (jrow + 1) * ROW + m * TX + lx);
-                    f2 acc = dFx[m] * inv_dx[0];
-                    acc = fma_v(fyu - Fyl[m], inv_dx[1], acc);
-                    acc = fma_v(Fzp[m] - Fzm[m], inv_dx[2], acc);
+                    f2 acc = dFx[m] * upd_dx[0];
+                    acc = fma_v(fyu - Fyl[m], upd_dx[1], acc);
+                    acc = fma_v(Fzp[m] - Fzm[m], upd_dx[2], acc);
                     qn[m] = fma_v(mdt, acc, qc[m]);
                     Fzm[m] = Fzp[m];
                     if (vx1) {
