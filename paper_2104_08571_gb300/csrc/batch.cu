@@ -55,7 +55,9 @@ static cudaError_t step_v(int staging, int grid, cudaStream_t s, const BatchEule
     using BC = BatchEulerCfg<T, LAYOUT, TX, TY>;
     if (kind != 0)
         batch_fim_kernel<T><<<grid, EikTile<2>::NT, 0, s>>>(static_cast<const BatchFim<T>*>(f), table, c);
-    else if (q)  // a dependency-driven round (TMA staging)
+    else if (q && staging == kBatchStagingWalk)  // a dependency-driven round over walk units
+        batch_euler_walk_async_kernel<T><<<grid, 256, 0, s>>>(e, table, c, q);
+    else if (q)  // a dependency-driven round over tiles (TMA staging)
         batch_euler_kernel<T, LAYOUT, TX, TY, true><<<grid, BC::NTHREADS, BC::SMEM, s>>>(e, table, c, q);
     else if (staging == kBatchStagingDirect)
         batch_euler_direct_kernel<T, LAYOUT, TX, TY><<<grid, 256, 0, s>>>(e, table, c);
@@ -727,9 +729,10 @@ static ripple_status grow(BatchRuntime* rt, int ne, int nf, int nt)
 }
 
 // Rebuild the descriptor arrays and the tile table of the resident set.
-// Table entries of an instance: its tiles, or with walk staging (per-step
-// rounds) its walk units of kSoloW columns x kBatchWalkRows rows.
-static bool walk_units(const BatchRuntime* rt) { return rt->cfg.staging == kBatchStagingWalk && !rt->cfg.async_queue; }
+// Table entries of an instance: its tiles, or with walk staging its walk
+// units of kSoloW columns x kBatchWalkRows rows (per-step launches and
+// dependency-driven rounds alike).
+static bool walk_units(const BatchRuntime* rt) { return rt->cfg.staging == kBatchStagingWalk; }
 static int walk_strips(const Inst* in) { return (int)((in->req.dims[0] + kSoloW - 1) / kSoloW); }
 static int table_entries(const BatchRuntime* rt, const Inst* in)
 {
@@ -919,11 +922,11 @@ static ripple_status launch_round_async(BatchRuntime* rt, int K, std::vector<lon
     rt->h_cum[0] = 0;
     int m = ne;  // instances with r > n form the prefix [0, m)
     long long tiles = 0;
-    for (int i = 0; i < ne; ++i) tiles += rt->euler_order[i]->ntiles;
+    for (int i = 0; i < ne; ++i) tiles += table_entries(rt, rt->euler_order[i]);
     for (int n = 0; n < K; ++n) {
         while (m > 0 && steps[m - 1] <= n) {
             --m;
-            tiles -= rt->euler_order[m]->ntiles;
+            tiles -= table_entries(rt, rt->euler_order[m]);
         }
         for (int i = 0; i < m; ++i)
             if (steps[i] <= n) return fail(RIPPLE_ERR_INTERNAL, "dependency-driven round: table not ordered");
@@ -934,11 +937,15 @@ static ripple_status launch_round_async(BatchRuntime* rt, int K, std::vector<lon
     a.next = 0;
     a.total = rt->h_cum[K];
     a.K = K;
-    // a step's tasks spread over the CTAs: take them several at a time only when
-    // every CTA gets that many (a small problem's step stays spread over many
-    // CTAs, so its next step is not held up behind one CTA's chunk)
-    const int per_cta = (int)std::min<long long>(kAsyncChunk, (long long)rt->h_cum[1] / std::max(1, rt->grid_async));
-    a.chunk = std::max(1, per_cta);
+    // a step's tasks spread over the workers (the tiled round's CTAs, or the
+    // walk round's warps): take them several at a time only when every worker
+    // gets that many (a small problem's step stays spread over many workers,
+    // so its next step is not held up behind one worker's chunk)
+    const bool walk = walk_units(rt);
+    const int grid = walk ? rt->grid : rt->grid_async;
+    const int workers = walk ? grid * (256 / 32) : grid;
+    const int per_worker = (int)std::min<long long>(kAsyncChunk, (long long)rt->h_cum[1] / std::max(1, workers));
+    a.chunk = std::max(1, per_worker);
     a.cum = rt->d_cum;
     a.done = rt->d_done;
     cudaStream_t s = rt->compute;
@@ -946,8 +953,9 @@ static ripple_status launch_round_async(BatchRuntime* rt, int K, std::vector<lon
     RIPPLE_CUDA(cudaMemcpyAsync(rt->d_async, rt->h_async, sizeof(BatchAsync), cudaMemcpyHostToDevice, s));
     RIPPLE_CUDA(cudaMemsetAsync(rt->d_done, 0, (size_t)std::max(ne, 1) * sizeof(unsigned), s));
     const int layout = rt->cfg.layout == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
-    RIPPLE_CUDA(launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant, kBatchStagingTma, rt->grid_async, s,
-                                  rt->d_euler, rt->d_fim, rt->d_table, rt->d_bctl, 0, rt->d_async));
+    RIPPLE_CUDA(launch_batch_step(rt->cfg.dtype, layout, rt->cfg.tile_variant,
+                                  walk ? kBatchStagingWalk : kBatchStagingTma, grid, s, rt->d_euler, rt->d_fim,
+                                  rt->d_table, rt->d_bctl, 0, rt->d_async));
     const int F = std::max(1, rt->cfg.fim_iters_per_step);
     long long nf = 0;
     for (long long k = 0; rt->has_f && k < (long long)K * F; ++k, ++nf)

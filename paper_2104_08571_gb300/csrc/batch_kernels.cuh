@@ -85,7 +85,8 @@ struct BatchAsync {
     int next;            // next task (atomic); the host zeroes it before the launch
     int total;           // tasks of the round: cum[K]
     int K;               // steps of the round
-    int chunk;           // tasks a producer takes at once (1..kAsyncChunk: fewer when a step has few tiles)
+    int chunk;           // tasks a worker (producer warp, or walk warp) takes at once (1..kAsyncChunk: fewer
+                         // when a step has few tasks)
     const int* cum;      // [K + 1] first task of each round step
     unsigned* done;      // [Euler instances] consumer-warp completions this round
 };

@@ -240,6 +240,45 @@ __global__ void __launch_bounds__(kSoloThreads) solo_euler2d_kernel(const SoloEu
 // ---------------------------------------------------------------------------
 constexpr int kBatchWalkRows = 16;
 
+// One walk unit of a batched step: local unit lu of instance d at the
+// instance's local step `local` (dt by lane 0 in FP64, broadcast; unit 0
+// advances t and clears the ring slot after next, as tile 0 does in the tiled
+// step), then the unit's wave-speed maximum into the instance's next ring slot.
+template <typename T>
+__device__ __forceinline__ void batch_walk_unit(const BatchEuler& d, int lu, long long local, int lane)
+{
+    const int rs = (int)(local % 3);
+    FieldCtl* ctl = d.ctl;
+    double dt = 0.0;
+    if (lane == 0) dt = d.cfl / __longlong_as_double((long long)__ldcg(&ctl->smax[rs]));
+    dt = __shfl_sync(0xffffffffu, dt, 0);
+    if (lu == 0 && lane == 0) {
+        ctl->t = local == 0 ? dt : ctl->t + dt;
+        ctl->dt_last = dt;
+        ctl->smax[(rs + 2) % 3] = 0ull;
+    }
+    const T dtT = (T)dt;
+    const T gamma = field_const<T>(d.gamma, d.gamma_f), gm1 = field_const<T>(d.gm1, d.gm1_f);
+    const T inv_dx[3] = {field_const<T>(d.inv_dx0, d.inv_dx0_f), field_const<T>(d.inv_dx1, d.inv_dx1_f), T(0)};
+    const T* in = static_cast<const T*>(d.buf[local & 1]);
+    T* out = static_cast<T*>(d.buf[(local & 1) ^ 1]);
+    SoloUnit<T> w;
+    solo_unit_begin(d.g, d.tiles_x, kBatchWalkRows, in, lu, lane, gamma, gm1, w);
+    T smax = T(0);
+    solo_unit_walk(d.g, d.bc, in, out, gamma, gm1, inv_dx, dtT, w, smax);
+    T v = smax;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const bool wbad = __any_sync(0xffffffffu, w.bad || !(w.chk > T(0)));
+    if (lane == 0) {
+        atomic_max_pos_double(&ctl->smax[(rs + 1) % 3], (double)v);
+        if (wbad) {
+            record_bad(ctl, BAD_STATE, w.strip * kSoloW, w.y0, 0);
+            atomicOr(&ctl->err, DEV_ERR_NUMERIC);
+        }
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) batch_euler_walk_kernel(const BatchEuler* __restrict__ euler,
                                                                const int* __restrict__ table,
@@ -255,40 +294,86 @@ __global__ void __launch_bounds__(256) batch_euler_walk_kernel(const BatchEuler*
         const BatchEuler& d = euler[inst];
         const long long local = (long long)gstep - d.start_step;
         if (local < 0 || local >= d.nsteps) continue;
-        const int lu = u - d.tile_begin;
-        const int rs = (int)(local % 3);
-        FieldCtl* ctl = d.ctl;
-        double dt = 0.0;
-        if (lane == 0) dt = d.cfl / __longlong_as_double((long long)__ldcg(&ctl->smax[rs]));
-        dt = __shfl_sync(0xffffffffu, dt, 0);
-        if (lu == 0 && lane == 0) {
-            ctl->t = local == 0 ? dt : ctl->t + dt;
-            ctl->dt_last = dt;
-            ctl->smax[(rs + 2) % 3] = 0ull;
-        }
-        const T dtT = (T)dt;
-        const T gamma = field_const<T>(d.gamma, d.gamma_f), gm1 = field_const<T>(d.gm1, d.gm1_f);
-        const T inv_dx[3] = {field_const<T>(d.inv_dx0, d.inv_dx0_f), field_const<T>(d.inv_dx1, d.inv_dx1_f), T(0)};
-        const T* in = static_cast<const T*>(d.buf[local & 1]);
-        T* out = static_cast<T*>(d.buf[(local & 1) ^ 1]);
-        SoloUnit<T> w;
-        solo_unit_begin(d.g, d.tiles_x, kBatchWalkRows, in, lu, lane, gamma, gm1, w);
-        T smax = T(0);
-        solo_unit_walk(d.g, d.bc, in, out, gamma, gm1, inv_dx, dtT, w, smax);
-        T v = smax;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-        const bool wbad = __any_sync(0xffffffffu, w.bad || !(w.chk > T(0)));
-        if (lane == 0) {
-            atomic_max_pos_double(&ctl->smax[(rs + 1) % 3], (double)v);
-            if (wbad) {
-                record_bad(ctl, BAD_STATE, w.strip * kSoloW, w.y0, 0);
-                atomicOr(&ctl->err, DEV_ERR_NUMERIC);
-            }
-        }
+        batch_walk_unit<T>(d, u - d.tile_begin, local, lane);
     }
     __syncwarp();
     batch_finish_launch(bctl, 0);
+}
+
+// The walk form of a dependency-driven round (BatchAsync; table entries are
+// walk units).  Warps take the round's tasks (round step n, table entry t)
+// from its counter, q->chunk at a time, in the step-major order of the tiled
+// round.  A unit of step n > 0 first waits (lane 0, bounded) until every unit
+// of its instance's step n - 1 is published: done[] counts units, ntiles of
+// them per step, and the unit's dt and every cell it reads come from that
+// step.  After its walk the warp publishes the unit: the warp barrier orders
+// every lane's stores (cells, ghost images, wave-speed maximum, unit 0's ring
+// slot) before lane 0's release add, which the waiting lane 0's acquire pairs
+// with; the waiting warp's barrier after that acquire orders its lanes' loads
+// (L2 loads, no stale L1 lines) after it.  A warp publishes every unit before
+// it takes or waits for the next, and the tasks a wait needs precede it in the
+// order and were taken by running warps, so the waits end; a wait that runs
+// out stops its warp and reports DEV_ERR_TIMEOUT.  Each unit's arithmetic is
+// the per-step walk kernel's, so results are those of per-step launches bit
+// for bit.
+template <typename T>
+__global__ void __launch_bounds__(256) batch_euler_walk_async_kernel(const BatchEuler* __restrict__ euler,
+                                                                     const int* __restrict__ table,
+                                                                     BatchCtl* __restrict__ bctl,
+                                                                     BatchAsync* __restrict__ q)
+{
+    const unsigned long long gstep = __ldcg(&bctl->gstep[0]);
+    const int lane = threadIdx.x & 31;
+    const int total = q->total, chunk = q->chunk, K = q->K;
+    bool ok = true;
+    // the current chunk of tasks [c_lo, c_hi), the cached task range [s_lo, s_hi) of round step s_n
+    int c_lo = 0, c_hi = 0, s_lo = 0, s_hi = 0, s_n = 0;
+    for (;;) {
+        if (c_lo == c_hi) {
+            int lo = 0;
+            if (lane == 0) lo = atomicAdd(&q->next, chunk);
+            lo = __shfl_sync(0xffffffffu, lo, 0);
+            if (lo >= total) break;
+            c_lo = lo;
+            c_hi = min(lo + chunk, total);
+        }
+        const int k = c_lo++;
+        if (k < s_lo || k >= s_hi) {
+            int lo = 0, hi = K;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(&q->cum[mid]) <= k) lo = mid;
+                else hi = mid;
+            }
+            s_n = lo;
+            s_lo = __ldg(&q->cum[lo]);
+            s_hi = __ldg(&q->cum[lo + 1]);
+        }
+        const int t = k - s_lo;
+        const int inst = __ldg(&table[t]) >> 1;
+        const BatchEuler& d = euler[inst];
+        if (s_n > 0) {
+            const unsigned need = (unsigned)s_n * (unsigned)d.ntiles;
+            int met = 1;
+            if (lane == 0) {
+                uint32_t i = 0;
+                while (ld_acquire_gpu(&q->done[inst]) < need && ++i < kDepSpinLimit) __nanosleep(64);
+                met = i < kDepSpinLimit;
+            }
+            met = __shfl_sync(0xffffffffu, met, 0);
+            __syncwarp();
+            if (!met) {
+                ok = false;
+                break;
+            }
+        }
+        batch_walk_unit<T>(d, t - d.tile_begin, (long long)gstep + s_n - d.start_step, lane);
+        __syncwarp();
+        if (lane == 0) red_release_gpu_add(&q->done[inst], 1u);
+    }
+    if (!ok && lane == 0) atomicOr(&bctl->err, DEV_ERR_TIMEOUT);
+    __syncwarp();
+    batch_finish_launch(bctl, 0, (unsigned long long)K);
 }
 
 }  // namespace ripple

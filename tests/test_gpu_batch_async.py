@@ -64,6 +64,22 @@ def test_async_rounds_equal_per_step_launches_bitwise(ctx):
             assert np.array_equal(q["output"], r["output"]), (sps, r["input"].shape)
 
 
+def test_async_walk_rounds_equal_per_step_launches_bitwise(ctx):
+    # walk staging: dependency-driven rounds take walk units (30 columns x 16
+    # rows) from the round's counter; every unit is the per-step walk's
+    # arithmetic, which is the tiled step's bit for bit
+    ref = _mix()
+    infos = _run(ctx, ref)
+    assert all(i["status"] == R.RIPPLE_OK for i in infos)
+    for sps, async_q in ((64, False), (64, True), (7, True), (1, True)):
+        R.ripple_batch_configure(ctx, steps_per_sync=sps, staging=2, async_queue=async_q, solo_rounds=False)
+        reqs = [_again(r) for r in ref]
+        infos = _run(ctx, reqs)
+        for r, q, i in zip(ref, reqs, infos):
+            assert i["status"] == R.RIPPLE_OK and i["work"] == r["nsteps"]
+            assert np.array_equal(q["output"], r["output"]), (sps, async_q, r["input"].shape)
+
+
 def test_async_rounds_match_oracle(ctx):
     R.ripple_batch_configure(ctx, steps_per_sync=128, async_queue=True, solo_rounds=False)
     reqs = _mix()
@@ -75,18 +91,22 @@ def test_async_rounds_match_oracle(ctx):
         assert_parity(req["output"], ref, 2e-5, LINF_F32)
 
 
-def test_one_launch_per_round(ctx):
+@pytest.mark.parametrize("staging", [0, 2])
+def test_one_launch_per_round(ctx, staging):
     # uneven step counts: per-step launches shrink a round to the shortest
     # remaining problem; a dependency-driven round runs each to its own end
+    # (staging 0: tiles staged by TMA; 2: walk units)
     reqs = [_euler(64 + 8 * i, 48, 0.1 + 0.01 * i, 5 + 7 * i) for i in range(8)]
-    R.ripple_batch_configure(ctx, steps_per_sync=64, async_queue=True, use_graphs=False, solo_rounds=False)
+    R.ripple_batch_configure(ctx, steps_per_sync=64, async_queue=True, use_graphs=False, staging=staging,
+                             solo_rounds=False)
     s0 = R.ripple_batch_get_stats(ctx)
     infos = _run(ctx, reqs)
     s1 = R.ripple_batch_get_stats(ctx)
     assert all(i["status"] == R.RIPPLE_OK for i in infos)
     assert s1["launches"] - s0["launches"] == 1
     assert s1["global_steps"] - s0["global_steps"] == max(r["nsteps"] for r in reqs)
-    R.ripple_batch_configure(ctx, steps_per_sync=64, async_queue=False, use_graphs=False, solo_rounds=False)
+    R.ripple_batch_configure(ctx, steps_per_sync=64, async_queue=False, use_graphs=False, staging=staging,
+                             solo_rounds=False)
     again = [_again(r) for r in reqs]
     s2 = R.ripple_batch_get_stats(ctx)
     _run(ctx, again)
@@ -110,8 +130,9 @@ def test_async_layouts_and_tile_shapes(ctx):
     R.ripple_batch_configure(ctx, solo_rounds=False)
 
 
-def test_async_with_eikonal_requests(ctx):
-    R.ripple_batch_configure(ctx, steps_per_sync=16, async_queue=True, solo_rounds=False)
+@pytest.mark.parametrize("staging", [0, 2])
+def test_async_with_eikonal_requests(ctx, staging):
+    R.ripple_batch_configure(ctx, steps_per_sync=16, async_queue=True, staging=staging, solo_rounds=False)
     s = inputs.eikonal_slowness((120, 90), seed=4).astype(np.float32)
     src = inputs.eikonal_sources((120, 90), seed=4)
     e = R.eikonal_request(s, src, 1.0 / 120)
@@ -126,9 +147,11 @@ def test_async_with_eikonal_requests(ctx):
     assert np.array_equal(alone["output"], a["output"])
 
 
-def test_async_with_cell_budget_and_late_requests(ctx):
+@pytest.mark.parametrize("staging", [0, 2])
+def test_async_with_cell_budget_and_late_requests(ctx, staging):
     # a per-round cell budget: problems join the stepped set as others finish
-    R.ripple_batch_configure(ctx, steps_per_sync=8, async_queue=True, active_cells=64 * 64 * 2, solo_rounds=False)
+    R.ripple_batch_configure(ctx, steps_per_sync=8, async_queue=True, active_cells=64 * 64 * 2, staging=staging,
+                             solo_rounds=False)
     reqs = [_euler(64, 64, 0.1 + 0.03 * i, 12 + 5 * i) for i in range(5)]
     t1 = R.ripple_batch_submit(ctx, reqs[:3])
     t2 = R.ripple_batch_submit(ctx, reqs[3:])
@@ -141,8 +164,9 @@ def test_async_with_cell_budget_and_late_requests(ctx):
         assert np.array_equal(b["output"], r["output"])
 
 
-def test_async_numeric_error_reported_per_request(ctx):
-    R.ripple_batch_configure(ctx, steps_per_sync=16, async_queue=True, solo_rounds=False)
+@pytest.mark.parametrize("staging", [0, 2])
+def test_async_numeric_error_reported_per_request(ctx, staging):
+    R.ripple_batch_configure(ctx, steps_per_sync=16, async_queue=True, staging=staging, solo_rounds=False)
     bad = _euler(40, 40, 0.2, 5)
     bad["input"][3, 10, 10] = -1.0  # negative energy -> negative pressure
     good = _euler(40, 40, 0.2, 9)
