@@ -43,7 +43,7 @@ BYTES_PER_CELL_UPDATE = 40  # FP32, 5 components: 20 B read + 20 B written per c
 # DRAM bytes per cell update of the sweep kernel (the row kernel, SoA) as measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum of one 256x256x128 launch, divided by its cells);
 # traffic scales with the cells of a launch.  Re-measure whenever the kernel changes.
-DRAM_BYTES_PER_CELL_UPDATE = (216841216 + 137352704) / (256 * 256 * 128)
+DRAM_BYTES_PER_CELL_UPDATE = (216594688 + 137211392) / (256 * 256 * 128)
 METRIC = "cell-updates/s"
 ACTIVE_CELLS = 4 << 20  # serving: per-step cell budget of stepped Euler problems
 

@@ -37,11 +37,7 @@
 //     bit-exact.  The y predicted states of all 16 warps' rows and the y
 //     faces of warps 1 .. 15 run through one copy of that code in the plane
 //     loop: the loop body's size sets how often warps stall on instruction
-//     fetch (a two-plane unrolled body ran 45 % slower);
-//   * faces are kept as twice the Rusanov flux and the update scales flux
-//     differences by 0.5/dx: both scalings are exact (short of subnormal
-//     fluxes), so the result has the bits of the halved flux times 1/dx,
-//     one multiplication per face component cheaper.
+//     fetch (a two-plane unrolled body ran 45 % slower).
 //
 // Every wait is bounded.  A wait first tests its phase without blocking (the
 // common case: the data is there); otherwise it polls with a suspend hint.  A
@@ -157,17 +153,12 @@ __global__ void __launch_bounds__(512, 1)
     __syncthreads();
     const f2 gamma = splat<f2>(prm.gamma_f), gm1 = splat<f2>(prm.gm1_f);
     const f2 mdt = splat<f2>(-sdt[0]);
-    // faces are twice the Rusanov flux (rus<..., false>); the update scales
-    // flux differences by 0.5/dx (upd_dx), which gives the bits of the other
-    // sweep kernels' halved flux times 1/dx
-    f2 inv_dx[3], half_dtdx[3], upd_dx[3];
+    f2 inv_dx[3], half_dtdx[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
         inv_dx[d] = splat<f2>(prm.inv_dx_f[d]);
         half_dtdx[d] = splat<f2>(sdt[1 + d]);
-        upd_dx[d] = splat<f2>(0.5f * prm.inv_dx_f[d]);
     }
-    constexpr bool kHalved = false;
 
     // ---- bounded waits; after the first that runs out, none waits any more ----
     // (a non-blocking test first: most waits find their phase complete, and
@@ -272,7 +263,7 @@ __global__ void __launch_bounds__(512, 1)
             load_pair(plane(seq_base + 3), my_off, q3);
             muscl<f2, 3, 2>(q0, q1, q2, gm1, half_dtdx[2], L1, R1, chk);
             muscl<f2, 3, 2>(q1, q2, q3, gm1, half_dtdx[2], L2, zR, chk);
-            rus<f2, 3, 2, kHalved>(R1, L2, gamma, gm1, Fzm, chk);
+            rus<f2, 3, 2>(R1, L2, gamma, gm1, Fzm, chk);
         }
         release(seq_base + 0);
         release(seq_base + 1);
@@ -315,7 +306,7 @@ __global__ void __launch_bounds__(512, 1)
                         a[m] = f2{Rh[m].x, Rh[m].x};
                         b[m] = f2{L[m].y, L[m].y};
                     }
-                    rus<f2, 3, 0, kHalved>(a, b, gamma, gm1, F, chk);
+                    rus<f2, 3, 0>(a, b, gamma, gm1, F, chk);
                     if (lane < TY) {
 #pragma unroll
                         for (int m = 0; m < NC; ++m) eb[K::E_FL + lane * NC + m] = F[m].x;
@@ -367,7 +358,7 @@ __global__ void __launch_bounds__(512, 1)
                 load_pair(plane(sz + 1), my_off, q1);
                 load_pair(plane(sz + 2), my_off, q2);
                 muscl<f2, 3, 2>(qc, q1, q2, gm1, half_dtdx[2], L, Rn, chk);
-                rus<f2, 3, 2, kHalved>(zR, L, gamma, gm1, Fzp, chk);
+                rus<f2, 3, 2>(zR, L, gamma, gm1, Fzp, chk);
 #pragma unroll
                 for (int m = 0; m < NC; ++m) zR[m] = Rn[m];
             }
@@ -387,7 +378,7 @@ __global__ void __launch_bounds__(512, 1)
                 f2 a[NC];
 #pragma unroll
                 for (int m = 0; m < NC; ++m) a[m] = ld2(below + m * TX + lx);
-                rus<f2, 3, 1, kHalved>(a, Ly, gamma, gm1, Fyl, chk);
+                rus<f2, 3, 1>(a, Ly, gamma, gm1, Fyl, chk);
 #pragma unroll
                 for (int m = 0; m < NC; ++m) st2(Fy + jrow * ROW + m * TX + lx, Fyl[m]);
                 mbar_arrive(&bars[K::BAR_FB + warp]);
@@ -413,7 +404,7 @@ __global__ void __launch_bounds__(512, 1)
                         if (lane == 31) nx = eL[m];
                         b[m] = f2{L[m].y, nx};
                     }
-                    rus<f2, 3, 0, kHalved>(Rh, b, gamma, gm1, F, chk);
+                    rus<f2, 3, 0>(Rh, b, gamma, gm1, F, chk);
                     const float* eF = eb + K::E_FL + jrow * NC;
 #pragma unroll
                     for (int m = 0; m < NC; ++m) {
@@ -429,9 +420,9 @@ __global__ void __launch_bounds__(512, 1)
 #pragma unroll
                 for (int m = 0; m < NC; ++m) {
                     const f2 fyu = ld2(Fy + (jrow + 1) * ROW + m * TX + lx);
-                    f2 acc = dFx[m] * upd_dx[0];
-                    acc = fma_v(fyu - Fyl[m], upd_dx[1], acc);
-                    acc = fma_v(Fzp[m] - Fzm[m], upd_dx[2], acc);
+                    f2 acc = dFx[m] * inv_dx[0];
+                    acc = fma_v(fyu - Fyl[m], inv_dx[1], acc);
+                    acc = fma_v(Fzp[m] - Fzm[m], inv_dx[2], acc);
                     qn[m] = fma_v(mdt, acc, qc[m]);
                     Fzm[m] = Fzp[m];
                     if (vx1) {

@@ -154,13 +154,8 @@ __device__ __forceinline__ f2 wave_sum2(const f2 (&q)[DIM + 2], f2 gamma, f2 gm1
 }
 
 // Rusanov face flux along D between left states a and right states b;
-// the smallest density/pressure of both goes to chk.  With HALVED = false the
-// result is twice the flux: the final halving is a multiplication by 0.5,
-// exact in binary floating point (short of a subnormal result), so a caller
-// that scales the flux differences by 0.5/dx instead of 1/dx gets the same
-// bits as with the halved flux and 1/dx, one multiplication per component
-// fewer.
-template <typename V, int DIM, int D, bool HALVED = true>
+// the smallest density/pressure of both goes to chk.
+template <typename V, int DIM, int D>
 __device__ __forceinline__ void rus(const V (&a)[DIM + 2], const V (&b)[DIM + 2], V gamma, V gm1, V (&F)[DIM + 2],
                                     float& chk)
 {
@@ -173,10 +168,7 @@ __device__ __forceinline__ void rus(const V (&a)[DIM + 2], const V (&b)[DIM + 2]
     const V s = max_v(abs_v(ua) + ca, abs_v(ub) + cb);
     const V half = splat<V>(0.5f);
 #pragma unroll
-    for (int m = 0; m < DIM + 2; ++m) {
-        if constexpr (HALVED) F[m] = half * fma_v(s, a[m] - b[m], Fa[m] + Fb[m]);
-        else F[m] = fma_v(s, a[m] - b[m], Fa[m] + Fb[m]);
-    }
+    for (int m = 0; m < DIM + 2; ++m) F[m] = half * fma_v(s, a[m] - b[m], Fa[m] + Fb[m]);
 }
 
 // FORCE face flux along D (Toro): the mean of the Lax-Friedrichs flux and
