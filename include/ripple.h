@@ -297,8 +297,9 @@ typedef struct {
                                  shrink when one problem ends); a tile of step n of a problem
                                  starts as soon as that problem has completed step n - 1 (its dt
                                  is the CFL limit of its whole state), with no barrier between
-                                 problems or global steps.  Uses TMA staging whatever `staging`
-                                 says.  0 = one launch per global step (default). */
+                                 problems or global steps.  With staging 2 the round's tasks are
+                                 walk units taken by warps; otherwise tiles staged by TMA (for
+                                 staging 1 as well).  0 = one launch per global step (default). */
     int solo_rounds;          /* n > 0 = while at most n problems are resident, each round runs the
                                  oldest of them alone on the single-problem kernels
                                  (Euler: one launch of the multi-step solver, up to about a millisecond

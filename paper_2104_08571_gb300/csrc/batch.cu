@@ -56,13 +56,13 @@ static cudaError_t step_v(int staging, int grid, cudaStream_t s, const BatchEule
     if (kind != 0)
         batch_fim_kernel<T><<<grid, EikTile<2>::NT, 0, s>>>(static_cast<const BatchFim<T>*>(f), table, c);
     else if (q && staging == kBatchStagingWalk)  // a dependency-driven round over walk units
-        batch_euler_walk_async_kernel<T><<<grid, 256, 0, s>>>(e, table, c, q);
+        batch_euler_walk_async_kernel<T><<<grid, kBatchWalkThreads, 0, s>>>(e, table, c, q);
     else if (q)  // a dependency-driven round over tiles (TMA staging)
         batch_euler_kernel<T, LAYOUT, TX, TY, true><<<grid, BC::NTHREADS, BC::SMEM, s>>>(e, table, c, q);
     else if (staging == kBatchStagingDirect)
         batch_euler_direct_kernel<T, LAYOUT, TX, TY><<<grid, 256, 0, s>>>(e, table, c);
     else if (staging == kBatchStagingWalk)
-        batch_euler_walk_kernel<T><<<grid, 256, 0, s>>>(e, table, c);
+        batch_euler_walk_kernel<T><<<grid, kBatchWalkThreads, 0, s>>>(e, table, c);
     else
         batch_euler_kernel<T, LAYOUT, TX, TY><<<grid, BC::NTHREADS, BC::SMEM, s>>>(e, table, c);
     return cudaGetLastError();
@@ -79,8 +79,11 @@ static int occ_v(int staging)
         return n;
     }
     if (staging == kBatchStagingWalk) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_euler_walk_kernel<T>, 256, 0);
-        return n;
+        // the per-step and the dependency-driven walk kernels share the grid
+        int na = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, batch_euler_walk_kernel<T>, kBatchWalkThreads, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&na, batch_euler_walk_async_kernel<T>, kBatchWalkThreads, 0);
+        return std::min(n, na);
     }
     using BC = BatchEulerCfg<T, LAYOUT, TX, TY>;
     auto k = batch_euler_kernel<T, LAYOUT, TX, TY, false>;
@@ -943,7 +946,7 @@ static ripple_status launch_round_async(BatchRuntime* rt, int K, std::vector<lon
     // so its next step is not held up behind one worker's chunk)
     const bool walk = walk_units(rt);
     const int grid = walk ? rt->grid : rt->grid_async;
-    const int workers = walk ? grid * (256 / 32) : grid;
+    const int workers = walk ? grid * (kBatchWalkThreads / 32) : grid;
     const int per_worker = (int)std::min<long long>(kAsyncChunk, (long long)rt->h_cum[1] / std::max(1, workers));
     a.chunk = std::max(1, per_worker);
     a.cum = rt->d_cum;

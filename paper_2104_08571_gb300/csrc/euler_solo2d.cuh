@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(kSoloThreads) solo_euler2d_kernel(const SoloEu
 // bit (same faces, same update).
 // ---------------------------------------------------------------------------
 constexpr int kBatchWalkRows = 16;
+constexpr int kBatchWalkThreads = 256;  // threads per CTA of the batched walk kernels (8 warps)
 
 // One walk unit of a batched step: local unit lu of instance d at the
 // instance's local step `local` (dt by lane 0 in FP64, broadcast; unit 0
@@ -280,7 +281,7 @@ __device__ __forceinline__ void batch_walk_unit(const BatchEuler& d, int lu, lon
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) batch_euler_walk_kernel(const BatchEuler* __restrict__ euler,
+__global__ void __launch_bounds__(kBatchWalkThreads) batch_euler_walk_kernel(const BatchEuler* __restrict__ euler,
                                                                const int* __restrict__ table,
                                                                BatchCtl* __restrict__ bctl)
 {
@@ -317,7 +318,7 @@ __global__ void __launch_bounds__(256) batch_euler_walk_kernel(const BatchEuler*
 // the per-step walk kernel's, so results are those of per-step launches bit
 // for bit.
 template <typename T>
-__global__ void __launch_bounds__(256) batch_euler_walk_async_kernel(const BatchEuler* __restrict__ euler,
+__global__ void __launch_bounds__(kBatchWalkThreads) batch_euler_walk_async_kernel(const BatchEuler* __restrict__ euler,
                                                                      const int* __restrict__ table,
                                                                      BatchCtl* __restrict__ bctl,
                                                                      BatchAsync* __restrict__ q)
