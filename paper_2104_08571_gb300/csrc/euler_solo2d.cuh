@@ -240,6 +240,11 @@ __global__ void __launch_bounds__(kSoloThreads) solo_euler2d_kernel(const SoloEu
 // ---------------------------------------------------------------------------
 constexpr int kBatchWalkRows = 16;
 constexpr int kBatchWalkThreads = 256;  // threads per CTA of the batched walk kernels (8 warps)
+// CTAs per SM the FP32 walk kernels are compiled for: three (80 registers, a
+// few bytes of spills) ran the 512-problem step 15 % faster than two (98
+// registers); the FP64 kernels need about 150 registers and keep one
+template <typename T>
+constexpr int batch_walk_min_blocks() { return sizeof(T) == 4 ? 3 : 1; }
 
 // One walk unit of a batched step: local unit lu of instance d at the
 // instance's local step `local` (dt by lane 0 in FP64, broadcast; unit 0
@@ -281,7 +286,7 @@ __device__ __forceinline__ void batch_walk_unit(const BatchEuler& d, int lu, lon
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBatchWalkThreads) batch_euler_walk_kernel(const BatchEuler* __restrict__ euler,
+__global__ void __launch_bounds__(kBatchWalkThreads, batch_walk_min_blocks<T>()) batch_euler_walk_kernel(const BatchEuler* __restrict__ euler,
                                                                const int* __restrict__ table,
                                                                BatchCtl* __restrict__ bctl)
 {
@@ -318,7 +323,7 @@ __global__ void __launch_bounds__(kBatchWalkThreads) batch_euler_walk_kernel(con
 // the per-step walk kernel's, so results are those of per-step launches bit
 // for bit.
 template <typename T>
-__global__ void __launch_bounds__(kBatchWalkThreads) batch_euler_walk_async_kernel(const BatchEuler* __restrict__ euler,
+__global__ void __launch_bounds__(kBatchWalkThreads, batch_walk_min_blocks<T>()) batch_euler_walk_async_kernel(const BatchEuler* __restrict__ euler,
                                                                      const int* __restrict__ table,
                                                                      BatchCtl* __restrict__ bctl,
                                                                      BatchAsync* __restrict__ q)
