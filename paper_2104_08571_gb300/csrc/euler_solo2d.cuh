@@ -286,9 +286,9 @@ __device__ __forceinline__ void batch_walk_unit(const BatchEuler& d, int lu, lon
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kBatchWalkThreads, batch_walk_min_blocks<T>()) batch_euler_walk_kernel(const BatchEuler* __restrict__ euler,
-                                                               const int* __restrict__ table,
-                                                               BatchCtl* __restrict__ bctl)
+__global__ void __launch_bounds__(kBatchWalkThreads, batch_walk_min_blocks<T>())
+    batch_euler_walk_kernel(const BatchEuler* __restrict__ euler, const int* __restrict__ table,
+                            BatchCtl* __restrict__ bctl)
 {
     const unsigned long long gstep = __ldcg(&bctl->gstep[0]);
     const int end = __ldcg(&bctl->ntiles_e);
@@ -323,10 +323,9 @@ __global__ void __launch_bounds__(kBatchWalkThreads, batch_walk_min_blocks<T>())
 // the per-step walk kernel's, so results are those of per-step launches bit
 // for bit.
 template <typename T>
-__global__ void __launch_bounds__(kBatchWalkThreads, batch_walk_min_blocks<T>()) batch_euler_walk_async_kernel(const BatchEuler* __restrict__ euler,
-                                                                     const int* __restrict__ table,
-                                                                     BatchCtl* __restrict__ bctl,
-                                                                     BatchAsync* __restrict__ q)
+__global__ void __launch_bounds__(kBatchWalkThreads, batch_walk_min_blocks<T>())
+    batch_euler_walk_async_kernel(const BatchEuler* __restrict__ euler, const int* __restrict__ table,
+                                  BatchCtl* __restrict__ bctl, BatchAsync* __restrict__ q)
 {
     const unsigned long long gstep = __ldcg(&bctl->gstep[0]);
     const int lane = threadIdx.x & 31;
