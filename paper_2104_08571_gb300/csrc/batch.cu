@@ -1518,8 +1518,16 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
                 cudaFree(d_t);
                 cudaFree(d_c);
             };
-            if (cudaMalloc(&ctl, n * sizeof(FieldCtl)) != cudaSuccess) { status = RIPPLE_ERR_OOM; break; }
-            cudaMemset(ctl, 0, n * sizeof(FieldCtl));
+            if (cudaMalloc(&ctl, n * sizeof(FieldCtl)) != cudaSuccess) {
+                ctl = nullptr;
+                status = fail(RIPPLE_ERR_OOM, "autotune: control blocks");
+                break;
+            }
+            if (cudaMemsetAsync(ctl, 0, n * sizeof(FieldCtl), s) != cudaSuccess) {
+                cleanup();
+                status = fail(RIPPLE_ERR_CUDA, "autotune: clearing control blocks");
+                break;
+            }
             for (int i = 0; i < n && status == RIPPLE_OK; ++i) {
                 const int64_t dims[2] = {sides[i], sides[i]};
                 size_t bytes = 0;
@@ -1564,22 +1572,36 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
                 const double smax0 = 4.0 * (double)sides[i];
                 std::memcpy(&hc[i].smax[0], &smax0, sizeof(double));
             }
-            cudaMemcpyAsync(ctl, hc.data(), n * sizeof(FieldCtl), cudaMemcpyHostToDevice, s);
-            cudaMalloc(&d_e, n * sizeof(BatchEuler));
-            cudaMalloc(&d_t, table.size() * sizeof(int));
-            cudaMalloc(&d_c, sizeof(BatchCtl));
+            // descriptors, table and control of the sample batch; no launch
+            // unless every one of them is in place
+            if (cudaMalloc(&d_e, n * sizeof(BatchEuler)) != cudaSuccess) d_e = nullptr;
+            if (cudaMalloc(&d_t, table.size() * sizeof(int)) != cudaSuccess) d_t = nullptr;
+            if (cudaMalloc(&d_c, sizeof(BatchCtl)) != cudaSuccess) d_c = nullptr;
+            if (!d_e || !d_t || !d_c) {
+                cleanup();
+                status = fail(RIPPLE_ERR_OOM, "autotune: sample descriptors");
+                break;
+            }
             BatchCtl hb{};
             hb.ntiles_e = (int)table.size();
             hb.ntiles = (int)table.size();
-            cudaMemcpyAsync(d_e, h.data(), n * sizeof(BatchEuler), cudaMemcpyHostToDevice, s);
-            cudaMemcpyAsync(d_t, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice, s);
-            cudaMemcpyAsync(d_c, &hb, sizeof(BatchCtl), cudaMemcpyHostToDevice, s);
+            cudaError_t ce = cudaMemcpyAsync(ctl, hc.data(), n * sizeof(FieldCtl), cudaMemcpyHostToDevice, s);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(d_e, h.data(), n * sizeof(BatchEuler), cudaMemcpyHostToDevice, s);
+            if (ce == cudaSuccess)
+                ce = cudaMemcpyAsync(d_t, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+            if (ce == cudaSuccess) ce = cudaMemcpyAsync(d_c, &hb, sizeof(BatchCtl), cudaMemcpyHostToDevice, s);
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (ce == cudaSuccess) ce = cudaEventCreate(&e0);
+            if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+            if (ce != cudaSuccess) {
+                if (e0) cudaEventDestroy(e0);
+                cleanup();
+                status = cuda_fail(ce, "autotune: sample set-up");
+                break;
+            }
             const int lay_i = lay == RIPPLE_SOA ? LAYOUT_SOA : LAYOUT_AOS;
             const int grid = std::max(1, batch_occupancy(dt, lay_i, v, sg)) * ctx->sm_count;
-            cudaEvent_t e0, e1;
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            cudaError_t ce = cudaSuccess;
             for (int k = 0; k < 3 && ce == cudaSuccess; ++k)
                 ce = launch_batch_step(dt, lay_i, v, sg, grid, s, d_e, nullptr, d_t, d_c, 0);
             cudaEventRecord(e0, s);
@@ -1593,7 +1615,10 @@ static ripple_status autotune(ripple_ctx ctx, const int64_t* sides, int n, rippl
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
             cleanup();
-            if (ce != cudaSuccess) return cuda_fail(ce, "autotune launch");
+            if (ce != cudaSuccess) {
+                status = cuda_fail(ce, "autotune launch");
+                break;
+            }
             const double t = el / reps;
             if (ms) ms[(sg * 2 + li) * kNumBatchVariants + v] = t;
             if (t < best_ms) {
